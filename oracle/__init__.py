@@ -1,0 +1,239 @@
+"""FP64 CPU oracle for the randomized SVD (arXiv:1608.02148), Python side.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The CUDA library
+never calls it, and it shares no code with the CUDA library.
+
+The arithmetic lives in ``rsvd_oracle.c`` (plain C, double precision, OpenMP);
+this module compiles it with gcc into ``oracle/_build/liboracle.so`` and wraps
+each exported function with numpy arrays.  See the C file for the paper
+passages each function follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "rsvd_oracle.c"
+_BUILD = _HERE / "_build"
+_LIB = _BUILD / "liboracle.so"
+
+SDIST = {"normal": 0, "unif": 1, "rademacher": 2}
+DTYPE = {np.dtype(np.float32): 0, np.dtype(np.uint16): 1, np.dtype(np.float64): 2}
+
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (portable flags: no -march, no FMA contraction)."""
+    _BUILD.mkdir(exist_ok=True)
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _BUILD / f"liboracle.{os.getpid()}.so"
+        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
+               str(_SRC), "-o", str(tmp), "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(str(_LIB))
+    P = ctypes.c_void_p
+    I64 = ctypes.c_int64
+    I = ctypes.c_int
+    U64 = ctypes.c_uint64
+    lib.oracle_philox4x32_10.argtypes = [P, P, P]
+    lib.oracle_philox4x32_10.restype = None
+    lib.oracle_omega.argtypes = [I64, I64, U64, I, P, I64]
+    lib.oracle_omega.restype = None
+    lib.oracle_householder_qr.argtypes = [I64, I64, P, P, P]
+    lib.oracle_householder_qr.restype = I
+    lib.oracle_jacobi_svd.argtypes = [I64, I64, P, P, P, P]
+    lib.oracle_jacobi_svd.restype = I
+    lib.oracle_rqb.argtypes = [P, I, I64, I64, I64, I, I, I, I, U64, P, P]
+    lib.oracle_rqb.restype = I
+    lib.oracle_rsvd.argtypes = [P, I, I64, I64, I64, I, I, I, I, U64, P, P, P, P, P]
+    lib.oracle_rsvd.restype = I
+    lib.oracle_power_direct.argtypes = [P, I, I64, I64, I64, I64, I, I, U64, P]
+    lib.oracle_power_direct.restype = I
+    lib.oracle_gemm_ax.argtypes = [P, I, I64, I64, I64, P, I64, P]
+    lib.oracle_gemm_ax.restype = I
+    lib.oracle_gemm_atx.argtypes = [P, I, I64, I64, I64, P, I64, P]
+    lib.oracle_gemm_atx.restype = I
+    lib.oracle_residual_fro2.argtypes = [P, I, I64, I64, I64, P, P, P, I64]
+    lib.oracle_residual_fro2.restype = ctypes.c_double
+    lib.oracle_fro2.argtypes = [P, I, I64, I64, I64]
+    lib.oracle_fro2.restype = ctypes.c_double
+    lib.oracle_sketch_width.argtypes = [I64, I64, I, I]
+    lib.oracle_sketch_width.restype = I64
+    lib.oracle_num_threads.argtypes = []
+    lib.oracle_num_threads.restype = I
+    lib.oracle_set_num_threads.argtypes = [I]
+    lib.oracle_set_num_threads.restype = None
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _amat(A: np.ndarray):
+    """(pointer, dtype code, m, n, lda) of a row-major 2-D array (float32,
+    float64, or uint16 holding BF16 bit patterns); rows may be padded."""
+    if A.ndim != 2 or A.strides[1] != A.itemsize or A.strides[0] % A.itemsize:
+        raise ValueError("A must be 2-D with unit column stride")
+    code = DTYPE.get(A.dtype)
+    if code is None:
+        raise TypeError(f"unsupported dtype {A.dtype}")
+    return _ptr(A), code, A.shape[0], A.shape[1], A.strides[0] // A.itemsize
+
+
+def num_threads() -> int:
+    return _load().oracle_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    _load().oracle_set_num_threads(int(n))
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 block function on one 128-bit counter and 64-bit key."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
+    out = np.zeros(4, dtype=np.uint32)
+    _load().oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def omega(rows: int, l: int, seed: int, sdist: str = "normal") -> np.ndarray:
+    """The FP32 test matrix Omega (rows x l) of Sec. 2.3 as defined in rsvd_oracle.c."""
+    out = np.zeros((rows, l), dtype=np.float32)
+    _load().oracle_omega(rows, l, seed, SDIST[sdist], _ptr(out), l)
+    return out
+
+
+def householder_qr(Y: np.ndarray):
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    m, l = Y.shape
+    Q = np.zeros((m, l))
+    R = np.zeros((l, l))
+    rc = _load().oracle_householder_qr(m, l, _ptr(Y), _ptr(Q), _ptr(R))
+    if rc:
+        raise RuntimeError(f"householder_qr failed ({rc})")
+    return Q, R
+
+
+def jacobi_svd(M: np.ndarray):
+    """One-sided Jacobi: M = Ucols diag(s) J^T, s descending. Returns (Ucols, s, J, sweeps)."""
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    rows, cols = M.shape
+    s = np.zeros(cols)
+    Uc = np.zeros((rows, cols))
+    J = np.zeros((cols, cols))
+    sweeps = _load().oracle_jacobi_svd(rows, cols, _ptr(M), _ptr(s), _ptr(Uc), _ptr(J))
+    if sweeps < 0:
+        raise RuntimeError("jacobi_svd did not converge")
+    return Uc, s, J, sweeps
+
+
+def sketch_width(m: int, n: int, k: int, p: int) -> int:
+    return int(_load().oracle_sketch_width(m, n, k, p))
+
+
+def rqb(A: np.ndarray, k: int, p: int = 10, q: int = 2, sdist: str = "normal", seed: int = 0):
+    """Algorithm rqb. For m < n it returns Q, B of the transposed problem."""
+    ptr, code, m, n, lda = _amat(A)
+    l = sketch_width(m, n, k, p)
+    rows, cols = (m, n) if m >= n else (n, m)
+    Q = np.zeros((rows, l))
+    B = np.zeros((l, cols))
+    rc = _load().oracle_rqb(ptr, code, m, n, lda, k, p, q, SDIST[sdist], seed, _ptr(Q), _ptr(B))
+    if rc:
+        raise RuntimeError(f"oracle rqb failed ({rc})")
+    return Q, B
+
+
+def rsvd(A: np.ndarray, k: int, p: int = 10, q: int = 2, sdist: str = "normal", seed: int = 0,
+         return_qb: bool = False):
+    """Algorithm rSVD: returns d (k), U (m x k), V (n x k) [, Q, B]."""
+    ptr, code, m, n, lda = _amat(A)
+    l = sketch_width(m, n, k, p)
+    rows, cols = (m, n) if m >= n else (n, m)
+    d = np.zeros(k)
+    U = np.zeros((m, k))
+    V = np.zeros((n, k))
+    Q = np.zeros((rows, l)) if return_qb else None
+    B = np.zeros((l, cols)) if return_qb else None
+    rc = _load().oracle_rsvd(ptr, code, m, n, lda, k, p, q, SDIST[sdist], seed, _ptr(d), _ptr(U), _ptr(V),
+                             _ptr(Q) if return_qb else None, _ptr(B) if return_qb else None)
+    if rc:
+        raise RuntimeError(f"oracle rsvd failed ({rc})")
+    if return_qb:
+        return d, U, V, Q, B
+    return d, U, V
+
+
+def power_direct(A: np.ndarray, l: int, q: int, sdist: str = "normal", seed: int = 0) -> np.ndarray:
+    """Algorithm poweriter_direct: Y = (A A^T)^q A Omega (m >= n)."""
+    ptr, code, m, n, lda = _amat(A)
+    Y = np.zeros((m, l))
+    rc = _load().oracle_power_direct(ptr, code, m, n, lda, l, q, SDIST[sdist], seed, _ptr(Y))
+    if rc:
+        raise RuntimeError(f"oracle power_direct failed ({rc})")
+    return Y
+
+
+def gemm_ax(A: np.ndarray, X: np.ndarray) -> np.ndarray:
+    ptr, code, m, n, lda = _amat(A)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    assert X.shape[0] == n
+    Y = np.zeros((m, X.shape[1]))
+    _load().oracle_gemm_ax(ptr, code, m, n, lda, _ptr(X), X.shape[1], _ptr(Y))
+    return Y
+
+
+def gemm_atx(A: np.ndarray, X: np.ndarray) -> np.ndarray:
+    ptr, code, m, n, lda = _amat(A)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    assert X.shape[0] == m
+    Z = np.zeros((n, X.shape[1]))
+    _load().oracle_gemm_atx(ptr, code, m, n, lda, _ptr(X), X.shape[1], _ptr(Z))
+    return Z
+
+
+def residual_fro2(A: np.ndarray, U: np.ndarray, d: np.ndarray, V: np.ndarray) -> float:
+    ptr, code, m, n, lda = _amat(A)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    k = d.shape[0]
+    return float(_load().oracle_residual_fro2(ptr, code, m, n, lda, _ptr(U), _ptr(d), _ptr(V), k))
+
+
+def fro2(A: np.ndarray) -> float:
+    ptr, code, m, n, lda = _amat(A)
+    return float(_load().oracle_fro2(ptr, code, m, n, lda))
+
+
+def canonical_signs(U: np.ndarray, V: np.ndarray):
+    """Flip each singular pair (u_i, v_i) so that the largest-magnitude entry
+    of v_i is positive (ties: lowest index).  Singular vectors are unique only
+    up to such a sign."""
+    U = U.copy()
+    V = V.copy()
+    for c in range(V.shape[1]):
+        i = int(np.argmax(np.abs(V[:, c])))
+        if V[i, c] < 0:
+            U[:, c] = -U[:, c]
+            V[:, c] = -V[:, c]
+    return U, V

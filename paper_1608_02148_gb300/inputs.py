@@ -1,0 +1,103 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws random matrices with a planted spectrum.  It holds none
+of the randomized-SVD arithmetic: orthonormal factors come from a library QR
+(numpy on the host, torch on a device), never from this project's kernels or
+from its CPU oracle.  Both the CUDA path and the oracle are fed the same stored
+values produced here.
+
+Recipes (all seeds explicit):
+
+* ``planted(m, n, sigma)`` -- A = U diag(sigma) V^T with U (m x r) and V (n x r)
+  the Q factors of seeded N(0,1) matrices, r = len(sigma); formed in float64
+  and stored as float32 (or BF16).  With sigma_i = exp(-i/20) on 2000 x 1000
+  this is the small planted workload; truncating sigma plants an exact rank.
+* ``spiked_noise(m, n, sigma, noise_std)`` -- A = W_m diag(sigma) W_n^T + E
+  with E i.i.d. N(0, noise_std^2): the 200000 x 2000 workload uses
+  sigma_i = 1/i and noise_std = 1e-3.  Built with torch on any device.
+* ``ragged_batch(...)`` -- many small planted matrices with log-uniform shapes
+  and exponential spectra exp(-r i), r uniform.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def bf16_bits(a: np.ndarray) -> np.ndarray:
+    """Round float32 values to BF16 (round to nearest even) and return the
+    16-bit patterns as uint16."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    rounding = ((u >> 16) & 1) + 0x7FFF
+    return ((u + rounding) >> 16).astype(np.uint16)
+
+
+def bf16_to_f32(bits: np.ndarray) -> np.ndarray:
+    return (bits.astype(np.uint32) << 16).view(np.float32)
+
+
+def _orthonormal(rng: np.random.Generator, rows: int, cols: int) -> np.ndarray:
+    g = rng.standard_normal((rows, cols))
+    q, r = np.linalg.qr(g)
+    # Fix the column signs so the factor is a deterministic function of the seed.
+    return q * np.sign(np.diag(r))[None, :]
+
+
+def planted(m: int, n: int, sigma, seed: int, dtype=np.float32) -> np.ndarray:
+    """A = U diag(sigma) V^T (float64 product, stored in ``dtype``)."""
+    sigma = np.asarray(sigma, dtype=np.float64)
+    r = sigma.shape[0]
+    assert r <= min(m, n)
+    rng = np.random.default_rng(seed)
+    U = _orthonormal(rng, m, r)
+    V = _orthonormal(rng, n, r)
+    A = (U * sigma[None, :]) @ V.T
+    if dtype == "bf16":
+        return bf16_bits(A.astype(np.float32))
+    return A.astype(dtype)
+
+
+def exp_spectrum(count: int, rate: float) -> np.ndarray:
+    """sigma_i = exp(-rate * i), i = 1..count."""
+    return np.exp(-rate * np.arange(1, count + 1, dtype=np.float64))
+
+
+def small_planted(seed: int = 0x160802148 + 1000) -> np.ndarray:
+    """2000 x 1000, sigma_i = exp(-i/20) (the small planted workload)."""
+    return planted(2000, 1000, exp_spectrum(1000, 1.0 / 20.0), seed)
+
+
+def spiked_noise(m: int, n: int, sigma, noise_std: float, seed: int, device="cpu", dtype=None):
+    """A = W_m diag(sigma) W_n^T + E on a torch device (float32 storage).
+
+    W_m (m x r) and W_n (n x r) are Q factors of seeded Gaussians (torch QR),
+    r = len(sigma); E is i.i.d. N(0, noise_std^2)."""
+    import torch
+
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+    sig = torch.as_tensor(np.asarray(sigma, dtype=np.float32), device=dev)
+    r = sig.shape[0]
+    Wm, _ = torch.linalg.qr(torch.randn(m, r, generator=gen, device=dev, dtype=torch.float32))
+    Wn, _ = torch.linalg.qr(torch.randn(n, r, generator=gen, device=dev, dtype=torch.float32))
+    A = torch.randn(m, n, generator=gen, device=dev, dtype=torch.float32)
+    A.mul_(noise_std)
+    A.addmm_(Wm * sig[None, :], Wn.T)
+    del Wm, Wn
+    if dtype is not None:
+        A = A.to(dtype)
+    return A
+
+
+def ragged_shapes(count: int, m_range, n_range, seed: int):
+    """Log-uniform integer shapes (m_b, n_b) and exponential decay rates."""
+    rng = np.random.default_rng(seed)
+    lm = rng.uniform(math.log(m_range[0]), math.log(m_range[1]), count)
+    ln = rng.uniform(math.log(n_range[0]), math.log(n_range[1]), count)
+    ms = np.rint(np.exp(lm)).astype(np.int64)
+    ns = np.rint(np.exp(ln)).astype(np.int64)
+    rates = rng.uniform(0.05, 0.5, count)
+    return ms, ns, rates
