@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark: rank-k randomized SVD wall time and HBM-roofline fraction on GB300.
+
+Default workload (N = 1): rSVD of a 200000 x 2000 FP32 matrix with planted
+spectrum sigma_i = 1/i plus i.i.d. N(0, 1e-3^2) noise, k = 100, p = 10, q = 2
+(2q + 2 = 6 passes over A).  A (1.6 GB) is larger than L2 (129 MB), so every
+pass streams it from HBM; no extra L2 flush is needed between steps.
+
+One step = one full rsvdgb_rsvd call (Omega, sketch, q subspace iterations
+with CholeskyQR, projection, SVD of B, back-projection) through the C ABI with
+A resident in HBM.  `value` is milliseconds per rSVD for the whole job (with
+N ranks each factoring its own matrix: max-over-ranks time / (N * steps)).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores (a bounded row
+sample of the same workload, scaled to the full row count).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "rank-k rSVD wall time and % HBM roofline, mixed/learned-q vs FP32 at equal error"
+
+WORKLOADS = {
+    "spiked200k": dict(desc="rsvd 200000x2000 fp32, sigma_i=1/i + N(0,1e-3^2) noise, k=100 p=10 q=2",
+                       m=200000, n=2000, k=100, p=10, q=2, noise=1e-3),
+    "planted2k": dict(desc="rsvd 2000x1000 fp32, sigma_i=exp(-i/20), k=20 p=10 q=2",
+                      m=2000, n=1000, k=20, p=10, q=2, noise=0.0),
+}
+
+# FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
+SIMT_FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="spiked200k")
+    ap.add_argument("--prec", default="fp32")
+    ap.add_argument("--engine", default="auto")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=40000, help="row sample for the oracle baseline")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = (uuid or "").lower()
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and self.uuid not in parts[0].lower():
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value, device):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_matrix(wl, seed, device):
+    import numpy as np
+    from paper_1608_02148_gb300 import inputs
+    m, n = wl["m"], wl["n"]
+    if wl["noise"] > 0:
+        sigma = 1.0 / np.arange(1, n + 1, dtype=np.float64)
+        return inputs.spiked_noise(m, n, sigma, wl["noise"], seed, device=device)
+    import torch
+    return torch.from_numpy(inputs.planted(m, n, inputs.exp_spectrum(n, 1.0 / 20.0), seed)).to(device)
+
+
+def cpu_oracle_time(A_host_rows, wl, seed_omega):
+    """Median-free single timing of the FP64 oracle rSVD on a row block."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.rsvd(A_host_rows, wl["k"], p=wl["p"], q=wl["q"], seed=seed_omega)
+    return time.perf_counter() - t0
+
+
+def run_reference(args, wl):
+    """The FP64 CPU oracle as the reference arm (rank 0 only)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    from paper_1608_02148_gb300 import inputs
+    oracle.build()
+    rows = min(wl["m"], 10000)
+    rng_seed = 0x160802148 + 2000
+    # same recipe as the GPU workload, on the host, restricted to a row block
+    if wl["noise"] > 0:
+        sigma = 1.0 / np.arange(1, wl["n"] + 1, dtype=np.float64)
+        A = inputs.spiked_noise(rows, wl["n"], sigma, wl["noise"], rng_seed,
+                                device="cpu").numpy()
+    else:
+        A = inputs.planted(rows, wl["n"], inputs.exp_spectrum(wl["n"], 1.0 / 20.0), rng_seed)
+    scale = wl["m"] / rows
+    for _ in range(max(args.warmup, 0)):
+        cpu_oracle_time(A, wl, 0)
+    times = [cpu_oracle_time(A, wl, 0) * scale * 1e3 for _ in range(args.steps)]
+    ms = statistics.median(times)
+    cores = oracle.num_threads()
+    line = {"metric": METRIC, "impl": "reference", "value": ms, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "m": wl["m"], "n": wl["n"], "k": wl["k"], "p": wl["p"],
+                       "q": wl["q"]},
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
+                             "sample": f"oracle rsvd on a {rows}x{wl['n']} row block of the workload, time x{scale:g}"},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import numpy as np
+    import torch
+    from paper_1608_02148_gb300 import build as cuda_build
+    from paper_1608_02148_gb300 import rsvdgb as rs
+
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if rank == 0 or not os.path.exists(cuda_build.LIB):
+        cuda_build.build()
+    barrier(world)
+    stream = torch.cuda.current_stream(dev)
+    h = rs.Handle(local, stream)
+    peaks, peak_kind = measured_peaks()
+
+    seed = 0x160802148 + 2000 + rank
+    A = make_matrix(wl, seed, dev)
+    torch.cuda.synchronize()
+    m, n, k = wl["m"], wl["n"], wl["k"]
+    opts = rs.make_opts(p=wl["p"], q=wl["q"], seed=rank, prec=args.prec, engine=args.engine)
+    bufs = (torch.empty(k, device=dev), torch.empty(m, k, device=dev), torch.empty(n, k, device=dev),
+            torch.zeros(rs.INFO_BYTES, dtype=torch.uint8, device=dev))
+
+    for _ in range(max(args.warmup, 0)):
+        rs.rsvdgb_rsvd(h, A, k, opts=opts, out=bufs, sync_info=False)
+    torch.cuda.synchronize()
+    info = rs._info_from(bufs[3])
+    if info.status != 0:
+        raise SystemExit(f"rsvd reported {info.as_dict()}")
+
+    # ---------------- timed region (device-resident A) ----------------
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    rs.rsvdgb_profile_passes(h, True)
+    launches0 = rs.rsvdgb_kernel_launches()
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        rs.rsvdgb_rsvd(h, A, k, opts=opts, out=bufs, sync_info=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    launches = rs.rsvdgb_kernel_launches() - launches0
+    pass_ms, pass_n, pass_bytes = rs.rsvdgb_profile_read(h)
+    rs.rsvdgb_profile_passes(h, False)
+    elapsed = ev0.elapsed_time(ev1)
+    elapsed = max_over_ranks(world, elapsed, dev)
+    ms_per_step = elapsed / args.steps
+    value = elapsed / (args.steps * world)
+
+    passes = 2 * wl["q"] + 2
+    a_bytes = m * n * 4
+    hbm = peaks["hbm_gbs"]
+    roof_ms = passes * a_bytes / (hbm * 1e9) * 1e3
+    pass_avg_ms = pass_ms / max(pass_n, 1)
+    l = rs.rsvdgb_sketch_width(m, n, k, wl["p"])
+    achieved_gbs = (pass_bytes / max(pass_n, 1)) / (pass_avg_ms * 1e-3) / 1e9
+    achieved_tflops = (2.0 * m * n * l) / (pass_avg_ms * 1e-3) / 1e12
+    engine = args.engine
+    if engine in ("auto", "simt"):
+        roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": SIMT_FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved_tflops / SIMT_FP32_PEAK_TFLOPS, "traffic": None,
+                    "kernel": "simt_gemm (pass over A, FP32 FMA)",
+                    "peak_source": "unit counts: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                    "hbm_view": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm, "frac": achieved_gbs / hbm,
+                                 "peak_source": peak_kind}}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm, "traffic": None, "peak_source": peak_kind}
+
+    # ---------------- end to end through the host-buffer entry point ----------------
+    e2e = None
+    if args.e2e_steps > 0:
+        A_host = A.cpu().pin_memory()
+        outs = (torch.empty(k, pin_memory=True), torch.empty(m, k, pin_memory=True),
+                torch.empty(n, k, pin_memory=True))
+        rs.rsvdgb_rsvd_host(h, A_host, k, opts=opts, out=outs)
+        ts = []
+        for _ in range(args.e2e_steps):
+            barrier(world)
+            t0 = time.perf_counter()
+            rs.rsvdgb_rsvd_host(h, A_host, k, opts=opts, out=outs)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        e2e_ms = max_over_ranks(world, statistics.median(ts), dev)
+        e2e = {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": a_bytes,
+               "d2h_bytes_per_step": 4 * (k + m * k + n * k) + rs.INFO_BYTES}
+        del A_host
+
+    # ---------------- CPU oracle baseline (rank 0, N = 1 only) ----------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rows = min(args.cpu_rows, m)
+        A_rows = A[:rows].cpu().numpy()
+        t = cpu_oracle_time(A_rows, wl, 0)
+        cpu = {"value": t * (m / rows) * 1e3, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"oracle rsvd on rows 0..{rows - 1} of the same A ({rows}x{n}), time x{m / rows:g}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl["desc"], "m": m, "n": n, "k": k, "p": wl["p"], "q": wl["q"], "l": l,
+                           "prec": args.prec, "engine": engine, "passes_over_A": passes,
+                           "l2": "A (%.1f GB) larger than L2; no flush needed" % (a_bytes / 1e9),
+                           "parallelism": f"replicas x{world}"},
+                "hbm_roofline": {"time_ms": roof_ms, "frac_of_step": roof_ms / ms_per_step,
+                                 "peak_gbs": hbm, "peak_source": peak_kind},
+                "roofline": roofline,
+                "pass_kernels": {"launches": pass_n, "avg_ms": pass_avg_ms, "share_of_step":
+                                 pass_ms / max(elapsed, 1e-9) if world == 1 else None},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+                "info": info.as_dict()}
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

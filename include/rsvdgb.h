@@ -1,0 +1,203 @@
+/*
+ * rsvdgb -- randomized SVD for NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of the library librsvdgb.so.  The method is the randomized SVD of
+ * Erichson, Voronin, Brunton and Kutz, "Randomized Matrix Decompositions Using
+ * R" (arXiv:1608.02148): the randomized QB decomposition (Algorithm rqb) with
+ * subspace iterations (Algorithm sub_iterations) followed by the SVD of the
+ * small factor and the back-projection U = Q Ut (Algorithm rSVD, Eq. UQU).
+ *
+ * General conventions (apply to every call unless its comment says otherwise)
+ *  - Pointers named "device" must point to memory of the handle's device.  The
+ *    caller owns every input and output buffer; the library never frees them
+ *    and never writes to an input.  The handle owns its workspace.
+ *  - Matrices are row-major with an explicit leading dimension (elements
+ *    between consecutive rows).  FP32 data must be 4-byte aligned, BF16 data
+ *    2-byte aligned.
+ *  - Calls are asynchronous on the handle's stream: they return after the
+ *    launches are queued, and outputs (including rsvdgb_info) are valid once
+ *    that stream has been synchronised.  Exceptions: rsvdgb_create,
+ *    rsvdgb_destroy and the *_host entry points, which synchronise.
+ *  - Argument errors are detected on the host before any launch and returned
+ *    as RSVDGB_ERR_INVALID_ARG with nothing queued.  Errors found on the device
+ *    (Cholesky breakdown, non-finite input, an expired bounded wait) are
+ *    written to rsvdgb_info.status; kernels never trap.
+ */
+#ifndef RSVDGB_H
+#define RSVDGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rsvdgb_handle rsvdgb_handle;
+
+/* Status codes returned by every int-returning call and stored in
+ * rsvdgb_info.status. */
+enum {
+    RSVDGB_OK = 0,
+    RSVDGB_ERR_INVALID_ARG = 1, /* bad size, pointer, alignment or option      */
+    RSVDGB_ERR_NOMEM = 2,       /* workspace allocation failed                 */
+    RSVDGB_ERR_CUDA = 3,        /* a CUDA runtime call failed                  */
+    RSVDGB_ERR_BREAKDOWN = 4,   /* Cholesky of a Gram matrix lost definiteness */
+    RSVDGB_ERR_NONFINITE = 5,   /* ||A||_F^2 is not finite                     */
+    RSVDGB_ERR_TIMEOUT = 6,     /* a bounded device-side wait expired          */
+    RSVDGB_ERR_UNSUPPORTED = 7  /* valid request this build does not serve     */
+};
+
+/* Element type of the input matrix A. */
+enum { RSVDGB_F32 = 0, RSVDGB_BF16 = 1 };
+
+/* Distribution of the test matrix Omega, Sec. 2.3 ("normal", "unif",
+ * "rademacher" of the rsvd() argument sdist, Sec. 3.6). */
+enum { RSVDGB_SDIST_NORMAL = 0, RSVDGB_SDIST_UNIF = 1, RSVDGB_SDIST_RADEMACHER = 2 };
+
+/* Arithmetic of the passes over A.
+ *  FP32        : every pass FP32-accurate (3xTF32 products on the tensor cores
+ *                or FP32 FMA), FP32 accumulation.
+ *  BF16_SKETCH : sketch and power passes with A and the panel rounded to BF16,
+ *                FP32 accumulation; the final projection B = Q^T A stays
+ *                FP32-accurate. */
+enum { RSVDGB_PREC_FP32 = 0, RSVDGB_PREC_BF16_SKETCH = 1 };
+
+/* Storage order of A as passed by the caller. COL_MAJOR is served as the
+ * row-major transpose (U and V swap roles internally). */
+enum { RSVDGB_ROW_MAJOR = 0, RSVDGB_COL_MAJOR = 1 };
+
+/* Kernel family for the passes over A. AUTO picks the tensor-core kernels
+ * where they apply; SIMT forces the FP32 FMA kernels. */
+enum { RSVDGB_ENGINE_AUTO = 0, RSVDGB_ENGINE_SIMT = 1, RSVDGB_ENGINE_TC = 2 };
+
+typedef struct rsvdgb_opts {
+    int32_t p;       /* oversampling, l = k + p (Sec. 2.2.1); default 10         */
+    int32_t q;       /* subspace iterations (Sec. 2.2.2); default 2              */
+    int32_t sdist;   /* RSVDGB_SDIST_*; default NORMAL                            */
+    int32_t prec;    /* RSVDGB_PREC_*; default FP32                               */
+    uint64_t seed;   /* Philox key of Omega; default 0                           */
+    int32_t layout;  /* RSVDGB_ROW_MAJOR / COL_MAJOR; default ROW_MAJOR          */
+    int32_t engine;  /* RSVDGB_ENGINE_*; default AUTO                             */
+    int32_t reserved[6];
+} rsvdgb_opts;
+
+/* Diagnostics written by the device at the end of a call (device memory). */
+typedef struct rsvdgb_info {
+    int32_t status;      /* RSVDGB_OK or a device-detected error code          */
+    int32_t q_used;      /* subspace iterations performed                      */
+    int32_t p_used;      /* oversampling used (l - k after clamping)           */
+    int32_t l;           /* sketch width l = min(k + p, min(m, n))             */
+    double fro2_A;       /* ||A||_F^2, accumulated in FP64 during the sketch   */
+    double fro2_B;       /* ||B||_F^2 = sum of all l squared singular values   */
+    double err2_QB;      /* ||A - Q B||_F^2 = fro2_A - fro2_B                  */
+    double err2_k;       /* ||A - U_k S_k V_k^T||_F^2 = fro2_A - sum_k s_i^2   */
+    int32_t breakdowns;  /* Cholesky breakdowns met (each retried with a shift) */
+    int32_t reserved[7];
+} rsvdgb_info;
+
+/* Create a handle bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The handle's workspace
+ * grows on demand and is freed by rsvdgb_destroy.  Returns RSVDGB_OK,
+ * RSVDGB_ERR_INVALID_ARG (h NULL, bad device) or RSVDGB_ERR_CUDA. */
+int rsvdgb_create(rsvdgb_handle** h, int device, void* cuda_stream);
+
+/* Synchronise the handle's stream and free the handle and its workspace. */
+int rsvdgb_destroy(rsvdgb_handle* h);
+
+/* Rebind the handle to another stream of the same device. */
+int rsvdgb_set_stream(rsvdgb_handle* h, void* cuda_stream);
+
+/* Defaults of the paper's rsvd() (Sec. 3.6, remark in Sec. 3.3): p = 10,
+ * q = 2, sdist = normal; prec FP32, seed 0, row-major, engine AUTO. */
+void rsvdgb_default_opts(rsvdgb_opts* o);
+
+/* Human-readable name of a status code (static storage). */
+const char* rsvdgb_status_string(int status);
+
+/* Sketch width l = min(k + p, min(m, n)) that a call with these sizes uses
+ * (Sec. 2.2.1 with the clamp to min(m, n)). */
+int rsvdgb_sketch_width(int64_t m, int64_t n, int k, int p);
+
+/*
+ * rsvd(A, k, nu, nv, p, q, sdist) of Sec. 3.6 -- Algorithm rSVD.
+ *   A      device, m x n (row-major, leading dimension lda >= n; with
+ *          opts->layout = COL_MAJOR it is n x m column-major, i.e. lda >= m),
+ *          element type dtype (RSVDGB_F32 or RSVDGB_BF16).  Read only.
+ *   k      target rank, 1 <= k < min(m, n) (Algorithm rqb input condition).
+ *   nu, nv number of left / right singular vectors to return, 0..k; -1 = k.
+ *   d      device float[k]: singular values, descending.
+ *   U      device float, m x nu row-major with ldu >= nu (may be NULL if nu = 0).
+ *   V      device float, n x nv row-major with ldv >= nv (NOT transposed, as in
+ *          the paper's return value v; may be NULL if nv = 0).
+ *   info   device rsvdgb_info or NULL.
+ * A is factored as A ~ U diag(d) V^T.  Singular vectors are defined up to the
+ * sign of each pair (u_i, v_i).  Returns RSVDGB_OK once queued,
+ * RSVDGB_ERR_INVALID_ARG, RSVDGB_ERR_NOMEM or RSVDGB_ERR_CUDA.
+ */
+int rsvdgb_rsvd(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k, int nu, int nv,
+                const rsvdgb_opts* opts, float* d, float* U, int64_t ldu, float* V, int64_t ldv, rsvdgb_info* info);
+
+/*
+ * Same as rsvdgb_rsvd, but A, d, U, V and info are HOST pointers (pinned
+ * memory gives full copy bandwidth; pageable memory works).  The call copies A
+ * to a device buffer owned by the handle, runs the factorisation, copies the
+ * results back and synchronises.  Returns the device status (info->status) if
+ * the launches succeeded.
+ */
+int rsvdgb_rsvd_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k, int nu,
+                     int nv, const rsvdgb_opts* opts, float* d, float* U, int64_t ldu, float* V, int64_t ldv,
+                     rsvdgb_info* info);
+
+/*
+ * Algorithm rqb (Sec. 3.3): A ~ Q B with Q (m x l) orthonormal and
+ * B = Q^T A (l x n), Eq. BQA.  Q is written row-major m x l (ldq >= l), B
+ * row-major l x n (ldb >= n); both device float.  Requires m >= n with a
+ * row-major A (the transposition trick of rsvdgb_rsvd is not applied here).
+ */
+int rsvdgb_rqb(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k,
+               const rsvdgb_opts* opts, float* Q, int64_t ldq, float* B, int64_t ldb, rsvdgb_info* info);
+
+/*
+ * The test matrix Omega of Sec. 2.3 (Algorithm rqb step 2), rows x l,
+ * written row-major to the device buffer out (ld >= l).  Element (i, j) comes
+ * from Philox4x32-10 with key (seed mod 2^32, seed >> 32) and counter
+ * (i/4 mod 2^32, i/4 >> 32, j, 0); normal entries are Box-Muller on word pairs
+ * (x0,x1) -> rows 4r, 4r+1 and (x2,x3) -> rows 4r+2, 4r+3, computed in double
+ * and rounded to float; unif = 2u - 1; rademacher = sign from bit 31.
+ */
+int rsvdgb_omega(rsvdgb_handle* h, int64_t rows, int l, uint64_t seed, int sdist, float* out, int64_t ld);
+
+/*
+ * Kernel-level access to the two passes over A, for tests and tuning:
+ *   rsvdgb_pass_ax  : Y (m x l) = A X,    X device float n x l row-major (ldx)
+ *   rsvdgb_pass_atx : Z (n x l) = A^T X,  X device float m x l row-major (ldx)
+ * Outputs row-major with leading dimension ldy / ldz.  `engine` and `prec`
+ * select the kernel family and arithmetic as in rsvdgb_opts.
+ */
+int rsvdgb_pass_ax(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const float* X,
+                   int64_t ldx, int l, float* Y, int64_t ldy, int engine, int prec);
+int rsvdgb_pass_atx(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const float* X,
+                    int64_t ldx, int l, float* Z, int64_t ldz, int engine, int prec);
+
+/*
+ * Instrumentation (not part of the paper's method).
+ *  rsvdgb_profile_passes : when enable != 0, the handle records a CUDA event
+ *      pair on its stream around every launch of a pass kernel over A (the
+ *      sketch, power and projection passes) and accumulates the algorithmic
+ *      bytes of A each launch must read.  enable = 0 stops recording; either
+ *      call clears what was recorded.
+ *  rsvdgb_profile_read : synchronises the handle's stream and returns the
+ *      summed event time in milliseconds, the number of recorded launches and
+ *      the summed algorithmic bytes.  Any output pointer may be NULL.
+ *  rsvdgb_kernel_launches : process-wide count of kernels this library has
+ *      launched (all handles, all devices).
+ */
+int rsvdgb_profile_passes(rsvdgb_handle* h, int enable);
+int rsvdgb_profile_read(rsvdgb_handle* h, double* pass_ms, int64_t* pass_launches, double* pass_bytes);
+int64_t rsvdgb_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSVDGB_H */

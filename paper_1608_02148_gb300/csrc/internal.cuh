@@ -1,0 +1,109 @@
+// Internal declarations shared by the CUDA translation units of librsvdgb.
+//
+// Storage convention inside the library: every tall-skinny matrix (the test
+// matrix Omega, the sketch Y, the bases Q and Q_n, A^T Y, B^T) is stored
+// COLUMN-MAJOR: column j of an r x l matrix starts at base + j * ld, with ld
+// a multiple of 32 elements.  Columns l..l_pad-1 and rows r..ld-1 are kept at
+// zero.  This makes every such matrix a K-major operand for the tensor cores
+// and gives coalesced column accesses for the FP32 kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rsvdgb.h"
+
+namespace rsvdgb {
+
+#define RSVDGB_CUDA_TRY(expr)                                   \
+    do {                                                        \
+        cudaError_t err_ = (expr);                              \
+        if (err_ != cudaSuccess) return RSVDGB_ERR_CUDA;        \
+    } while (0)
+
+// Process-wide count of kernel launches issued by the library.
+void count_launches(int n = 1);
+int64_t launches_so_far();
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }
+
+// ---------------------------------------------------------------------------
+// Test matrix (Sec. 2.3)
+// ---------------------------------------------------------------------------
+// Writes Omega (rows x l) column-major into out (column j at out + j*ld),
+// zero-filling rows rows..rows_pad-1 and columns l..l_pad-1.
+void launch_omega(cudaStream_t s, int64_t rows, int64_t rows_pad, int l, int l_pad, uint64_t seed, int sdist,
+                  float* out, int64_t ld);
+// Row-major variant used by the public rsvdgb_omega entry point.
+void launch_omega_rowmajor(cudaStream_t s, int64_t rows, int l, uint64_t seed, int sdist, float* out, int64_t ld);
+
+// ---------------------------------------------------------------------------
+// FP32 FMA (SIMT) general product  C = op(A) op(B)
+//   op(A)(i,k) = AT ? A[k*lda + i] : A[i*lda + k]          (M x K)
+//   op(B)(k,j) = BT ? B[j*ldb + k] : B[k*ldb + j]          (K x N)
+//   C(i,j) stored at CT ? C[j*ldc + i] : C[i*ldc + j]       (M x N)
+// With splits > 1 the K range is cut into `splits` chunks and chunk z writes
+// its partial product at C + z * split_stride (reduce afterwards).
+// If fro2 != nullptr, the squares of op(A) are summed (FP64 atomics) from the
+// first N-tile of every block row: that is ||A||_F^2 when A is read once.
+// ---------------------------------------------------------------------------
+struct GemmArgs {
+    const void* A;
+    int64_t lda;
+    int a_bf16;  // op(A) elements stored as BF16 (only for A, not B)
+    const float* B;
+    int64_t ldb;
+    float* C;
+    int64_t ldc;
+    int64_t M, N, K;
+    int splits;
+    int64_t split_stride;
+    double* fro2;
+};
+void launch_simt_gemm(cudaStream_t s, bool AT, bool BT, bool CT, const GemmArgs& g);
+
+// Sum `splits` partial matrices (each rows x cols with leading dimension ld,
+// consecutive partials split_stride apart) in FP64 and write FP32 (out32) or
+// FP64 (out64) with leading dimension ld_out.
+void launch_reduce_splits(cudaStream_t s, const float* part, int splits, int64_t split_stride, int64_t rows,
+                          int64_t cols, int64_t ld, float* out32, double* out64, int64_t ld_out);
+
+// ---------------------------------------------------------------------------
+// Small l x l kernels (one CTA)
+// ---------------------------------------------------------------------------
+// Cholesky G + shift*I = R^T R of a symmetric l x l Gram matrix (FP64 input,
+// row-major, ld = l) by Gaussian elimination that also produces R^{-T};
+// writes R (if non-null) and T = R^{-1} as FP32 row-major l x l (upper
+// triangular, zero below).  A non-positive or non-finite pivot sets
+// *status = RSVDGB_ERR_BREAKDOWN and increments *breakdowns; the pivot is then
+// replaced so that the factor stays finite.
+void launch_chol_inv(cudaStream_t s, const double* G, int l, float shift_rel, float* R, float* T, int* status,
+                     int* breakdowns);
+// C = A B for l x l FP32 row-major matrices (used for T1 T2 and R2 R1).
+void launch_small_matmul(cudaStream_t s, const float* A, const float* B, float* C, int l);
+// One-sided Jacobi SVD of the l x l FP32 matrix M (row-major): M J = W with
+// orthogonal columns.  Outputs (sorted by descending sigma):
+//   sigma[l] (FP32), Ut (l x l row-major, Ut[:,c] = W[:,c] / sigma_c),
+//   Jt (l x l row-major, the accumulated rotations, column c = right vector).
+// Also writes the first k values to d (float) and sum-of-squares diagnostics.
+void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, float* Ut, float* Jt, float* work);
+// Transpose an l x l row-major matrix: out = in^T.
+void launch_small_transpose(cudaStream_t s, const float* in, float* out, int l);
+// d[0..k) = sigma[0..k); info fields from fro2_A and sigma.
+void launch_finalize_info(cudaStream_t s, const float* sigma, int l, int k, float* d, const double* fro2A,
+                          const int* status, const int* breakdowns, int q, int p_used, rsvdgb_info* info);
+// Raise the dynamic shared-memory limit of the one-CTA kernels on the
+// current device (called once per handle).
+int init_small_kernels();
+// Set an int to zero and a double to zero.
+void launch_clear_scalars(cudaStream_t s, int* status, int* breakdowns, double* fro2);
+
+// Convert a column-major r x l (ld) matrix to row-major (ldo) with cols
+// columns (cols <= l), i.e. out[i*ldo + j] = in[j*ld + i].
+void launch_colmajor_to_rowmajor(cudaStream_t s, const float* in, int64_t ld, int64_t rows, int cols, float* out,
+                                 int64_t ldo);
+void launch_rowmajor_to_colmajor(cudaStream_t s, const float* in, int64_t ldi, int64_t rows, int cols, int cols_pad,
+                                 float* out, int64_t ld);
+
+}  // namespace rsvdgb

@@ -1,0 +1,696 @@
+// Host orchestration and the C ABI of librsvdgb.
+//
+// rsvdgb_rsvd runs Algorithm rSVD of Sec. 3.3 on the device:
+//   1  l = min(k + p, min(m, n))                          (Sec. 2.2.1)
+//   2  Omega (n x l) from Philox                          (Sec. 2.3)
+//   3  Y = A Omega                                        (Eq. YAQ)
+//   4  q times: Q = qr(Y); Q = qr(A^T Q); Y = A Q         (Algorithm sub_iterations)
+//   9  Q = qr(Y)                                          (Algorithm rqb step 9)
+//  10  B = Q^T A                                          (Eq. BQA)
+//      [Ut, S, V] = svd(B); U = Q Ut                      (Algorithm rSVD, Eq. UQU)
+// Every step is a kernel on the handle's stream; nothing synchronises with
+// the host.  "qr" is CholeskyQR: Gram matrix, Cholesky, basis change.  The
+// m-side factorisations inside the iteration only need the span of Y, so they
+// use one Cholesky step; the final Q, the n-side bases and the factorisation
+// of B^T use two (CholeskyQR2).  The SVD of B is taken as B^T = Q_B R_B
+// (CholeskyQR2) followed by the one-sided Jacobi SVD of the l x l R_B^T:
+// R_B^T J = W Sigma gives B = W Sigma (Q_B J)^T, i.e. Ut = W and V = Q_B J.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace rsvdgb;
+
+namespace rsvdgb {
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace rsvdgb
+
+// Event pairs bracketing the pass kernels over A (instrumentation).
+struct PassProfile {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;  // 2 per recorded launch
+    size_t used = 0;              // recorded launches
+    double bytes = 0.0;           // algorithmic bytes of A over the recorded launches
+};
+
+struct rsvdgb_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 148;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    void* host_stage = nullptr;  // device buffers for the *_host entry points
+    size_t host_stage_bytes = 0;
+    PassProfile prof;
+};
+
+namespace {
+
+constexpr int kMaxL = 224;  // widest sketch the one-CTA l x l kernels hold in shared memory
+
+// Bump allocator over the handle's workspace (256-byte aligned pieces).
+struct Carve {
+    char* base;
+    size_t off = 0;
+    explicit Carve(void* b) : base((char*)b) {}
+    template <class T>
+    T* take(size_t count)
+    {
+        off = (size_t)round_up((int64_t)off, 256);
+        T* p = base ? (T*)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// Problem geometry after the m >= n normalisation.  The logical matrix is
+// either the stored row-major matrix S or its transpose.
+struct Geom {
+    const void* A;
+    int64_t lda;
+    int a_bf16;
+    int64_t m, n;  // logical rows >= logical cols
+    bool trans;    // logical = S^T
+    bool swap_uv;  // user's U <- logical V
+    int l;
+    int64_t ldm, ldn;
+};
+
+struct Work {
+    float *Pt, *Yt, *Qt, *Wt, *Zt, *part;
+    double* G;
+    float *T1, *T2, *T, *R1, *R2, *RB, *M, *sigma, *Ut, *Jt, *jwork;
+    int *status, *breakdowns;
+    double* fro2;
+};
+
+int splits_for(int64_t tiles, int64_t K, int sm_count)
+{
+    int64_t want = ceil_div(4 * (int64_t)sm_count, std::max<int64_t>(tiles, 1));
+    int64_t cap = std::max<int64_t>(1, K / 256);
+    want = std::min<int64_t>(std::min<int64_t>(want, cap), 256);
+    return (int)std::max<int64_t>(want, 1);
+}
+
+size_t partial_floats(const Geom& g, int sm_count)
+{
+    const int64_t L = g.l;
+    // largest K-split product: A^T-side pass (M = n, K = m), Grams (M = N = l)
+    int64_t tiles_at = ceil_div(g.n, 64) * ceil_div(L, 64);
+    int64_t s_at = splits_for(tiles_at, g.m, sm_count);
+    int64_t tiles_g = ceil_div(L, 64) * ceil_div(L, 64);
+    int64_t s_gm = splits_for(tiles_g, g.m, sm_count);
+    int64_t need = std::max<int64_t>(s_at * L * g.ldn, s_gm * L * L);
+    // the transposed A-side pass splits over K = n with M = m
+    int64_t tiles_a = ceil_div(g.m, 64) * ceil_div(L, 64);
+    int64_t s_a = splits_for(tiles_a, g.n, sm_count);
+    need = std::max<int64_t>(need, s_a * L * g.ldm);
+    return (size_t)need;
+}
+
+void carve_work(Carve& c, const Geom& g, int sm_count, Work& w)
+{
+    const int64_t L = g.l;
+    w.Pt = c.take<float>(L * g.ldn);
+    w.Yt = c.take<float>(L * g.ldm);
+    w.Qt = c.take<float>(L * g.ldm);
+    w.Wt = c.take<float>(L * g.ldn);
+    w.Zt = c.take<float>(L * g.ldn);
+    w.part = c.take<float>(partial_floats(g, sm_count));
+    w.G = c.take<double>(L * L);
+    w.T1 = c.take<float>(L * L);
+    w.T2 = c.take<float>(L * L);
+    w.T = c.take<float>(L * L);
+    w.R1 = c.take<float>(L * L);
+    w.R2 = c.take<float>(L * L);
+    w.RB = c.take<float>(L * L);
+    w.M = c.take<float>(L * L);
+    w.sigma = c.take<float>(256);
+    w.Ut = c.take<float>(L * L);
+    w.Jt = c.take<float>(L * L);
+    w.jwork = c.take<float>(2 * (L + 2) * (L + 2));
+    w.status = c.take<int>(1);
+    w.breakdowns = c.take<int>(1);
+    w.fro2 = c.take<double>(1);
+}
+
+int ensure_workspace(rsvdgb_handle* h, size_t bytes)
+{
+    if (bytes <= h->ws_bytes) return RSVDGB_OK;
+    if (h->ws) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return RSVDGB_ERR_NOMEM;
+    }
+    h->ws_bytes = bytes;
+    RSVDGB_CUDA_TRY(cudaMemsetAsync(h->ws, 0, bytes, h->stream));
+    return RSVDGB_OK;
+}
+
+// ----- tall-skinny products on the logical matrix ---------------------------
+
+// Generic tall product with optional K split: C = op(A) op(B), written to
+// C (layout CT) with the partial buffer used when splitting.
+void prof_mark(rsvdgb_handle* h, bool start, double bytes)
+{
+    if (!h || !h->prof.on) return;
+    PassProfile& p = h->prof;
+    const size_t idx = 2 * p.used + (start ? 0 : 1);
+    while (p.ev.size() <= idx) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            p.on = false;
+            return;
+        }
+        p.ev.push_back(e);
+    }
+    cudaEventRecord(p.ev[idx], h->stream);
+    if (!start) {
+        p.used += 1;
+        p.bytes += bytes;
+    }
+}
+
+// When `prof` is non-null the main product kernel is bracketed by an event
+// pair and counted as one pass over A of `pass_bytes` algorithmic bytes.
+void tall_gemm(cudaStream_t s, int sm, bool AT, bool BT, bool CT, const void* A, int64_t lda, int a_bf16,
+               const float* B, int64_t ldb, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float* part,
+               double* fro2, rsvdgb_handle* prof = nullptr, double pass_bytes = 0.0)
+{
+    GemmArgs a{};
+    a.A = A;
+    a.lda = lda;
+    a.a_bf16 = a_bf16;
+    a.B = B;
+    a.ldb = ldb;
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.fro2 = fro2;
+    const int64_t tiles = ceil_div(M, 64) * ceil_div(N, 64);
+    const int splits = splits_for(tiles, K, sm);
+    if (splits <= 1) {
+        a.C = C;
+        a.ldc = ldc;
+        a.splits = 1;
+        a.split_stride = 0;
+        prof_mark(prof, true, 0);
+        launch_simt_gemm(s, AT, BT, CT, a);
+        prof_mark(prof, false, pass_bytes);
+        return;
+    }
+    // partials in the same layout as C but packed with leading dimension ldc
+    const int64_t rows = CT ? N : M, cols = CT ? M : N;
+    a.C = part;
+    a.ldc = ldc;
+    a.splits = splits;
+    a.split_stride = rows * ldc;
+    prof_mark(prof, true, 0);
+    launch_simt_gemm(s, AT, BT, CT, a);
+    prof_mark(prof, false, pass_bytes);
+    launch_reduce_splits(s, part, splits, rows * ldc, rows, cols, ldc, C, nullptr, ldc);
+}
+
+double a_bytes(const Geom& g) { return (double)g.m * (double)g.n * (g.a_bf16 ? 2.0 : 4.0); }
+
+// Y (m x l, column-major ldm) = A_logical X (X: n x l column-major, ldn)
+void apply_A(rsvdgb_handle* h, const Geom& g, const float* Xt, float* Yt, float* part, double* fro2)
+{
+    // logical(i,k) = trans ? S[k*lda + i] : S[i*lda + k]
+    tall_gemm(h->stream, h->sm_count, g.trans, true, true, g.A, g.lda, g.a_bf16, Xt, g.ldn, Yt, g.ldm, g.m, g.l,
+              g.n, part, fro2, h, a_bytes(g));
+}
+
+// W (n x l, column-major ldn) = A_logical^T Y (Y: m x l column-major, ldm)
+void apply_At(rsvdgb_handle* h, const Geom& g, const float* Yt, float* Wt, float* part)
+{
+    // logical^T(i,k) = logical(k,i) = trans ? S[i*lda + k] : S[k*lda + i]
+    tall_gemm(h->stream, h->sm_count, !g.trans, true, true, g.A, g.lda, g.a_bf16, Yt, g.ldm, Wt, g.ldn, g.n, g.l,
+              g.m, part, nullptr, h, a_bytes(g));
+}
+
+// G (l x l, FP64) = X^T X for a column-major rows x l matrix.
+void gram(cudaStream_t s, int sm, const float* Xt, int64_t ld, int64_t rows, int l, float* part, double* G)
+{
+    GemmArgs a{};
+    a.A = Xt;
+    a.lda = ld;
+    a.B = Xt;
+    a.ldb = ld;
+    a.M = l;
+    a.N = l;
+    a.K = rows;
+    const int64_t tiles = ceil_div(l, 64) * ceil_div(l, 64);
+    const int splits = splits_for(tiles, rows, sm);
+    a.C = part;
+    a.ldc = l;
+    a.splits = splits;
+    a.split_stride = (int64_t)l * l;
+    launch_simt_gemm(s, false, true, false, a);
+    launch_reduce_splits(s, part, splits, (int64_t)l * l, l, l, l, nullptr, G, l);
+}
+
+// Zt (rows x l, column-major) = X T with X column-major (rows x l) and T an
+// l x l row-major matrix.
+void times_small(cudaStream_t s, int sm, const float* Xt, int64_t ld, int64_t rows, int l, const float* T, float* Zt,
+                 float* part)
+{
+    tall_gemm(s, sm, true, false, true, Xt, ld, 0, T, l, Zt, ld, rows, l, l, part, nullptr);
+}
+
+// CholeskyQR2 of a column-major rows x l matrix X (in Xt); the orthonormal
+// basis goes to Qt (may equal tmp? no: Qt != Xt != tmp).  R = R2 R1 is
+// written to Rout when non-null.
+void cholqr2(cudaStream_t s, int sm, Work& w, const float* Xt, int64_t ld, int64_t rows, int l, float* tmp, float* Qt,
+             float* Rout)
+{
+    gram(s, sm, Xt, ld, rows, l, w.part, w.G);
+    launch_chol_inv(s, w.G, l, 0.f, Rout ? w.R1 : nullptr, w.T1, w.status, w.breakdowns);
+    times_small(s, sm, Xt, ld, rows, l, w.T1, tmp, w.part);
+    gram(s, sm, tmp, ld, rows, l, w.part, w.G);
+    launch_chol_inv(s, w.G, l, 0.f, Rout ? w.R2 : nullptr, w.T2, w.status, w.breakdowns);
+    times_small(s, sm, tmp, ld, rows, l, w.T2, Qt, w.part);
+    if (Rout) launch_small_matmul(s, w.R2, w.R1, Rout, l);
+}
+
+struct Outputs {
+    float* d;
+    float* U;  // logical left vectors, row-major (ldU), nU columns
+    int64_t ldU;
+    int nU;
+    float* V;  // logical right vectors
+    int64_t ldV;
+    int nV;
+    float* Qrow;  // optional row-major Q (m x l) for rqb
+    int64_t ldq;
+    float* Brow;  // optional row-major B (l x n) for rqb
+    int64_t ldb;
+    rsvdgb_info* info;
+};
+
+// Algorithm rqb (+ rSVD when d != nullptr) on the logical matrix.
+int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t seed, const Outputs& o)
+{
+    const cudaStream_t s = h->stream;
+    const int sm = h->sm_count;
+    Carve probe(nullptr);
+    Work w{};
+    carve_work(probe, g, sm, w);
+    int rc = ensure_workspace(h, probe.off + 1024);
+    if (rc) return rc;
+    Carve c(h->ws);
+    carve_work(c, g, sm, w);
+    const int l = g.l;
+
+    launch_clear_scalars(s, w.status, w.breakdowns, w.fro2);
+    // step 2: Omega (n x l) into the panel
+    launch_omega(s, g.n, g.ldn, l, l, seed, sdist, w.Pt, g.ldn);
+    // step 3: Y = A Omega, with ||A||_F^2 accumulated on the way
+    apply_A(h, g, w.Pt, w.Yt, w.part, w.fro2);
+    gram(s, sm, w.Yt, g.ldm, g.m, l, w.part, w.G);
+    // step 4: subspace iterations
+    for (int it = 0; it < q; ++it) {
+        // Q = qr(Y): only the span is carried forward, so one Cholesky step
+        // (Q = Y T); A^T Q = (A^T Y) T.
+        launch_chol_inv(s, w.G, l, 0.f, nullptr, w.T, w.status, w.breakdowns);
+        apply_At(h, g, w.Yt, w.Wt, w.part);
+        times_small(s, sm, w.Wt, g.ldn, g.n, l, w.T, w.Zt, w.part);
+        // Q = qr(A^T Q): CholeskyQR2 on the n side, result in the panel
+        cholqr2(s, sm, w, w.Zt, g.ldn, g.n, l, w.Wt, w.Pt, nullptr);
+        // Y = A Q
+        apply_A(h, g, w.Pt, w.Yt, w.part, nullptr);
+        gram(s, sm, w.Yt, g.ldm, g.m, l, w.part, w.G);
+    }
+    // step 9: Q = qr(Y) with CholeskyQR2 (the first Gram is already in G):
+    // Y1 = Y T1, G = Y1^T Y1, Q = Y1 T2.  Q ends up in Yt.
+    launch_chol_inv(s, w.G, l, 0.f, nullptr, w.T1, w.status, w.breakdowns);
+    times_small(s, sm, w.Yt, g.ldm, g.m, l, w.T1, w.Qt, w.part);
+    gram(s, sm, w.Qt, g.ldm, g.m, l, w.part, w.G);
+    launch_chol_inv(s, w.G, l, 0.f, nullptr, w.T2, w.status, w.breakdowns);
+    times_small(s, sm, w.Qt, g.ldm, g.m, l, w.T2, w.Yt, w.part);
+    // step 10: B^T = A^T Q (n x l, column-major: row j of B is contiguous)
+    apply_At(h, g, w.Yt, w.Wt, w.part);
+    if (o.Qrow) launch_colmajor_to_rowmajor(s, w.Yt, g.ldm, g.m, l, o.Qrow, o.ldq);
+    if (o.Brow)
+        RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(o.Brow, o.ldb * sizeof(float), w.Wt, g.ldn * sizeof(float),
+                                          g.n * sizeof(float), l, cudaMemcpyDeviceToDevice, s));
+    if (o.d) {
+        // [Ut, S, V] = svd(B): B^T = Q_B R_B, then Jacobi on R_B^T.
+        cholqr2(s, sm, w, w.Wt, g.ldn, g.n, l, w.Zt, w.Pt, w.RB);
+        launch_small_transpose(s, w.RB, w.M, l);
+        launch_jacobi_svd(s, w.M, l, w.sigma, w.Ut, w.Jt, w.jwork);
+        // U = Q Ut (Eq. UQU) and V = Q_B J, truncated
+        if (o.nU > 0)
+            tall_gemm(s, sm, true, false, false, w.Yt, g.ldm, 0, w.Ut, l, o.U, o.ldU, g.m, o.nU, l, w.part,
+                      nullptr);
+        if (o.nV > 0)
+            tall_gemm(s, sm, true, false, false, w.Pt, g.ldn, 0, w.Jt, l, o.V, o.ldV, g.n, o.nV, l, w.part,
+                      nullptr);
+    } else {
+        // rqb only: singular values not requested; still report the QB error
+        // through a cheap Gram of B (sigma unused).
+    }
+    launch_finalize_info(s, o.d ? w.sigma : nullptr, o.d ? l : 0, k, o.d, w.fro2, w.status, w.breakdowns, q,
+                         l - k, o.info);
+    RSVDGB_CUDA_TRY(cudaGetLastError());
+    return RSVDGB_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+namespace {
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int check_handle(rsvdgb_handle* h)
+{
+    if (!h) return RSVDGB_ERR_INVALID_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return RSVDGB_ERR_CUDA;
+    return RSVDGB_OK;
+}
+
+// Validate a user matrix and build the m >= n geometry.
+int make_geom(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int layout, int k, int p, Geom& g)
+{
+    if (!A || m < 1 || n < 1) return RSVDGB_ERR_INVALID_ARG;
+    if (dtype != RSVDGB_F32 && dtype != RSVDGB_BF16) return RSVDGB_ERR_INVALID_ARG;
+    if (layout != RSVDGB_ROW_MAJOR && layout != RSVDGB_COL_MAJOR) return RSVDGB_ERR_INVALID_ARG;
+    if (!aligned(A, dtype == RSVDGB_F32 ? 4 : 2)) return RSVDGB_ERR_INVALID_ARG;
+    const int64_t inner = layout == RSVDGB_ROW_MAJOR ? n : m;
+    if (lda < inner) return RSVDGB_ERR_INVALID_ARG;
+    const int64_t mn = std::min(m, n);
+    if (k < 1 || k >= mn || p < 0) return RSVDGB_ERR_INVALID_ARG;
+    g.A = A;
+    g.lda = lda;
+    g.a_bf16 = dtype == RSVDGB_BF16;
+    g.m = std::max(m, n);
+    g.n = mn;
+    g.swap_uv = m < n;
+    // stored S is A (row-major) or A^T (column-major); the logical matrix is
+    // A when m >= n and A^T otherwise.
+    const bool logical_is_A = m >= n;
+    const bool S_is_A = layout == RSVDGB_ROW_MAJOR;
+    g.trans = (logical_is_A != S_is_A);
+    g.l = (int)std::min<int64_t>((int64_t)k + p, mn);
+    g.ldm = round_up(g.m, 32);
+    g.ldn = round_up(g.n, 32);
+    if (g.l > kMaxL) return RSVDGB_ERR_UNSUPPORTED;
+    return RSVDGB_OK;
+}
+
+const char* kStatusNames[] = {"RSVDGB_OK",           "RSVDGB_ERR_INVALID_ARG", "RSVDGB_ERR_NOMEM",
+                              "RSVDGB_ERR_CUDA",     "RSVDGB_ERR_BREAKDOWN",   "RSVDGB_ERR_NONFINITE",
+                              "RSVDGB_ERR_TIMEOUT",  "RSVDGB_ERR_UNSUPPORTED"};
+
+}  // namespace
+
+extern "C" {
+
+void rsvdgb_default_opts(rsvdgb_opts* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->p = 10;
+    o->q = 2;
+    o->sdist = RSVDGB_SDIST_NORMAL;
+    o->prec = RSVDGB_PREC_FP32;
+    o->seed = 0;
+    o->layout = RSVDGB_ROW_MAJOR;
+    o->engine = RSVDGB_ENGINE_AUTO;
+}
+
+const char* rsvdgb_status_string(int status)
+{
+    if (status < 0 || status > RSVDGB_ERR_UNSUPPORTED) return "RSVDGB_UNKNOWN_STATUS";
+    return kStatusNames[status];
+}
+
+int rsvdgb_sketch_width(int64_t m, int64_t n, int k, int p)
+{
+    const int64_t mn = std::min(m, n);
+    return (int)std::min<int64_t>((int64_t)k + p, mn);
+}
+
+int rsvdgb_create(rsvdgb_handle** h, int device, void* cuda_stream)
+{
+    if (!h) return RSVDGB_ERR_INVALID_ARG;
+    *h = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return RSVDGB_ERR_CUDA;
+    }
+    if (device < 0 || device >= count) return RSVDGB_ERR_INVALID_ARG;
+    RSVDGB_CUDA_TRY(cudaSetDevice(device));
+    rsvdgb_handle* hh = new (std::nothrow) rsvdgb_handle();
+    if (!hh) return RSVDGB_ERR_NOMEM;
+    hh->device = device;
+    hh->stream = (cudaStream_t)cuda_stream;
+    cudaDeviceGetAttribute(&hh->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (init_small_kernels() != RSVDGB_OK) {
+        delete hh;
+        return RSVDGB_ERR_CUDA;
+    }
+    *h = hh;
+    return RSVDGB_OK;
+}
+
+int rsvdgb_destroy(rsvdgb_handle* h)
+{
+    if (!h) return RSVDGB_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    if (h->ws) cudaFree(h->ws);
+    if (h->host_stage) cudaFree(h->host_stage);
+    for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
+    delete h;
+    return RSVDGB_OK;
+}
+
+int rsvdgb_set_stream(rsvdgb_handle* h, void* cuda_stream)
+{
+    if (!h) return RSVDGB_ERR_INVALID_ARG;
+    h->stream = (cudaStream_t)cuda_stream;
+    return RSVDGB_OK;
+}
+
+int rsvdgb_rsvd(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k, int nu, int nv,
+                const rsvdgb_opts* opts, float* d, float* U, int64_t ldu, float* V, int64_t ldv, rsvdgb_info* info)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    rsvdgb_opts o;
+    if (opts)
+        o = *opts;
+    else
+        rsvdgb_default_opts(&o);
+    if (o.q < 0 || o.sdist < 0 || o.sdist > 2) return RSVDGB_ERR_INVALID_ARG;
+    Geom g{};
+    rc = make_geom(A, m, n, lda, dtype, o.layout, k, o.p, g);
+    if (rc) return rc;
+    if (nu < 0) nu = k;
+    if (nv < 0) nv = k;
+    if (nu > k || nv > k || !d) return RSVDGB_ERR_INVALID_ARG;
+    if (nu > 0 && (!U || ldu < nu)) return RSVDGB_ERR_INVALID_ARG;
+    if (nv > 0 && (!V || ldv < nv)) return RSVDGB_ERR_INVALID_ARG;
+    if (o.prec != RSVDGB_PREC_FP32) return RSVDGB_ERR_UNSUPPORTED;
+    if (o.engine == RSVDGB_ENGINE_TC) return RSVDGB_ERR_UNSUPPORTED;
+    Outputs out{};
+    out.d = d;
+    out.info = info;
+    if (!g.swap_uv) {
+        out.U = U; out.ldU = ldu; out.nU = nu;
+        out.V = V; out.ldV = ldv; out.nV = nv;
+    } else {
+        out.U = V; out.ldU = ldv; out.nU = nv;
+        out.V = U; out.ldV = ldu; out.nV = nu;
+    }
+    return run_fp32(h, g, k, o.q, o.sdist, o.seed, out);
+}
+
+int rsvdgb_rqb(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k,
+               const rsvdgb_opts* opts, float* Q, int64_t ldq, float* B, int64_t ldb, rsvdgb_info* info)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    rsvdgb_opts o;
+    if (opts)
+        o = *opts;
+    else
+        rsvdgb_default_opts(&o);
+    if (o.q < 0 || o.sdist < 0 || o.sdist > 2) return RSVDGB_ERR_INVALID_ARG;
+    if (m < n || o.layout != RSVDGB_ROW_MAJOR) return RSVDGB_ERR_INVALID_ARG;
+    Geom g{};
+    rc = make_geom(A, m, n, lda, dtype, o.layout, k, o.p, g);
+    if (rc) return rc;
+    if (!Q || !B || ldq < g.l || ldb < n) return RSVDGB_ERR_INVALID_ARG;
+    if (o.prec != RSVDGB_PREC_FP32) return RSVDGB_ERR_UNSUPPORTED;
+    Outputs out{};
+    out.Qrow = Q;
+    out.ldq = ldq;
+    out.Brow = B;
+    out.ldb = ldb;
+    out.info = info;
+    return run_fp32(h, g, k, o.q, o.sdist, o.seed, out);
+}
+
+int rsvdgb_rsvd_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k, int nu,
+                     int nv, const rsvdgb_opts* opts, float* d, float* U, int64_t ldu, float* V, int64_t ldv,
+                     rsvdgb_info* info)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!A || !d || m < 1 || n < 1) return RSVDGB_ERR_INVALID_ARG;
+    rsvdgb_opts o;
+    if (opts)
+        o = *opts;
+    else
+        rsvdgb_default_opts(&o);
+    if (nu < 0) nu = k;
+    if (nv < 0) nv = k;
+    if (nu > k || nv > k || k < 1) return RSVDGB_ERR_INVALID_ARG;
+    const size_t esz = dtype == RSVDGB_BF16 ? 2 : 4;
+    const int64_t rows_s = o.layout == RSVDGB_ROW_MAJOR ? m : n;
+    const int64_t cols_s = o.layout == RSVDGB_ROW_MAJOR ? n : m;
+    if (lda < cols_s) return RSVDGB_ERR_INVALID_ARG;
+    // device staging: A (packed), d, U, V, info
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (size_t)round_up((int64_t)off, 256);
+        size_t at = off;
+        off += bytes;
+        return at;
+    };
+    const size_t oA = take((size_t)rows_s * cols_s * esz);
+    const size_t od = take((size_t)k * sizeof(float));
+    const size_t oU = take((size_t)m * std::max(nu, 1) * sizeof(float));
+    const size_t oV = take((size_t)n * std::max(nv, 1) * sizeof(float));
+    const size_t oI = take(sizeof(rsvdgb_info));
+    if (off > h->host_stage_bytes) {
+        if (h->host_stage) {
+            cudaStreamSynchronize(h->stream);
+            cudaFree(h->host_stage);
+            h->host_stage = nullptr;
+            h->host_stage_bytes = 0;
+        }
+        if (cudaMalloc(&h->host_stage, off) != cudaSuccess) {
+            cudaGetLastError();
+            return RSVDGB_ERR_NOMEM;
+        }
+        h->host_stage_bytes = off;
+    }
+    char* base = (char*)h->host_stage;
+    RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(base + oA, cols_s * esz, A, lda * esz, cols_s * esz, rows_s,
+                                      cudaMemcpyHostToDevice, h->stream));
+    rc = rsvdgb_rsvd(h, base + oA, m, n, cols_s, dtype, k, nu, nv, &o, (float*)(base + od),
+                     nu > 0 ? (float*)(base + oU) : nullptr, std::max(nu, 1), nv > 0 ? (float*)(base + oV) : nullptr,
+                     std::max(nv, 1), (rsvdgb_info*)(base + oI));
+    if (rc) return rc;
+    RSVDGB_CUDA_TRY(cudaMemcpyAsync(d, base + od, (size_t)k * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (nu > 0 && U)
+        RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(U, ldu * sizeof(float), base + oU, nu * sizeof(float), nu * sizeof(float), m,
+                                          cudaMemcpyDeviceToHost, h->stream));
+    if (nv > 0 && V)
+        RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(V, ldv * sizeof(float), base + oV, nv * sizeof(float), nv * sizeof(float), n,
+                                          cudaMemcpyDeviceToHost, h->stream));
+    rsvdgb_info hinfo;
+    RSVDGB_CUDA_TRY(cudaMemcpyAsync(&hinfo, base + oI, sizeof(hinfo), cudaMemcpyDeviceToHost, h->stream));
+    RSVDGB_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (info) *info = hinfo;
+    return hinfo.status;
+}
+
+int rsvdgb_omega(rsvdgb_handle* h, int64_t rows, int l, uint64_t seed, int sdist, float* out, int64_t ld)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (rows < 1 || l < 1 || !out || ld < l || sdist < 0 || sdist > 2 || !aligned(out, 4))
+        return RSVDGB_ERR_INVALID_ARG;
+    launch_omega_rowmajor(h->stream, rows, l, seed, sdist, out, ld);
+    RSVDGB_CUDA_TRY(cudaGetLastError());
+    return RSVDGB_OK;
+}
+
+static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const float* X,
+                       int64_t ldx, int l, float* Y, int64_t ldy, int engine, int prec, bool transpose)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!A || !X || !Y || m < 1 || n < 1 || l < 1 || lda < n) return RSVDGB_ERR_INVALID_ARG;
+    if (dtype != RSVDGB_F32 && dtype != RSVDGB_BF16) return RSVDGB_ERR_INVALID_ARG;
+    if (ldx < l || ldy < l) return RSVDGB_ERR_INVALID_ARG;
+    if (prec != RSVDGB_PREC_FP32 || engine == RSVDGB_ENGINE_TC) return RSVDGB_ERR_UNSUPPORTED;
+    // partial buffer for the K split
+    const int64_t M = transpose ? n : m, K = transpose ? m : n;
+    const int64_t tiles = ceil_div(M, 64) * ceil_div(l, 64);
+    const int splits = splits_for(tiles, K, h->sm_count);
+    rc = ensure_workspace(h, (size_t)splits * M * ldy * sizeof(float) + 1024);
+    if (rc) return rc;
+    tall_gemm(h->stream, h->sm_count, transpose, false, false, A, lda, dtype == RSVDGB_BF16, X, ldx, Y, ldy, M, l, K,
+              (float*)h->ws, nullptr);
+    RSVDGB_CUDA_TRY(cudaGetLastError());
+    return RSVDGB_OK;
+}
+
+int rsvdgb_pass_ax(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const float* X,
+                   int64_t ldx, int l, float* Y, int64_t ldy, int engine, int prec)
+{
+    return pass_common(h, A, m, n, lda, dtype, X, ldx, l, Y, ldy, engine, prec, false);
+}
+
+int rsvdgb_pass_atx(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const float* X,
+                    int64_t ldx, int l, float* Z, int64_t ldz, int engine, int prec)
+{
+    return pass_common(h, A, m, n, lda, dtype, X, ldx, l, Z, ldz, engine, prec, true);
+}
+
+int rsvdgb_profile_passes(rsvdgb_handle* h, int enable)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    cudaStreamSynchronize(h->stream);
+    h->prof.on = enable != 0;
+    h->prof.used = 0;
+    h->prof.bytes = 0.0;
+    return RSVDGB_OK;
+}
+
+int rsvdgb_profile_read(rsvdgb_handle* h, double* pass_ms, int64_t* pass_launches, double* pass_bytes)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    RSVDGB_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    double total = 0.0;
+    for (size_t i = 0; i < h->prof.used; ++i) {
+        float ms = 0.f;
+        RSVDGB_CUDA_TRY(cudaEventElapsedTime(&ms, h->prof.ev[2 * i], h->prof.ev[2 * i + 1]));
+        total += ms;
+    }
+    if (pass_ms) *pass_ms = total;
+    if (pass_launches) *pass_launches = (int64_t)h->prof.used;
+    if (pass_bytes) *pass_bytes = h->prof.bytes;
+    return RSVDGB_OK;
+}
+
+int64_t rsvdgb_kernel_launches(void) { return launches_so_far(); }
+
+}  // extern "C"

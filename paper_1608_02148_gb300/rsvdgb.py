@@ -1,0 +1,293 @@
+"""Python binding of librsvdgb (ctypes): argument marshalling only.
+
+Every function here forwards torch tensors' device pointers and sizes to the
+C entry point of the same name declared in include/rsvdgb.h; all arithmetic
+runs in the library's CUDA kernels.  PyTorch supplies device memory and the
+current CUDA stream.  If the shared library has not been built, loading fails
+with an error -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "_build" / "librsvdgb.so"
+
+RSVDGB_OK = 0
+STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_NOMEM", 3: "ERR_CUDA", 4: "ERR_BREAKDOWN", 5: "ERR_NONFINITE",
+          6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
+F32, BF16 = 0, 1
+SDIST = {"normal": 0, "unif": 1, "rademacher": 2}
+PREC = {"fp32": 0, "bf16_sketch": 1}
+ENGINE = {"auto": 0, "simt": 1, "tc": 2}
+LAYOUT = {"row": 0, "col": 1}
+
+# Entry points declared in include/rsvdgb.h (checked by the ABI test).
+EXPORTS = ["rsvdgb_create", "rsvdgb_destroy", "rsvdgb_set_stream", "rsvdgb_default_opts", "rsvdgb_status_string",
+           "rsvdgb_sketch_width", "rsvdgb_rsvd", "rsvdgb_rsvd_host", "rsvdgb_rqb", "rsvdgb_omega",
+           "rsvdgb_pass_ax", "rsvdgb_pass_atx", "rsvdgb_profile_passes", "rsvdgb_profile_read",
+           "rsvdgb_kernel_launches"]
+
+
+class RsvdgbOpts(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int32), ("q", ctypes.c_int32), ("sdist", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("layout", ctypes.c_int32), ("engine", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class RsvdgbInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("q_used", ctypes.c_int32), ("p_used", ctypes.c_int32),
+                ("l", ctypes.c_int32), ("fro2_A", ctypes.c_double), ("fro2_B", ctypes.c_double),
+                ("err2_QB", ctypes.c_double), ("err2_k", ctypes.c_double), ("breakdowns", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+INFO_BYTES = ctypes.sizeof(RsvdgbInfo)
+
+_lib = None
+
+
+class RsvdgbError(RuntimeError):
+    def __init__(self, where, status):
+        super().__init__(f"{where} failed: {STATUS.get(status, status)}")
+        self.status = status
+
+
+def load(path: Path | str | None = None):
+    """Load librsvdgb.so (build it first with paper_1608_02148_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        raise RuntimeError(f"{p} is missing: build the CUDA library first (paper_1608_02148_gb300.build.build())")
+    lib = ctypes.CDLL(str(p))
+    P, I, I64, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
+    lib.rsvdgb_create.argtypes = [ctypes.POINTER(P), I, P]
+    lib.rsvdgb_destroy.argtypes = [P]
+    lib.rsvdgb_set_stream.argtypes = [P, P]
+    lib.rsvdgb_default_opts.argtypes = [ctypes.POINTER(RsvdgbOpts)]
+    lib.rsvdgb_default_opts.restype = None
+    lib.rsvdgb_status_string.argtypes = [I]
+    lib.rsvdgb_status_string.restype = ctypes.c_char_p
+    lib.rsvdgb_sketch_width.argtypes = [I64, I64, I, I]
+    sig = [P, P, I64, I64, I64, I, I, I, I, ctypes.POINTER(RsvdgbOpts), P, P, I64, P, I64, P]
+    lib.rsvdgb_rsvd.argtypes = sig
+    lib.rsvdgb_rsvd_host.argtypes = sig
+    lib.rsvdgb_rqb.argtypes = [P, P, I64, I64, I64, I, I, ctypes.POINTER(RsvdgbOpts), P, I64, P, I64, P]
+    lib.rsvdgb_omega.argtypes = [P, I64, I, U64, I, P, I64]
+    lib.rsvdgb_pass_ax.argtypes = [P, P, I64, I64, I64, I, P, I64, I, P, I64, I, I]
+    lib.rsvdgb_pass_atx.argtypes = [P, P, I64, I64, I64, I, P, I64, I, P, I64, I, I]
+    lib.rsvdgb_profile_passes.argtypes = [P, I]
+    lib.rsvdgb_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64),
+                                        ctypes.POINTER(ctypes.c_double)]
+    lib.rsvdgb_kernel_launches.argtypes = []
+    lib.rsvdgb_kernel_launches.restype = I64
+    _lib = lib
+    return lib
+
+
+def _check(where, rc):
+    if rc != RSVDGB_OK:
+        raise RsvdgbError(where, rc)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t):
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.bfloat16:
+        return BF16
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _rowmajor_ld(t):
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("expected a 2-D tensor with unit column stride (row-major)")
+    return t.stride(0)
+
+
+def make_opts(p=10, q=2, sdist="normal", prec="fp32", seed=0, layout="row", engine="auto") -> RsvdgbOpts:
+    o = RsvdgbOpts()
+    load().rsvdgb_default_opts(ctypes.byref(o))
+    o.p, o.q, o.sdist, o.prec = p, q, SDIST[sdist], PREC[prec]
+    o.seed, o.layout, o.engine = seed, LAYOUT[layout], ENGINE[engine]
+    return o
+
+
+def rsvdgb_default_opts() -> RsvdgbOpts:
+    o = RsvdgbOpts()
+    load().rsvdgb_default_opts(ctypes.byref(o))
+    return o
+
+
+def rsvdgb_status_string(status: int) -> str:
+    return load().rsvdgb_status_string(status).decode()
+
+
+def rsvdgb_sketch_width(m, n, k, p) -> int:
+    return load().rsvdgb_sketch_width(m, n, k, p)
+
+
+class Handle:
+    """Owns an rsvdgb_handle bound to a device and (by default) torch's
+    current stream on that device."""
+
+    def __init__(self, device: int = 0, stream=None):
+        torch = _torch()
+        lib = load()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self._stream = stream
+        h = ctypes.c_void_p()
+        _check("rsvdgb_create", lib.rsvdgb_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream)))
+        self.ptr = h
+
+    def close(self):
+        if self.ptr:
+            load().rsvdgb_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._stream = stream
+        _check("rsvdgb_set_stream", load().rsvdgb_set_stream(self.ptr, ctypes.c_void_p(stream.cuda_stream)))
+
+
+def _info_from(buf) -> RsvdgbInfo:
+    raw = bytes(buf.cpu().numpy().tobytes())
+    return RsvdgbInfo.from_buffer_copy(raw)
+
+
+def rsvdgb_rsvd(h: Handle, A, k, nu=-1, nv=-1, opts: RsvdgbOpts | None = None, out=None, sync_info=True):
+    """rsvd(A, k, nu, nv, p, q, sdist) on a device tensor A (row-major unless
+    opts.layout = col, where A is the column-major matrix given as its
+    row-major transpose view).  Returns (d, U, V, info)."""
+    torch = _torch()
+    lib = load()
+    opts = opts or make_opts()
+    if opts.layout == LAYOUT["row"]:
+        m, n = A.shape
+        lda = _rowmajor_ld(A)
+    else:  # column-major m x n matrix stored as the row-major n x m tensor A
+        n, m = A.shape
+        lda = _rowmajor_ld(A)
+    nu_ = k if nu < 0 else nu
+    nv_ = k if nv < 0 else nv
+    dev = A.device
+    if out is None:
+        d = torch.empty(k, dtype=torch.float32, device=dev)
+        U = torch.empty(m, max(nu_, 1), dtype=torch.float32, device=dev)
+        V = torch.empty(n, max(nv_, 1), dtype=torch.float32, device=dev)
+        info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=dev)
+    else:
+        d, U, V, info = out
+    rc = lib.rsvdgb_rsvd(h.ptr, A.data_ptr(), m, n, lda, _dtype_code(A), k, nu_, nv_, ctypes.byref(opts),
+                         d.data_ptr(), U.data_ptr() if nu_ > 0 else None, U.stride(0),
+                         V.data_ptr() if nv_ > 0 else None, V.stride(0), info.data_ptr())
+    _check("rsvdgb_rsvd", rc)
+    if not sync_info:
+        return d, U[:, :nu_], V[:, :nv_], info
+    return d, U[:, :nu_], V[:, :nv_], _info_from(info)
+
+
+def rsvdgb_rsvd_host(h: Handle, A_host, k, nu=-1, nv=-1, opts: RsvdgbOpts | None = None, out=None):
+    """Host-buffer variant: A_host, and the outputs, are CPU tensors (pin
+    them for full copy bandwidth).  Synchronous."""
+    torch = _torch()
+    lib = load()
+    opts = opts or make_opts()
+    m, n = A_host.shape if opts.layout == LAYOUT["row"] else A_host.shape[::-1]
+    lda = _rowmajor_ld(A_host)
+    nu_ = k if nu < 0 else nu
+    nv_ = k if nv < 0 else nv
+    if out is None:
+        pin = A_host.is_pinned()
+        d = torch.empty(k, dtype=torch.float32, pin_memory=pin)
+        U = torch.empty(m, max(nu_, 1), dtype=torch.float32, pin_memory=pin)
+        V = torch.empty(n, max(nv_, 1), dtype=torch.float32, pin_memory=pin)
+    else:
+        d, U, V = out
+    info = RsvdgbInfo()
+    rc = lib.rsvdgb_rsvd_host(h.ptr, A_host.data_ptr(), m, n, lda, _dtype_code(A_host), k, nu_, nv_,
+                              ctypes.byref(opts), d.data_ptr(), U.data_ptr() if nu_ > 0 else None, U.stride(0),
+                              V.data_ptr() if nv_ > 0 else None, V.stride(0), ctypes.byref(info))
+    _check("rsvdgb_rsvd_host", rc)
+    return d, U[:, :nu_], V[:, :nv_], info
+
+
+def rsvdgb_rqb(h: Handle, A, k, opts: RsvdgbOpts | None = None):
+    """Algorithm rqb: returns Q (m x l), B (l x n), info."""
+    torch = _torch()
+    lib = load()
+    opts = opts or make_opts()
+    m, n = A.shape
+    l = rsvdgb_sketch_width(m, n, k, opts.p)
+    Q = torch.empty(m, l, dtype=torch.float32, device=A.device)
+    B = torch.empty(l, n, dtype=torch.float32, device=A.device)
+    info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=A.device)
+    rc = lib.rsvdgb_rqb(h.ptr, A.data_ptr(), m, n, _rowmajor_ld(A), _dtype_code(A), k, ctypes.byref(opts),
+                        Q.data_ptr(), Q.stride(0), B.data_ptr(), B.stride(0), info.data_ptr())
+    _check("rsvdgb_rqb", rc)
+    return Q, B, _info_from(info)
+
+
+def rsvdgb_omega(h: Handle, rows, l, seed=0, sdist="normal", device="cuda"):
+    torch = _torch()
+    out = torch.empty(rows, l, dtype=torch.float32, device=device)
+    _check("rsvdgb_omega", load().rsvdgb_omega(h.ptr, rows, l, seed, SDIST[sdist], out.data_ptr(), out.stride(0)))
+    return out
+
+
+def _pass(fn, name, h, A, X, engine, prec, out_rows):
+    torch = _torch()
+    m, n = A.shape
+    l = X.shape[1]
+    Y = torch.empty(out_rows, l, dtype=torch.float32, device=A.device)
+    rc = fn(h.ptr, A.data_ptr(), m, n, _rowmajor_ld(A), _dtype_code(A), X.data_ptr(), _rowmajor_ld(X), l,
+            Y.data_ptr(), Y.stride(0), ENGINE[engine], PREC[prec])
+    _check(name, rc)
+    return Y
+
+
+def rsvdgb_pass_ax(h: Handle, A, X, engine="auto", prec="fp32"):
+    """Y = A X (X: n x l float32 row-major)."""
+    return _pass(load().rsvdgb_pass_ax, "rsvdgb_pass_ax", h, A, X, engine, prec, A.shape[0])
+
+
+def rsvdgb_pass_atx(h: Handle, A, X, engine="auto", prec="fp32"):
+    """Z = A^T X (X: m x l float32 row-major)."""
+    return _pass(load().rsvdgb_pass_atx, "rsvdgb_pass_atx", h, A, X, engine, prec, A.shape[1])
+
+
+def rsvdgb_profile_passes(h: Handle, enable: bool = True):
+    _check("rsvdgb_profile_passes", load().rsvdgb_profile_passes(h.ptr, 1 if enable else 0))
+
+
+def rsvdgb_profile_read(h: Handle):
+    """(summed pass-kernel time in ms, launches, algorithmic bytes of A)."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    b = ctypes.c_double()
+    _check("rsvdgb_profile_read", load().rsvdgb_profile_read(h.ptr, ctypes.byref(ms), ctypes.byref(n),
+                                                             ctypes.byref(b)))
+    return ms.value, n.value, b.value
+
+
+def rsvdgb_kernel_launches() -> int:
+    return int(load().rsvdgb_kernel_launches())

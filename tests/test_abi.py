@@ -1,0 +1,68 @@
+"""The C-ABI library builds, loads without a GPU, and exports every entry
+point that include/rsvdgb.h declares.  Only host-only calls are made here."""
+import ctypes
+import json
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rsvdgb.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rsvdgb_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1608_02148_gb300 import build, rsvdgb
+    build.build()
+    return rsvdgb.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_the_declared_entry_points(lib):
+    from paper_1608_02148_gb300 import rsvdgb
+    assert sorted(rsvdgb.EXPORTS) == sorted(set(rsvdgb.EXPORTS))
+    assert set(rsvdgb.EXPORTS) <= set(declared_functions())
+    assert set(declared_functions()) <= set(rsvdgb.EXPORTS)
+
+
+def test_struct_sizes_match_header(lib):
+    from paper_1608_02148_gb300 import rsvdgb
+    assert ctypes.sizeof(rsvdgb.RsvdgbOpts) == 56
+    assert ctypes.sizeof(rsvdgb.RsvdgbInfo) == 80
+
+
+def test_default_opts_are_the_papers(lib):
+    """p = 10, q = 2, sdist = normal (Sec. 3.6 signature; Sec. 3.3 remark)."""
+    from paper_1608_02148_gb300 import rsvdgb
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))["rsvd_defaults"]
+    o = rsvdgb.rsvdgb_default_opts()
+    assert o.p == gold["p"] and o.q == gold["q"]
+    assert o.sdist == rsvdgb.SDIST[gold["sdist"]]
+    assert o.prec == 0 and o.layout == 0 and o.seed == 0
+
+
+def test_status_strings_and_sketch_width(lib):
+    from paper_1608_02148_gb300 import rsvdgb
+    assert rsvdgb.rsvdgb_status_string(0) == "RSVDGB_OK"
+    assert rsvdgb.rsvdgb_status_string(4) == "RSVDGB_ERR_BREAKDOWN"
+    assert rsvdgb.rsvdgb_status_string(99) == "RSVDGB_UNKNOWN_STATUS"
+    assert rsvdgb.rsvdgb_sketch_width(2000, 1000, 20, 10) == 30
+    assert rsvdgb.rsvdgb_sketch_width(100, 40, 35, 10) == 40
+
+
+def test_null_handle_is_rejected_without_gpu(lib):
+    assert lib.rsvdgb_destroy(None) == 1
+    assert lib.rsvdgb_rsvd(None, None, 10, 10, 10, 0, 2, 2, 2, None, None, None, 0, None, 0, None) == 1
