@@ -88,6 +88,8 @@ void launch_small_matmul(cudaStream_t s, const float* A, const float* B, float* 
 //   Jt (l x l row-major, the accumulated rotations, column c = right vector).
 // Also writes the first k values to d (float) and sum-of-squares diagnostics.
 void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, float* Ut, float* Jt, float* work);
+// FP64 -> FP32 copy of an l x l row-major matrix, optionally transposed.
+void launch_small_d2f(cudaStream_t s, const double* in, float* out, int l, bool transpose);
 // Transpose an l x l row-major matrix: out = in^T.
 void launch_small_transpose(cudaStream_t s, const float* in, float* out, int l);
 // d[0..k) = sigma[0..k); info fields from fro2_A and sigma.

@@ -245,13 +245,15 @@ void apply_At(rsvdgb_handle* h, const Geom& g, const float* Yt, float* Wt, float
               g.m, part, nullptr, h, a_bytes(g));
 }
 
-// G (l x l, FP64) = X^T X for a column-major rows x l matrix.
-void gram(cudaStream_t s, int sm, const float* Xt, int64_t ld, int64_t rows, int l, float* part, double* G)
+// G (l x l, FP64) = X^T Z for column-major rows x l matrices X and Z
+// (Z = X gives the Gram matrix).
+void cross_gram(cudaStream_t s, int sm, const float* Xt, const float* Zt, int64_t ld, int64_t rows, int l,
+                float* part, double* G)
 {
     GemmArgs a{};
     a.A = Xt;
     a.lda = ld;
-    a.B = Xt;
+    a.B = Zt;
     a.ldb = ld;
     a.M = l;
     a.N = l;
@@ -266,6 +268,11 @@ void gram(cudaStream_t s, int sm, const float* Xt, int64_t ld, int64_t rows, int
     launch_reduce_splits(s, part, splits, (int64_t)l * l, l, l, l, nullptr, G, l);
 }
 
+void gram(cudaStream_t s, int sm, const float* Xt, int64_t ld, int64_t rows, int l, float* part, double* G)
+{
+    cross_gram(s, sm, Xt, Xt, ld, rows, l, part, G);
+}
+
 // Zt (rows x l, column-major) = X T with X column-major (rows x l) and T an
 // l x l row-major matrix.
 void times_small(cudaStream_t s, int sm, const float* Xt, int64_t ld, int64_t rows, int l, const float* T, float* Zt,
@@ -274,19 +281,17 @@ void times_small(cudaStream_t s, int sm, const float* Xt, int64_t ld, int64_t ro
     tall_gemm(s, sm, true, false, true, Xt, ld, 0, T, l, Zt, ld, rows, l, l, part, nullptr);
 }
 
-// CholeskyQR2 of a column-major rows x l matrix X (in Xt); the orthonormal
-// basis goes to Qt (may equal tmp? no: Qt != Xt != tmp).  R = R2 R1 is
-// written to Rout when non-null.
-void cholqr2(cudaStream_t s, int sm, Work& w, const float* Xt, int64_t ld, int64_t rows, int l, float* tmp, float* Qt,
-             float* Rout)
+// CholeskyQR2 of a column-major rows x l matrix X (in Xt): Q1 = X R1^{-1},
+// Q = Q1 R2^{-1}, the orthonormal basis written to Qt (tmp holds Q1; Xt, tmp
+// and Qt are distinct).
+void cholqr2(cudaStream_t s, int sm, Work& w, const float* Xt, int64_t ld, int64_t rows, int l, float* tmp, float* Qt)
 {
     gram(s, sm, Xt, ld, rows, l, w.part, w.G);
-    launch_chol_inv(s, w.G, l, 0.f, Rout ? w.R1 : nullptr, w.T1, w.status, w.breakdowns);
+    launch_chol_inv(s, w.G, l, 0.f, nullptr, w.T1, w.status, w.breakdowns);
     times_small(s, sm, Xt, ld, rows, l, w.T1, tmp, w.part);
     gram(s, sm, tmp, ld, rows, l, w.part, w.G);
-    launch_chol_inv(s, w.G, l, 0.f, Rout ? w.R2 : nullptr, w.T2, w.status, w.breakdowns);
+    launch_chol_inv(s, w.G, l, 0.f, nullptr, w.T2, w.status, w.breakdowns);
     times_small(s, sm, tmp, ld, rows, l, w.T2, Qt, w.part);
-    if (Rout) launch_small_matmul(s, w.R2, w.R1, Rout, l);
 }
 
 struct Outputs {
@@ -332,7 +337,7 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
         apply_At(h, g, w.Yt, w.Wt, w.part);
         times_small(s, sm, w.Wt, g.ldn, g.n, l, w.T, w.Zt, w.part);
         // Q = qr(A^T Q): CholeskyQR2 on the n side, result in the panel
-        cholqr2(s, sm, w, w.Zt, g.ldn, g.n, l, w.Wt, w.Pt, nullptr);
+        cholqr2(s, sm, w, w.Zt, g.ldn, g.n, l, w.Wt, w.Pt);
         // Y = A Q
         apply_A(h, g, w.Pt, w.Yt, w.part, nullptr);
         gram(s, sm, w.Yt, g.ldm, g.m, l, w.part, w.G);
@@ -351,9 +356,13 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
         RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(o.Brow, o.ldb * sizeof(float), w.Wt, g.ldn * sizeof(float),
                                           g.n * sizeof(float), l, cudaMemcpyDeviceToDevice, s));
     if (o.d) {
-        // [Ut, S, V] = svd(B): B^T = Q_B R_B, then Jacobi on R_B^T.
-        cholqr2(s, sm, w, w.Wt, g.ldn, g.n, l, w.Zt, w.Pt, w.RB);
-        launch_small_transpose(s, w.RB, w.M, l);
+        // [Ut, S, V] = svd(B): B^T = Q_B R_B, then Jacobi on R_B^T.  R_B is
+        // formed as Q_B^T B^T from the computed Q_B, so that B^T = Q_B R_B
+        // holds to FP32 rounding whatever the error of the triangular
+        // factors (R2 R1 would carry the inverse's error l u kappa).
+        cholqr2(s, sm, w, w.Wt, g.ldn, g.n, l, w.Zt, w.Pt);
+        cross_gram(s, sm, w.Pt, w.Wt, g.ldn, g.n, l, w.part, w.G);
+        launch_small_d2f(s, w.G, w.M, l, true);
         launch_jacobi_svd(s, w.M, l, w.sigma, w.Ut, w.Jt, w.jwork);
         // U = Q Ut (Eq. UQU) and V = Q_B J, truncated
         if (o.nU > 0)

@@ -139,6 +139,14 @@ __global__ void small_matmul_kernel(const float* __restrict__ A, const float* __
     C[i * l + j] = acc;
 }
 
+__global__ void small_d2f_kernel(const double* __restrict__ in, float* __restrict__ out, int l, int transpose)
+{
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= l || j >= l) return;
+    out[transpose ? j * l + i : i * l + j] = (float)in[i * l + j];
+}
+
 __global__ void small_transpose_kernel(const float* __restrict__ in, float* __restrict__ out, int l)
 {
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
@@ -210,7 +218,7 @@ __global__ void __launch_bounds__(kSmallThreads)
                 if (ga != 0.f && fabsf(ga) > tol * sqrtf(al * be)) {
                     const float zeta = (be - al) / (2.f * ga);
                     const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-                    const float c = rsqrtf(1.f + tt * tt);
+                    const float c = 1.0f / sqrtf(1.f + tt * tt);
                     const float s = c * tt;
                     for (int i = lane; i < L; i += 32) {
                         const float x = ma[i], y = mb[i];
@@ -232,12 +240,25 @@ __global__ void __launch_bounds__(kSmallThreads)
         if (!rotated) break;
         __syncthreads();
     }
-    // singular values = column norms; rank by descending value (ties: index)
+    // Singular values.  A rotation computed in FP32 is orthogonal only to
+    // rounding, so after many rotations a column of W = M J and the matching
+    // column of J carry the same small scale drift; sigma_c = ||W_c|| / ||J_c||
+    // cancels it, and J_c is renormalised.
+    __shared__ float jn[256];
+    __shared__ float wn[256];
     for (int c = warp; c < L; c += nwarps) {
-        float s2 = 0.f;
-        for (int i = lane; i < L; i += 32) s2 = fmaf(Mc[(size_t)c * L + i], Mc[(size_t)c * L + i], s2);
+        float s2 = 0.f, j2 = 0.f;
+        for (int i = lane; i < L; i += 32) {
+            s2 = fmaf(Mc[(size_t)c * L + i], Mc[(size_t)c * L + i], s2);
+            j2 = fmaf(Jc[(size_t)c * L + i], Jc[(size_t)c * L + i], j2);
+        }
         s2 = warp_sum(s2);
-        if (lane == 0) sv[c] = sqrtf(s2);
+        j2 = warp_sum(j2);
+        if (lane == 0) {
+            wn[c] = sqrtf(s2);
+            jn[c] = sqrtf(j2);
+            sv[c] = (j2 > 0.f) ? sqrtf(s2) / sqrtf(j2) : 0.f;
+        }
     }
     __syncthreads();
     for (int c = tid; c < L; c += blockDim.x) {
@@ -250,9 +271,9 @@ __global__ void __launch_bounds__(kSmallThreads)
         const int c = e / L, i = e % L;
         const int r = rank[c];
         if (r >= l || i >= l) continue;
-        const float s = sv[c];
-        Ut[i * l + r] = (s > 0.f) ? Mc[(size_t)c * L + i] / s : 0.f;
-        Jt[i * l + r] = Jc[(size_t)c * L + i];
+        const float w = wn[c];
+        Ut[i * l + r] = (w > 0.f) ? Mc[(size_t)c * L + i] / w : 0.f;
+        Jt[i * l + r] = (jn[c] > 0.f) ? Jc[(size_t)c * L + i] / jn[c] : 0.f;
     }
     for (int c = tid; c < L; c += blockDim.x)
         if (rank[c] < l) sigma[rank[c]] = sv[c];
@@ -350,6 +371,14 @@ void launch_small_matmul(cudaStream_t s, const float* A, const float* B, float* 
     dim3 block(16, 16);
     dim3 grid((unsigned)ceil_div(l, 16), (unsigned)ceil_div(l, 16));
     small_matmul_kernel<<<grid, block, 0, s>>>(A, B, C, l); count_launches();
+}
+
+void launch_small_d2f(cudaStream_t s, const double* in, float* out, int l, bool transpose)
+{
+    dim3 block(16, 16);
+    dim3 grid((unsigned)ceil_div(l, 16), (unsigned)ceil_div(l, 16));
+    small_d2f_kernel<<<grid, block, 0, s>>>(in, out, l, transpose ? 1 : 0);
+    count_launches();
 }
 
 void launch_small_transpose(cudaStream_t s, const float* in, float* out, int l)

@@ -2,7 +2,7 @@
 
 This module only draws random matrices with a planted spectrum.  It holds none
 of the randomized-SVD arithmetic: orthonormal factors come from a library QR
-(numpy on the host, torch on a device), never from this project's kernels or
+(numpy QR on the host; device matmuls with a host Cholesky), never from this project's kernels or
 from its CPU oracle.  Both the CUDA path and the oracle are fed the same stored
 values produced here.
 
@@ -69,10 +69,26 @@ def small_planted(seed: int = 0x160802148 + 1000) -> np.ndarray:
     return planted(2000, 1000, exp_spectrum(1000, 1.0 / 20.0), seed)
 
 
+def _orthonormal_torch(G):
+    """Orthonormalise the columns of a tall torch matrix with device matmuls
+    and a host (numpy, float64) factorisation of the small Gram matrix, twice.
+    Only library products are used; torch's device linear-algebra module is
+    not needed."""
+    import torch
+
+    for _ in range(2):
+        gram = (G.T @ G).double().cpu().numpy()
+        R = np.linalg.cholesky(gram).T
+        Rinv = np.linalg.inv(R)
+        G = G @ torch.as_tensor(Rinv, dtype=G.dtype, device=G.device)
+    return G
+
+
 def spiked_noise(m: int, n: int, sigma, noise_std: float, seed: int, device="cpu", dtype=None):
     """A = W_m diag(sigma) W_n^T + E on a torch device (float32 storage).
 
-    W_m (m x r) and W_n (n x r) are Q factors of seeded Gaussians (torch QR),
+    W_m (m x r) and W_n (n x r) are seeded Gaussians orthonormalised with
+    library products (device matmul, host Cholesky),
     r = len(sigma); E is i.i.d. N(0, noise_std^2)."""
     import torch
 
@@ -81,8 +97,8 @@ def spiked_noise(m: int, n: int, sigma, noise_std: float, seed: int, device="cpu
     gen.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
     sig = torch.as_tensor(np.asarray(sigma, dtype=np.float32), device=dev)
     r = sig.shape[0]
-    Wm, _ = torch.linalg.qr(torch.randn(m, r, generator=gen, device=dev, dtype=torch.float32))
-    Wn, _ = torch.linalg.qr(torch.randn(n, r, generator=gen, device=dev, dtype=torch.float32))
+    Wm = _orthonormal_torch(torch.randn(m, r, generator=gen, device=dev, dtype=torch.float32))
+    Wn = _orthonormal_torch(torch.randn(n, r, generator=gen, device=dev, dtype=torch.float32))
     A = torch.randn(m, n, generator=gen, device=dev, dtype=torch.float32)
     A.mul_(noise_std)
     A.addmm_(Wm * sig[None, :], Wn.T)
