@@ -179,6 +179,33 @@ int rsvdgb_pass_ax(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_
 int rsvdgb_pass_atx(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const float* X,
                     int64_t ldx, int l, float* Z, int64_t ldz, int engine, int prec);
 
+/* Size of the static device scratch used by rsvdgb_pass_atx_noalloc (16 MiB
+ * per device that loads the library, held until the process exits). */
+#define RSVDGB_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/*
+ * Allocation-free A^T X.  The paper has no counterpart: this entry point
+ * serves callers that cannot allocate device memory while they run -- code
+ * whose device memory is owned by a pool or arena, code that must not risk
+ * the device synchronisation a cudaMalloc / cudaFree can cause, or real-time
+ * code with a fixed memory budget.
+ *   Computes Z (n x l) = A^T X like rsvdgb_pass_atx with the FP32 FMA kernels:
+ *   A device m x n row-major (lda >= n, F32 or BF16), X device float m x l
+ *   row-major (ldx >= l), Z device float n x l row-major (ldz >= l); the work
+ *   is queued on cuda_stream of the CURRENT device.  No handle is needed.
+ *   Scratch: the K-split partial sums go to a static device array of
+ *   RSVDGB_NOALLOC_SCRATCH_BYTES; the call allocates and frees nothing.  A
+ *   problem with n * ldz * 4 bytes above that size is rejected with
+ *   RSVDGB_ERR_INVALID_ARG before anything is queued.
+ *   The first call on a device looks up the array's device address (once per
+ *   device); make that first call before any stream capture.  All calls on a
+ *   device share the array and it keeps the last call's contents, so calls
+ *   that overlap on the GPU (other streams, other host threads) race.
+ * Returns RSVDGB_OK once queued, RSVDGB_ERR_INVALID_ARG or RSVDGB_ERR_CUDA.
+ */
+int rsvdgb_pass_atx_noalloc(void* cuda_stream, const void* A, int64_t m, int64_t n, int64_t lda, int dtype,
+                            const float* X, int64_t ldx, int l, float* Z, int64_t ldz);
+
 /*
  * Instrumentation (not part of the paper's method).
  *  rsvdgb_profile_passes : when enable != 0, the handle records a CUDA event

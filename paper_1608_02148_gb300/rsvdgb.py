@@ -27,7 +27,10 @@ LAYOUT = {"row": 0, "col": 1}
 EXPORTS = ["rsvdgb_create", "rsvdgb_destroy", "rsvdgb_set_stream", "rsvdgb_default_opts", "rsvdgb_status_string",
            "rsvdgb_sketch_width", "rsvdgb_rsvd", "rsvdgb_rsvd_host", "rsvdgb_rqb", "rsvdgb_omega",
            "rsvdgb_pass_ax", "rsvdgb_pass_atx", "rsvdgb_profile_passes", "rsvdgb_profile_read",
-           "rsvdgb_kernel_launches"]
+           "rsvdgb_kernel_launches", "rsvdgb_pass_atx_noalloc"]
+
+# Static scratch of rsvdgb_pass_atx_noalloc (RSVDGB_NOALLOC_SCRATCH_BYTES).
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class RsvdgbOpts(ctypes.Structure):
@@ -85,6 +88,7 @@ def load(path: Path | str | None = None):
     lib.rsvdgb_profile_passes.argtypes = [P, I]
     lib.rsvdgb_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64),
                                         ctypes.POINTER(ctypes.c_double)]
+    lib.rsvdgb_pass_atx_noalloc.argtypes = [P, P, I64, I64, I64, I, P, I64, I, P, I64]
     lib.rsvdgb_kernel_launches.argtypes = []
     lib.rsvdgb_kernel_launches.restype = I64
     _lib = lib
@@ -291,3 +295,22 @@ def rsvdgb_profile_read(h: Handle):
 
 def rsvdgb_kernel_launches() -> int:
     return int(load().rsvdgb_kernel_launches())
+
+
+def rsvdgb_pass_atx_noalloc(A, X, Z=None, stream=None):
+    """Z = A^T X with no device allocation inside the library (static
+    scratch).  Z may be preallocated by the caller (n x l float32)."""
+    torch = _torch()
+    m, n = A.shape
+    l = X.shape[1]
+    if Z is None:
+        Z = torch.empty(n, l, dtype=torch.float32, device=A.device)
+    if n * Z.stride(0) * 4 > NOALLOC_SCRATCH_BYTES:
+        raise ValueError(f"A^T X with n={n}, ldz={Z.stride(0)} needs {n * Z.stride(0) * 4} bytes of scratch; "
+                         f"the static scratch holds {NOALLOC_SCRATCH_BYTES}")
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device)
+    rc = load().rsvdgb_pass_atx_noalloc(ctypes.c_void_p(stream.cuda_stream), A.data_ptr(), m, n, _rowmajor_ld(A),
+                                        _dtype_code(A), X.data_ptr(), _rowmajor_ld(X), l, Z.data_ptr(), Z.stride(0))
+    _check("rsvdgb_pass_atx_noalloc", rc)
+    return Z
