@@ -70,6 +70,26 @@ void launch_reduce_splits(cudaStream_t s, const float* part, int splits, int64_t
                           int64_t cols, int64_t ld, float* out32, double* out64, int64_t ld_out);
 
 // ---------------------------------------------------------------------------
+// Tensor-core passes over A (tcgen05 + TMA, 3xTF32, FP32 A only)
+//   trans = false: out (m x l_pad, column-major ld_out) = A P, P = n x l_pad
+//                  given column-major as TF32 hi/lo parts (Phi, Plo, ldp);
+//                  optional out_hi/out_lo receive the TF32 split of out.
+//   trans = true : partial sums of A^T P (n x l_pad per split, column-major
+//                  ld_out, consecutive splits l_pad*ld_out apart) with P = m x
+//                  l_pad; *splits_out receives the split count to reduce.
+// fro2 (optional) accumulates ||A||_F^2.  Device errors go to *status.
+// ---------------------------------------------------------------------------
+bool tc_pass_supported(int64_t m, int64_t n, int64_t lda, int l_pad, const void* A, int a_bf16);
+int launch_tc_pass(cudaStream_t s, int sm_count, bool trans, const float* A, int64_t m, int64_t n, int64_t lda,
+                   const float* Phi, const float* Plo, int64_t ldp, int l_pad, float* out, float* out_hi,
+                   float* out_lo, int64_t ld_out, float* partial, int64_t* splits_out, int* status, double* fro2);
+int64_t tc_pass_max_splits(int64_t m, int64_t n, int l_pad, int sm_count);
+// TF32 split of a column-major rows x l matrix (ld) into hi + lo parts over
+// l_pad columns; rows >= rows and columns >= l are written as zero.
+void launch_split_tf32(cudaStream_t s, const float* in, int64_t ld, int64_t rows, int l, int l_pad, float* hi,
+                       float* lo);
+
+// ---------------------------------------------------------------------------
 // Small l x l kernels (one CTA)
 // ---------------------------------------------------------------------------
 // Cholesky G + shift*I = R^T R of a symmetric l x l Gram matrix (FP64 input,

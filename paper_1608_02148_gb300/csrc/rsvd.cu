@@ -84,11 +84,17 @@ struct Geom {
     bool trans;    // logical = S^T
     bool swap_uv;  // user's U <- logical V
     int l;
+    int L;         // l rounded up to 16 (tensor-core N granularity)
+    bool use_tc;   // passes over A on the tensor cores
     int64_t ldm, ldn;
+    // stored matrix dimensions (rows x cols of the row-major S)
+    int64_t sm() const { return trans ? n : m; }
+    int64_t sn() const { return trans ? m : n; }
 };
 
 struct Work {
     float *Pt, *Yt, *Qt, *Wt, *Zt, *part;
+    float *Pth, *Ptl, *Yth, *Ytl;  // TF32 hi/lo parts of the panels (tensor-core engine)
     double* G;
     float *T1, *T2, *T, *R1, *R2, *RB, *M, *sigma, *Ut, *Jt, *jwork;
     int *status, *breakdowns;
@@ -105,7 +111,7 @@ int splits_for(int64_t tiles, int64_t K, int sm_count)
 
 size_t partial_floats(const Geom& g, int sm_count)
 {
-    const int64_t L = g.l;
+    const int64_t L = g.L;
     // largest K-split product: A^T-side pass (M = n, K = m), Grams (M = N = l)
     int64_t tiles_at = ceil_div(g.n, 64) * ceil_div(L, 64);
     int64_t s_at = splits_for(tiles_at, g.m, sm_count);
@@ -116,15 +122,27 @@ size_t partial_floats(const Geom& g, int sm_count)
     int64_t tiles_a = ceil_div(g.m, 64) * ceil_div(L, 64);
     int64_t s_a = splits_for(tiles_a, g.n, sm_count);
     need = std::max<int64_t>(need, s_a * L * g.ldm);
+    if (g.use_tc) {
+        // tensor-core A^T-side kernel on the stored matrix: lanes = stored columns
+        const int64_t s_tc = tc_pass_max_splits(g.sm(), g.sn(), g.L, sm_count);
+        need = std::max<int64_t>(need, s_tc * L * std::max(g.ldm, g.ldn));
+    }
     return (size_t)need;
 }
 
 void carve_work(Carve& c, const Geom& g, int sm_count, Work& w)
 {
-    const int64_t L = g.l;
+    const int64_t L = g.L;
     w.Pt = c.take<float>(L * g.ldn);
     w.Yt = c.take<float>(L * g.ldm);
     w.Qt = c.take<float>(L * g.ldm);
+    w.Pth = w.Ptl = w.Yth = w.Ytl = nullptr;
+    if (g.use_tc) {
+        w.Pth = c.take<float>(L * g.ldn);
+        w.Ptl = c.take<float>(L * g.ldn);
+        w.Yth = c.take<float>(L * g.ldm);
+        w.Ytl = c.take<float>(L * g.ldm);
+    }
     w.Wt = c.take<float>(L * g.ldn);
     w.Zt = c.take<float>(L * g.ldn);
     w.part = c.take<float>(partial_floats(g, sm_count));
@@ -229,20 +247,56 @@ void tall_gemm(cudaStream_t s, int sm, bool AT, bool BT, bool CT, const void* A,
 
 double a_bytes(const Geom& g) { return (double)g.m * (double)g.n * (g.a_bf16 ? 2.0 : 4.0); }
 
-// Y (m x l, column-major ldm) = A_logical X (X: n x l column-major, ldn)
-void apply_A(rsvdgb_handle* h, const Geom& g, const float* Xt, float* Yt, float* part, double* fro2)
+// One pass over A:  out = A_logical P (A_side) or A_logical^T P (!A_side).
+// P is column-major (K x l, ldP) in FP32 (SIMT engine) or as its TF32 hi/lo
+// parts (tensor-core engine).  out is column-major (rows x l, ldO); when
+// out_h/out_l are given (tensor-core engine) they receive its TF32 split.
+void pass_over_A(rsvdgb_handle* h, const Geom& g, Work& w, bool A_side, const float* P, const float* Ph,
+                 const float* Pl, float* out, float* out_h, float* out_l, double* fro2)
 {
-    // logical(i,k) = trans ? S[k*lda + i] : S[i*lda + k]
-    tall_gemm(h->stream, h->sm_count, g.trans, true, true, g.A, g.lda, g.a_bf16, Xt, g.ldn, Yt, g.ldm, g.m, g.l,
-              g.n, part, fro2, h, a_bytes(g));
+    const cudaStream_t s = h->stream;
+    const int64_t rows = A_side ? g.m : g.n;
+    const int64_t K = A_side ? g.n : g.m;
+    const int64_t ldP = A_side ? g.ldn : g.ldm;
+    const int64_t ldO = A_side ? g.ldm : g.ldn;
+    if (!g.use_tc) {
+        // logical(i,k) = trans ? S[k*lda + i] : S[i*lda + k]; the transpose flips it
+        const bool AT = A_side ? g.trans : !g.trans;
+        tall_gemm(s, h->sm_count, AT, true, true, g.A, g.lda, g.a_bf16, P, ldP, out, ldO, rows, g.l, K, w.part,
+                  fro2, h, a_bytes(g));
+        return;
+    }
+    // Tensor-core engine.  The kernel's lanes are stored rows (A X kernel) or
+    // stored columns (A^T X kernel, K split across CTAs, partials reduced).
+    const bool stored_atx = (A_side == g.trans);
+    int64_t splits = 1;
+    prof_mark(h, true, 0);
+    launch_tc_pass(s, h->sm_count, stored_atx, (const float*)g.A, g.sm(), g.sn(), g.lda, Ph, Pl, ldP, g.L,
+                   stored_atx ? nullptr : out, stored_atx ? nullptr : out_h, stored_atx ? nullptr : out_l, ldO,
+                   w.part, &splits, w.status, fro2);
+    prof_mark(h, false, a_bytes(g));
+    if (stored_atx) {
+        launch_reduce_splits(s, w.part, (int)splits, (int64_t)g.L * ldO, g.l, rows, ldO, out, nullptr, ldO);
+        if (out_h) launch_split_tf32(s, out, ldO, rows, g.l, g.L, out_h, out_l);
+    }
 }
 
-// W (n x l, column-major ldn) = A_logical^T Y (Y: m x l column-major, ldm)
-void apply_At(rsvdgb_handle* h, const Geom& g, const float* Yt, float* Wt, float* part)
+// Y = A_logical X with X = Pt (n x l) -> Yt (m x l) [+ TF32 split of Y]
+void apply_A(rsvdgb_handle* h, const Geom& g, Work& w, double* fro2)
 {
-    // logical^T(i,k) = logical(k,i) = trans ? S[i*lda + k] : S[k*lda + i]
-    tall_gemm(h->stream, h->sm_count, !g.trans, true, true, g.A, g.lda, g.a_bf16, Yt, g.ldm, Wt, g.ldn, g.n, g.l,
-              g.m, part, nullptr, h, a_bytes(g));
+    pass_over_A(h, g, w, true, w.Pt, w.Pth, w.Ptl, w.Yt, w.Yth, w.Ytl, fro2);
+}
+
+// W = A_logical^T Y with Y = Yt (m x l) -> Wt (n x l)
+void apply_At(rsvdgb_handle* h, const Geom& g, Work& w)
+{
+    pass_over_A(h, g, w, false, w.Yt, w.Yth, w.Ytl, w.Wt, nullptr, nullptr, nullptr);
+}
+
+// After the panel Pt changed: its TF32 split for the tensor-core engine.
+void split_panel(cudaStream_t s, const Geom& g, Work& w)
+{
+    if (g.use_tc) launch_split_tf32(s, w.Pt, g.ldn, g.n, g.l, g.L, w.Pth, w.Ptl);
 }
 
 // G (l x l, FP64) = X^T Z for column-major rows x l matrices X and Z
@@ -325,21 +379,23 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
 
     launch_clear_scalars(s, w.status, w.breakdowns, w.fro2);
     // step 2: Omega (n x l) into the panel
-    launch_omega(s, g.n, g.ldn, l, l, seed, sdist, w.Pt, g.ldn);
+    launch_omega(s, g.n, g.ldn, l, g.L, seed, sdist, w.Pt, g.ldn);
+    split_panel(s, g, w);
     // step 3: Y = A Omega, with ||A||_F^2 accumulated on the way
-    apply_A(h, g, w.Pt, w.Yt, w.part, w.fro2);
+    apply_A(h, g, w, w.fro2);
     gram(s, sm, w.Yt, g.ldm, g.m, l, w.part, w.G);
     // step 4: subspace iterations
     for (int it = 0; it < q; ++it) {
         // Q = qr(Y): only the span is carried forward, so one Cholesky step
         // (Q = Y T); A^T Q = (A^T Y) T.
         launch_chol_inv(s, w.G, l, 0.f, nullptr, w.T, w.status, w.breakdowns);
-        apply_At(h, g, w.Yt, w.Wt, w.part);
+        apply_At(h, g, w);
         times_small(s, sm, w.Wt, g.ldn, g.n, l, w.T, w.Zt, w.part);
         // Q = qr(A^T Q): CholeskyQR2 on the n side, result in the panel
         cholqr2(s, sm, w, w.Zt, g.ldn, g.n, l, w.Wt, w.Pt);
+        split_panel(s, g, w);
         // Y = A Q
-        apply_A(h, g, w.Pt, w.Yt, w.part, nullptr);
+        apply_A(h, g, w, nullptr);
         gram(s, sm, w.Yt, g.ldm, g.m, l, w.part, w.G);
     }
     // step 9: Q = qr(Y) with CholeskyQR2 (the first Gram is already in G):
@@ -349,8 +405,9 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
     gram(s, sm, w.Qt, g.ldm, g.m, l, w.part, w.G);
     launch_chol_inv(s, w.G, l, 0.f, nullptr, w.T2, w.status, w.breakdowns);
     times_small(s, sm, w.Qt, g.ldm, g.m, l, w.T2, w.Yt, w.part);
+    if (g.use_tc) launch_split_tf32(s, w.Yt, g.ldm, g.m, l, g.L, w.Yth, w.Ytl);
     // step 10: B^T = A^T Q (n x l, column-major: row j of B is contiguous)
-    apply_At(h, g, w.Yt, w.Wt, w.part);
+    apply_At(h, g, w);
     if (o.Qrow) launch_colmajor_to_rowmajor(s, w.Yt, g.ldm, g.m, l, o.Qrow, o.ldq);
     if (o.Brow)
         RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(o.Brow, o.ldb * sizeof(float), w.Wt, g.ldn * sizeof(float),
@@ -398,7 +455,8 @@ int check_handle(rsvdgb_handle* h)
 }
 
 // Validate a user matrix and build the m >= n geometry.
-int make_geom(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int layout, int k, int p, Geom& g)
+int make_geom(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int layout, int k, int p, int engine,
+              Geom& g)
 {
     if (!A || m < 1 || n < 1) return RSVDGB_ERR_INVALID_ARG;
     if (dtype != RSVDGB_F32 && dtype != RSVDGB_BF16) return RSVDGB_ERR_INVALID_ARG;
@@ -422,7 +480,12 @@ int make_geom(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int l
     g.l = (int)std::min<int64_t>((int64_t)k + p, mn);
     g.ldm = round_up(g.m, 32);
     g.ldn = round_up(g.n, 32);
+    g.L = (int)round_up(g.l, 16);
     if (g.l > kMaxL) return RSVDGB_ERR_UNSUPPORTED;
+    if (engine < RSVDGB_ENGINE_AUTO || engine > RSVDGB_ENGINE_TC) return RSVDGB_ERR_INVALID_ARG;
+    const bool tc_ok = tc_pass_supported(g.sm(), g.sn(), g.lda, g.L, A, g.a_bf16);
+    if (engine == RSVDGB_ENGINE_TC && !tc_ok) return RSVDGB_ERR_UNSUPPORTED;
+    g.use_tc = (engine != RSVDGB_ENGINE_SIMT) && tc_ok;
     return RSVDGB_OK;
 }
 
@@ -514,7 +577,7 @@ int rsvdgb_rsvd(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t l
         rsvdgb_default_opts(&o);
     if (o.q < 0 || o.sdist < 0 || o.sdist > 2) return RSVDGB_ERR_INVALID_ARG;
     Geom g{};
-    rc = make_geom(A, m, n, lda, dtype, o.layout, k, o.p, g);
+    rc = make_geom(A, m, n, lda, dtype, o.layout, k, o.p, o.engine, g);
     if (rc) return rc;
     if (nu < 0) nu = k;
     if (nv < 0) nv = k;
@@ -522,7 +585,6 @@ int rsvdgb_rsvd(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t l
     if (nu > 0 && (!U || ldu < nu)) return RSVDGB_ERR_INVALID_ARG;
     if (nv > 0 && (!V || ldv < nv)) return RSVDGB_ERR_INVALID_ARG;
     if (o.prec != RSVDGB_PREC_FP32) return RSVDGB_ERR_UNSUPPORTED;
-    if (o.engine == RSVDGB_ENGINE_TC) return RSVDGB_ERR_UNSUPPORTED;
     Outputs out{};
     out.d = d;
     out.info = info;
@@ -549,7 +611,7 @@ int rsvdgb_rqb(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t ld
     if (o.q < 0 || o.sdist < 0 || o.sdist > 2) return RSVDGB_ERR_INVALID_ARG;
     if (m < n || o.layout != RSVDGB_ROW_MAJOR) return RSVDGB_ERR_INVALID_ARG;
     Geom g{};
-    rc = make_geom(A, m, n, lda, dtype, o.layout, k, o.p, g);
+    rc = make_geom(A, m, n, lda, dtype, o.layout, k, o.p, o.engine, g);
     if (rc) return rc;
     if (!Q || !B || ldq < g.l || ldb < n) return RSVDGB_ERR_INVALID_ARG;
     if (o.prec != RSVDGB_PREC_FP32) return RSVDGB_ERR_UNSUPPORTED;
@@ -647,15 +709,51 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
     if (!A || !X || !Y || m < 1 || n < 1 || l < 1 || lda < n) return RSVDGB_ERR_INVALID_ARG;
     if (dtype != RSVDGB_F32 && dtype != RSVDGB_BF16) return RSVDGB_ERR_INVALID_ARG;
     if (ldx < l || ldy < l) return RSVDGB_ERR_INVALID_ARG;
-    if (prec != RSVDGB_PREC_FP32 || engine == RSVDGB_ENGINE_TC) return RSVDGB_ERR_UNSUPPORTED;
-    // partial buffer for the K split
+    if (engine < RSVDGB_ENGINE_AUTO || engine > RSVDGB_ENGINE_TC) return RSVDGB_ERR_INVALID_ARG;
+    if (prec != RSVDGB_PREC_FP32) return RSVDGB_ERR_UNSUPPORTED;
     const int64_t M = transpose ? n : m, K = transpose ? m : n;
-    const int64_t tiles = ceil_div(M, 64) * ceil_div(l, 64);
-    const int splits = splits_for(tiles, K, h->sm_count);
-    rc = ensure_workspace(h, (size_t)splits * M * ldy * sizeof(float) + 1024);
+    const int L = (int)round_up(l, 16);
+    const bool tc_ok = l <= 256 && tc_pass_supported(m, n, lda, L, A, dtype == RSVDGB_BF16);
+    if (engine == RSVDGB_ENGINE_TC && !tc_ok) return RSVDGB_ERR_UNSUPPORTED;
+    if (engine == RSVDGB_ENGINE_SIMT || !tc_ok) {
+        const int64_t tiles = ceil_div(M, 64) * ceil_div(l, 64);
+        const int splits = splits_for(tiles, K, h->sm_count);
+        rc = ensure_workspace(h, (size_t)splits * M * ldy * sizeof(float) + 1024);
+        if (rc) return rc;
+        tall_gemm(h->stream, h->sm_count, transpose, false, false, A, lda, dtype == RSVDGB_BF16, X, ldx, Y, ldy, M, l,
+                  K, (float*)h->ws, nullptr);
+        RSVDGB_CUDA_TRY(cudaGetLastError());
+        return RSVDGB_OK;
+    }
+    // tensor-core engine: stage X column-major and TF32-split, run, copy back
+    const int64_t ldK = round_up(K, 32), ldM = round_up(M, 32);
+    const int64_t splits = transpose ? tc_pass_max_splits(m, n, L, h->sm_count) : 1;
+    Carve probe(nullptr);
+    probe.take<float>(L * ldK);
+    probe.take<float>(L * ldK);
+    probe.take<float>(L * ldK);
+    probe.take<float>(L * ldM);
+    probe.take<float>(splits * L * ldM);
+    probe.take<int>(4);
+    rc = ensure_workspace(h, probe.off + 1024);
     if (rc) return rc;
-    tall_gemm(h->stream, h->sm_count, transpose, false, false, A, lda, dtype == RSVDGB_BF16, X, ldx, Y, ldy, M, l, K,
-              (float*)h->ws, nullptr);
+    Carve c(h->ws);
+    float* Xc = c.take<float>(L * ldK);
+    float* Xh = c.take<float>(L * ldK);
+    float* Xl = c.take<float>(L * ldK);
+    float* Yc = c.take<float>(L * ldM);
+    float* part = c.take<float>(splits * L * ldM);
+    int* status = c.take<int>(4);
+    const cudaStream_t s = h->stream;
+    RSVDGB_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    launch_rowmajor_to_colmajor(s, X, ldx, K, l, L, Xc, ldK);
+    launch_split_tf32(s, Xc, ldK, K, l, L, Xh, Xl);
+    int64_t used = 1;
+    rc = launch_tc_pass(s, h->sm_count, transpose, (const float*)A, m, n, lda, Xh, Xl, ldK, L,
+                        transpose ? nullptr : Yc, nullptr, nullptr, ldM, part, &used, status, nullptr);
+    if (rc) return rc;
+    if (transpose) launch_reduce_splits(s, part, (int)used, (int64_t)L * ldM, l, M, ldM, Yc, nullptr, ldM);
+    launch_colmajor_to_rowmajor(s, Yc, ldM, M, l, Y, ldy);
     RSVDGB_CUDA_TRY(cudaGetLastError());
     return RSVDGB_OK;
 }

@@ -315,6 +315,26 @@ __global__ void clear_scalars_kernel(int* status, int* breakdowns, double* fro2)
     if (fro2) *fro2 = 0.0;
 }
 
+__global__ void split_tf32_kernel(const float* __restrict__ in, int64_t ld, int64_t rows, int l, int l_pad,
+                                  float* __restrict__ hi, float* __restrict__ lo)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= ld || j >= l_pad) return;
+    const int64_t o = (int64_t)j * ld + i;
+    float h = 0.f, r = 0.f;
+    if (i < rows && j < l) {
+        const float x = in[o];
+        uint32_t hb, rb;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(x));
+        h = __uint_as_float(hb);
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(rb) : "f"(x - h));
+        r = __uint_as_float(rb);
+    }
+    hi[o] = h;
+    lo[o] = r;
+}
+
 __global__ void col_to_row_kernel(const float* __restrict__ in, int64_t ld, int64_t rows, int cols,
                                   float* __restrict__ out, int64_t ldo)
 {
@@ -405,6 +425,14 @@ void launch_finalize_info(cudaStream_t s, const float* sigma, int l, int k, floa
 void launch_clear_scalars(cudaStream_t s, int* status, int* breakdowns, double* fro2)
 {
     clear_scalars_kernel<<<1, 1, 0, s>>>(status, breakdowns, fro2); count_launches();
+}
+
+void launch_split_tf32(cudaStream_t s, const float* in, int64_t ld, int64_t rows, int l, int l_pad, float* hi,
+                       float* lo)
+{
+    dim3 grid((unsigned)ceil_div(ld, 256), (unsigned)l_pad);
+    split_tf32_kernel<<<grid, 256, 0, s>>>(in, ld, rows, l, l_pad, hi, lo);
+    count_launches();
 }
 
 void launch_colmajor_to_rowmajor(cudaStream_t s, const float* in, int64_t ld, int64_t rows, int cols, float* out,

@@ -1,0 +1,587 @@
+// Tensor-core (tcgen05 + TMA) passes over A with FP32-accurate 3xTF32 products.
+//
+// One kernel serves both products of the method:
+//   AX  (TRANS = false): Y = A X      -- sketch Y = A Omega (Eq. YAQ) and the
+//                                        power step Y = A Q (Algorithm
+//                                        sub_iterations step 4);
+//   AtX (TRANS = true) : Z = A^T Y    -- power step A^T Q (step 3) and the
+//                                        projection B = Q^T A = (A^T Q)^T
+//                                        (Eq. BQA).
+// The MMA is D[128 x N] += A_op[128 x 8] * P[8 x N] with N = l_pad:
+//   * the 128 accumulator lanes are 128 rows of A (AX) or 128 columns of A
+//     (AtX); each CTA keeps G such accumulators in tensor memory (TMEM);
+//   * the panel P (Omega, Q_n or Y; column-major, i.e. K-major) is streamed by
+//     TMA into shared memory, already split into TF32 hi and lo parts;
+//   * A is streamed by TMA into shared memory once; four "converter" warps read
+//     each element once, split it a = a_hi + a_lo (a_hi = TF32 round-to-
+//     nearest of a, a_lo = TF32 of the remainder) and store both into TMEM,
+//     where the MMA reads its A operand (tcgen05.mma ... [a_tmem]);
+//   * three MMAs per K step, a_hi p_hi + a_hi p_lo + a_lo p_hi, accumulate in
+//     FP32; the dropped a_lo p_lo term and the TF32 rounding of the lo parts
+//     are below 2^-21 relative per product.
+// Roles (192 threads): warp 0 issues TMA, warp 1 allocates TMEM and issues
+// MMAs (one elected lane), warps 2..5 convert A and run the epilogue.  Every
+// mbarrier wait is bounded; on expiry the kernel records RSVDGB_ERR_TIMEOUT,
+// stops issuing work, waits (bounded) for its copies and MMAs in flight, frees
+// its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "internal.cuh"
+
+namespace rsvdgb {
+namespace {
+
+constexpr int kBK = 32;            // K elements per stage (one 128-byte swizzle row)
+constexpr int kTileRows = 128;     // accumulator lanes
+constexpr int kThreads = 192;      // 6 warps
+constexpr int kTmemStages = 2;     // A-operand buffers in TMEM
+constexpr long long kSpinLimit = 4000000000LL;  // clock64 ticks (about 2 s)
+
+struct TcParams {
+    int64_t m, n;          // stored A: row-major m x n
+    int l_pad;             // MMA N (multiple of 16, <= 256)
+    int64_t num_tiles;     // 128-wide tiles along the lane dimension
+    int64_t k_total;       // extent of K (n for AX, m for AtX)
+    int64_t k_per_split;   // AtX: K rows per split (multiple of kBK); AX: k_total
+    int stages;            // shared-memory pipeline depth
+    float* out;            // AX: Yt (column-major, ld_out); AtX: partial base
+    float* out_hi;         // AX: TF32 hi part of Y (may be null)
+    float* out_lo;         // AX: TF32 lo part of Y (may be null)
+    int64_t ld_out;
+    int64_t split_stride;  // AtX: floats between partials
+    int* status;
+    double* fro2;          // if set: ||A||_F^2 is accumulated by the converters
+};
+
+// ----------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase.  Returns false (and raises the CTA's
+// abort flag and the global status) if the phase did not complete in time
+// or another role already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status)
+{
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kSpinLimit) {
+            *abort_flag = 1;
+            if (status) atomicExch(status, RSVDGB_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int c0, int c1)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+            "r"(smem_u32(dst)),
+        "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);        // start address
+    d |= (uint64_t)1 << 16;                         // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                         // descriptor version
+    d |= (uint64_t)2 << 61;                         // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major.
+__device__ __forceinline__ uint32_t tf32_idesc(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32_tmemA(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                               uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// 32 lanes x 32 bit, 32 consecutive columns per thread.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]),
+        "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]),
+        "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+
+// 32 lanes x 32 bit, 16 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ----------------------------------------------------------------- the kernel
+template <bool TRANS, int G>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_pass_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapPhi,
+                   const __grid_constant__ CUtensorMap tmapPlo, TcParams p)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // 1024-byte aligned base for the swizzled tiles
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+
+    __shared__ uint64_t full_bar[4], empty_bar[4];
+    __shared__ uint64_t conv_bar[kTmemStages], tfree_bar[kTmemStages];
+    __shared__ uint64_t accf_bar, acce_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_flag;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int S = p.stages;
+    const int l_pad = p.l_pad;
+    const uint32_t a_tile_bytes = kTileRows * kBK * 4;         // 16 KB
+    const uint32_t p_tile_bytes = (uint32_t)l_pad * kBK * 4;   // l_pad rows x 128 B
+    const uint32_t stage_bytes = G * a_tile_bytes + 2 * p_tile_bytes;
+
+    // ---- work of this CTA: a range of lane tiles and a K range
+    int64_t tile_begin, tile_end, k_begin, k_end;
+    if (!TRANS) {
+        tile_begin = p.num_tiles * blockIdx.x / gridDim.x;
+        tile_end = p.num_tiles * (blockIdx.x + 1) / gridDim.x;
+        k_begin = 0;
+        k_end = p.k_total;
+    } else {
+        tile_begin = (int64_t)blockIdx.x * G;
+        tile_end = min(p.num_tiles, tile_begin + G);
+        k_begin = (int64_t)blockIdx.y * p.k_per_split;
+        k_end = min(p.k_total, k_begin + p.k_per_split);
+    }
+    const int64_t num_sets = (tile_end - tile_begin + G - 1) / G;
+    const int64_t nk = (k_end > k_begin) ? (k_end - k_begin + kBK - 1) / kBK : 0;
+
+    // ---- TMEM columns: G accumulators of l_pad, then A buffers
+    const uint32_t acc_cols = (uint32_t)G * l_pad;
+    const uint32_t a_col0 = (acc_cols + 31) & ~31u;
+    const uint32_t need = a_col0 + kTmemStages * G * 2 * kBK;
+    uint32_t tmem_cols = 32;
+    while (tmem_cols < need) tmem_cols <<= 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int s = 0; s < kTmemStages; ++s) {
+            mbar_init(&conv_bar[s], 4);
+            mbar_init(&tfree_bar[s], 1);
+        }
+        mbar_init(&accf_bar, 1);
+        mbar_init(&acce_bar, 4);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp == 0) {
+        // =========================== TMA producer
+        if (lane == 0) {
+            int64_t it = 0;
+            bool ok = true;
+            for (int64_t set = 0; set < num_sets && ok; ++set) {
+                const int64_t t0 = tile_begin + set * G;
+                const int gv = (int)min((int64_t)G, tile_end - t0);
+                for (int64_t c = 0; c < nk && ok; ++c, ++it) {
+                    const int s = (int)(it % S);
+                    const uint32_t ph = (uint32_t)((it / S) & 1);
+                    if (!(ok = mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, p.status))) break;
+                    uint8_t* st = smem + (size_t)s * stage_bytes;
+                    mbar_expect_tx(&full_bar[s], gv * a_tile_bytes + 2 * p_tile_bytes);
+                    const int kc = (int)(k_begin + c * kBK);
+                    for (int g = 0; g < gv; ++g) {
+                        const int lane0 = (int)((t0 + g) * kTileRows);
+                        if (!TRANS)
+                            tma_load_2d(&tmapA, &full_bar[s], st + g * a_tile_bytes, kc, lane0);  // {col k, row}
+                        else
+                            tma_load_2d(&tmapA, &full_bar[s], st + g * a_tile_bytes, lane0, kc);  // {col, row k}
+                    }
+                    tma_load_2d(&tmapPhi, &full_bar[s], st + G * a_tile_bytes, kc, 0);
+                    tma_load_2d(&tmapPlo, &full_bar[s], st + G * a_tile_bytes + p_tile_bytes, kc, 0);
+                }
+            }
+            if (!ok) {
+                // drain: wait (bounded) for the copies already issued
+                const long long t0 = clock64();
+                for (int64_t j = (it > S ? it - S : 0); j < it; ++j) {
+                    const int s = (int)(j % S);
+                    const uint32_t ph = (uint32_t)((j / S) & 1);
+                    while (!mbar_test(&full_bar[s], ph) && clock64() - t0 < kSpinLimit) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // =========================== MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = tf32_idesc(kTileRows, l_pad);
+            int64_t it = 0;
+            bool ok = true;
+            for (int64_t set = 0; set < num_sets && ok; ++set) {
+                const int64_t t0 = tile_begin + set * G;
+                const int gv = (int)min((int64_t)G, tile_end - t0);
+                if (!(ok = mbar_wait(&acce_bar, ((uint32_t)set & 1) ^ 1, &abort_flag, p.status))) break;
+                tmem_fence_after();
+                for (int64_t c = 0; c < nk; ++c, ++it) {
+                    const int s = (int)(it % S);
+                    const uint32_t ph = (uint32_t)((it / S) & 1);
+                    const int ts = (int)(it % kTmemStages);
+                    const uint32_t tph = (uint32_t)((it / kTmemStages) & 1);
+                    if (!(ok = mbar_wait(&conv_bar[ts], tph, &abort_flag, p.status))) break;
+                    if (!(ok = mbar_wait(&full_bar[s], ph, &abort_flag, p.status))) break;
+                    tmem_fence_after();
+                    const uint32_t phi = smem_u32(smem + (size_t)s * stage_bytes + G * a_tile_bytes);
+                    const uint32_t plo = phi + p_tile_bytes;
+                    for (int g = 0; g < gv; ++g) {
+                        const uint32_t d = tmem + (uint32_t)(g * l_pad);
+                        const uint32_t ahi = tmem + a_col0 + (uint32_t)((ts * G + g) * 2 * kBK);
+                        const uint32_t alo = ahi + kBK;
+#pragma unroll
+                        for (int kk = 0; kk < kBK / 8; ++kk) {
+                            const uint64_t bhi = sw128_desc(phi + kk * 32);
+                            const uint64_t blo = sw128_desc(plo + kk * 32);
+                            const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+                            mma_tf32_tmemA(d, ahi + kk * 8, bhi, idesc, acc);
+                            mma_tf32_tmemA(d, ahi + kk * 8, blo, idesc, 1u);
+                            mma_tf32_tmemA(d, alo + kk * 8, bhi, idesc, 1u);
+                        }
+                    }
+                    mma_commit(&empty_bar[s]);
+                    mma_commit(&tfree_bar[ts]);
+                }
+                if (!ok) break;
+                mma_commit(&accf_bar);
+            }
+            if (!ok) {
+                // wait (bounded) for the MMAs already issued before TMEM is freed
+                __shared__ uint64_t drain_bar;
+                mbar_init(&drain_bar, 1);
+                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+                mma_commit(&drain_bar);
+                const long long t0 = clock64();
+                while (!mbar_test(&drain_bar, 0) && clock64() - t0 < kSpinLimit) {
+                }
+            }
+        }
+    } else {
+        // =========================== converters + epilogue (warps 2..5)
+        const int q = warp & 3;                 // TMEM lane quarter of this warp
+        const int r = q * 32 + lane;            // lane (row of the tile) of this thread
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        float sq = 0.f;  // sum of squares of the A elements this thread converted
+        int64_t it = 0;
+        bool ok = true;
+        for (int64_t set = 0; set < num_sets && ok; ++set) {
+            const int64_t t0 = tile_begin + set * G;
+            const int gv = (int)min((int64_t)G, tile_end - t0);
+            for (int64_t c = 0; c < nk; ++c, ++it) {
+                const int s = (int)(it % S);
+                const uint32_t ph = (uint32_t)((it / S) & 1);
+                const int ts = (int)(it % kTmemStages);
+                const uint32_t tph = (uint32_t)((it / kTmemStages) & 1);
+                if (!(ok = mbar_wait(&full_bar[s], ph, &abort_flag, p.status))) break;
+                if (!(ok = mbar_wait(&tfree_bar[ts], tph ^ 1, &abort_flag, p.status))) break;
+                tmem_fence_after();
+                const uint8_t* st = smem + (size_t)s * stage_bytes;
+                for (int g = 0; g < gv; ++g) {
+                    const float* tile = (const float*)(st + g * a_tile_bytes);
+                    uint32_t hi[32], lo[32];
+                    if (!TRANS) {
+                        // row r of a 128 x 32 tile, 128-byte swizzle: 16-byte chunk c of
+                        // row r sits at chunk (c ^ (r & 7))
+#pragma unroll
+                        for (int ch = 0; ch < 8; ++ch) {
+                            const float4 v =
+                                *(const float4*)((const uint8_t*)tile + r * 128 + ((ch ^ (r & 7)) << 4));
+                            const float a4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                sq = fmaf(a4[e], a4[e], sq);
+                                const uint32_t h = tf32_rna(a4[e]);
+                                hi[ch * 4 + e] = h;
+                                lo[ch * 4 + e] = tf32_rna(a4[e] - __uint_as_float(h));
+                            }
+                        }
+                    } else {
+                        // column r of a 32 x 128 tile (rows of 512 bytes, no swizzle)
+#pragma unroll
+                        for (int k = 0; k < kBK; ++k) {
+                            const float a = tile[k * kTileRows + r];
+                            sq = fmaf(a, a, sq);
+                            const uint32_t h = tf32_rna(a);
+                            hi[k] = h;
+                            lo[k] = tf32_rna(a - __uint_as_float(h));
+                        }
+                    }
+                    const uint32_t col = tmem + a_col0 + (uint32_t)((ts * G + g) * 2 * kBK);
+                    tmem_st32(col + lane_off, hi);
+                    tmem_st32(col + kBK + lane_off, lo);
+                }
+                tmem_wait_st();
+                tmem_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&conv_bar[ts]);
+            }
+            if (!ok) break;
+            // ---- epilogue of this tile set
+            if (!(ok = mbar_wait(&accf_bar, (uint32_t)set & 1, &abort_flag, p.status))) break;
+            tmem_fence_after();
+            for (int g = 0; g < gv; ++g) {
+                const int64_t idx = (t0 + g) * kTileRows + r;  // row (AX) or column (AtX) of A
+                const int64_t lim = TRANS ? p.n : p.m;
+                float* out = p.out + (TRANS ? (int64_t)blockIdx.y * p.split_stride : 0);
+                for (int j0 = 0; j0 < l_pad; j0 += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(tmem + (uint32_t)(g * l_pad + j0) + lane_off, v);
+                    tmem_wait_ld();
+                    if (idx < lim) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const float y = __uint_as_float(v[e]);
+                            const int64_t o = (int64_t)(j0 + e) * p.ld_out + idx;
+                            out[o] = y;
+                            if (!TRANS && p.out_hi) {
+                                const uint32_t h = tf32_rna(y);
+                                p.out_hi[o] = __uint_as_float(h);
+                                p.out_lo[o] = __uint_as_float(tf32_rna(y - __uint_as_float(h)));
+                            }
+                        }
+                    }
+                }
+            }
+            tmem_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce_bar);
+        }
+        if (p.fro2) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            if (lane == 0) atomicAdd(p.fro2, (double)sq);
+        }
+    }
+
+    tmem_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tmem_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+    }
+}
+
+// ----------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 get_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+    }
+    return fn;
+}
+
+bool encode_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+               uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz)
+{
+    auto enc = get_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {row_bytes};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <bool TRANS, int G>
+int launch_typed(cudaStream_t s, const CUtensorMap& mA, const CUtensorMap& mhi, const CUtensorMap& mlo,
+                 TcParams p, dim3 grid, size_t smem)
+{
+    auto kern = tc_pass_kernel<TRANS, G>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return RSVDGB_ERR_CUDA;
+    kern<<<grid, kThreads, smem, s>>>(mA, mhi, mlo, p);
+    count_launches();
+    return cudaGetLastError() == cudaSuccess ? RSVDGB_OK : RSVDGB_ERR_CUDA;
+}
+
+int groups_for(int l_pad)
+{
+    // TMEM: G accumulators of l_pad columns + 2 stages x G x 64 A columns <= 512
+    int g = 3;
+    while (g > 1 && ((g * l_pad + 31) / 32 * 32 + kTmemStages * g * 2 * kBK) > 512) --g;
+    return g;
+}
+
+}  // namespace
+
+bool tc_pass_supported(int64_t m, int64_t n, int64_t lda, int l_pad, const void* A, int a_bf16)
+{
+    if (a_bf16) return false;
+    if (l_pad < 16 || l_pad > 256 || (l_pad % 16)) return false;
+    if ((lda * 4) % 16 || ((uintptr_t)A % 16)) return false;
+    if (m > 0x7fffffff || n > 0x7fffffff) return false;
+    return get_encoder() != nullptr;
+}
+
+int launch_tc_pass(cudaStream_t s, int sm_count, bool trans, const float* A, int64_t m, int64_t n, int64_t lda,
+                   const float* Phi, const float* Plo, int64_t ldp, int l_pad, float* out, float* out_hi,
+                   float* out_lo, int64_t ld_out, float* partial, int64_t* splits_out, int* status, double* fro2)
+{
+    const int G = groups_for(l_pad);
+    const uint32_t stage_bytes = G * kTileRows * kBK * 4 + 2 * (uint32_t)l_pad * kBK * 4;
+    const size_t smem_budget = 225 * 1024;
+    int stages = (int)std::min<size_t>(4, (smem_budget - 1024) / stage_bytes);
+    if (stages < 2) return RSVDGB_ERR_UNSUPPORTED;
+    const size_t smem = (size_t)stages * stage_bytes + 1024;
+
+    CUtensorMap mA, mhi, mlo;
+    const int64_t k_total = trans ? m : n;
+    bool ok;
+    if (!trans)
+        ok = encode_2d(&mA, A, n, m, lda * 4, kBK, kTileRows, CU_TENSOR_MAP_SWIZZLE_128B);
+    else
+        ok = encode_2d(&mA, A, n, m, lda * 4, kTileRows, kBK, CU_TENSOR_MAP_SWIZZLE_NONE);
+    ok = ok && encode_2d(&mhi, Phi, k_total, l_pad, ldp * 4, kBK, l_pad, CU_TENSOR_MAP_SWIZZLE_128B);
+    ok = ok && encode_2d(&mlo, Plo, k_total, l_pad, ldp * 4, kBK, l_pad, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (!ok) return RSVDGB_ERR_CUDA;
+
+    TcParams p{};
+    p.m = m;
+    p.n = n;
+    p.l_pad = l_pad;
+    p.k_total = k_total;
+    p.stages = stages;
+    p.status = status;
+    p.fro2 = fro2;
+    p.ld_out = ld_out;
+    dim3 grid;
+    if (!trans) {
+        p.num_tiles = ceil_div(m, kTileRows);
+        p.k_per_split = n;
+        p.out = out;
+        p.out_hi = out_hi;
+        p.out_lo = out_lo;
+        grid = dim3((unsigned)std::min<int64_t>(sm_count, p.num_tiles));
+        if (splits_out) *splits_out = 1;
+    } else {
+        p.num_tiles = ceil_div(n, kTileRows);
+        const int64_t sets = ceil_div(p.num_tiles, G);
+        int64_t splits = std::max<int64_t>(1, (int64_t)sm_count / sets);
+        splits = std::min<int64_t>(splits, std::max<int64_t>(1, m / (4 * kBK)));
+        p.k_per_split = round_up(ceil_div(m, splits), kBK);
+        splits = ceil_div(m, p.k_per_split);
+        p.out = partial;
+        p.split_stride = (int64_t)l_pad * ld_out;
+        grid = dim3((unsigned)sets, (unsigned)splits);
+        if (splits_out) *splits_out = splits;
+    }
+    switch ((trans ? 8 : 0) + G) {
+        case 1: return launch_typed<false, 1>(s, mA, mhi, mlo, p, grid, smem);
+        case 2: return launch_typed<false, 2>(s, mA, mhi, mlo, p, grid, smem);
+        case 3: return launch_typed<false, 3>(s, mA, mhi, mlo, p, grid, smem);
+        case 9: return launch_typed<true, 1>(s, mA, mhi, mlo, p, grid, smem);
+        case 10: return launch_typed<true, 2>(s, mA, mhi, mlo, p, grid, smem);
+        case 11: return launch_typed<true, 3>(s, mA, mhi, mlo, p, grid, smem);
+        default: return RSVDGB_ERR_UNSUPPORTED;
+    }
+}
+
+int64_t tc_pass_max_splits(int64_t m, int64_t n, int l_pad, int sm_count)
+{
+    const int G = groups_for(l_pad);
+    const int64_t sets = ceil_div(ceil_div(n, kTileRows), G);
+    int64_t splits = std::max<int64_t>(1, (int64_t)sm_count / sets);
+    splits = std::min<int64_t>(splits, std::max<int64_t>(1, m / (4 * kBK)));
+    const int64_t kps = round_up(ceil_div(m, splits), kBK);
+    return ceil_div(m, kps);
+}
+
+}  // namespace rsvdgb

@@ -1,0 +1,94 @@
+"""Parity of the tensor-core (tcgen05 + TMA, 3xTF32) passes over A with the
+FP64 oracle, through the C ABI.
+
+Error model of one 3xTF32 product: a_hi p_hi + a_hi p_lo + a_lo p_hi with the
+lo parts rounded to TF32 and a_lo p_lo dropped leaves at most 2^-20 |a||p| per
+product; FP32 accumulation adds K u32 |a||p|.  The bound below is
+(2^-19 + 2 K u32) (|A| |X|) element by element.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1608_02148_gb300 import inputs
+from tests.helpers import sigma_err, sin_theta, subspace_tol
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import torch
+    from paper_1608_02148_gb300 import build, rsvdgb
+    build.build()
+    assert torch.cuda.is_available()
+    return rsvdgb
+
+
+@pytest.fixture(scope="module")
+def handle(rs):
+    h = rs.Handle(0)
+    yield h
+    h.close()
+
+
+def to_dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("m,n,l", [(300, 200, 30), (1000, 64, 1), (520, 332, 24), (260, 128, 110),
+                                   (64, 640, 8), (1030, 516, 220), (4096, 256, 256), (777, 1000, 112)])
+def test_tc_passes_match_oracle_products(rs, handle, m, n, l):
+    rng = np.random.default_rng(7 * m + n + l)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    X = rng.standard_normal((n, l)).astype(np.float32)
+    W = rng.standard_normal((m, l)).astype(np.float32)
+    Ad = to_dev(A)
+    Y = rs.rsvdgb_pass_ax(handle, Ad, to_dev(X), engine="tc").cpu().numpy().astype(np.float64)
+    Z = rs.rsvdgb_pass_atx(handle, Ad, to_dev(W), engine="tc").cpu().numpy().astype(np.float64)
+    Yo = oracle.gemm_ax(A, X.astype(np.float64))
+    Zo = oracle.gemm_atx(A, W.astype(np.float64))
+    Aa = np.abs(A).astype(np.float64)
+    by = (2.0 ** -19 + 2 * n * 2.0 ** -24) * (Aa @ np.abs(X))
+    bz = (2.0 ** -19 + 2 * m * 2.0 ** -24) * (Aa.T @ np.abs(W))
+    assert np.all(np.abs(Y - Yo) <= by), float(np.max(np.abs(Y - Yo) / by))
+    assert np.all(np.abs(Z - Zo) <= bz), float(np.max(np.abs(Z - Zo) / bz))
+
+
+def test_tc_rejects_unaligned_rows(rs, handle):
+    import torch
+    A = torch.zeros(100, 33, device="cuda")  # lda = 33 floats: rows not 16-byte aligned
+    X = torch.zeros(33, 8, device="cuda")
+    with pytest.raises(rs.RsvdgbError) as e:
+        rs.rsvdgb_pass_ax(handle, A, X, engine="tc")
+    assert e.value.status == 7
+
+
+@pytest.mark.parametrize("m,n,k,p,q", [(2000, 1000, 20, 10, 2), (513, 256, 100, 10, 1), (300, 1000, 12, 6, 2),
+                                       (400, 232, 200, 20, 1), (4096, 64, 10, 6, 3)])
+def test_tc_rsvd_matches_oracle(rs, handle, m, n, k, p, q):
+    import torch
+    sigma = inputs.exp_spectrum(min(m, n), 3.0 / min(m, n)) if (m, n) != (2000, 1000) else \
+        inputs.exp_spectrum(1000, 1.0 / 20.0)
+    A = inputs.planted(m, n, sigma, seed=m + 3 * n)
+    d_o, U_o, V_o, Q_o, B_o = oracle.rsvd(A, k, p=p, q=q, seed=5, return_qb=True)
+    d, U, V, info = rs.rsvdgb_rsvd(handle, to_dev(A), k, opts=rs.make_opts(p=p, q=q, seed=5, engine="tc"))
+    torch.cuda.synchronize()
+    assert info.status == 0, info.as_dict()
+    assert sigma_err(d.cpu().numpy(), d_o) <= 1e-5, sigma_err(d.cpu().numpy(), d_o)
+    sB = np.linalg.svd(B_o, compute_uv=False)
+    tol = subspace_tol(sB, k, sB[0])
+    assert sin_theta(U.cpu().numpy(), U_o) <= tol
+    assert sin_theta(V.cpu().numpy(), V_o) <= tol
+    fa = oracle.fro2(A)
+    assert abs(info.fro2_A - fa) <= 1e-5 * fa
+
+
+def test_tc_and_simt_engines_agree(rs, handle):
+    A = inputs.planted(3000, 400, inputs.exp_spectrum(400, 0.03), seed=77)
+    Ad = to_dev(A)
+    d1, U1, V1, _ = rs.rsvdgb_rsvd(handle, Ad, 30, opts=rs.make_opts(engine="tc"))
+    d2, U2, V2, _ = rs.rsvdgb_rsvd(handle, Ad, 30, opts=rs.make_opts(engine="simt"))
+    d1, d2 = d1.cpu().numpy(), d2.cpu().numpy()
+    assert np.max(np.abs(d1 - d2)) <= 2e-5 * d2[0]
