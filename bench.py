@@ -280,8 +280,8 @@ def main():
     l = rs.rsvdgb_sketch_width(m, n, k, wl["p"])
     achieved_gbs = (pass_bytes / max(pass_n, 1)) / (pass_avg_ms * 1e-3) / 1e9
     achieved_tflops = (2.0 * m * n * l) / (pass_avg_ms * 1e-3) / 1e12
-    engine = args.engine
-    if engine in ("auto", "simt"):
+    engine = "tc" if info.engine == 2 else "simt"
+    if engine == "simt":
         roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": SIMT_FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved_tflops / SIMT_FP32_PEAK_TFLOPS, "traffic": None,
                     "kernel": "simt_gemm (pass over A, FP32 FMA)",
@@ -290,7 +290,10 @@ def main():
                                  "peak_source": peak_kind}}
     else:
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved_gbs / hbm, "traffic": None, "peak_source": peak_kind}
+                    "frac": achieved_gbs / hbm, "traffic": None, "peak_source": peak_kind,
+                    "kernel": "tc_pass_kernel (pass over A, tcgen05 3xTF32)",
+                    "tensor_view": {"achieved_tflops_algorithmic": achieved_tflops,
+                                    "tf32_flops_issued_per_algorithmic": 3.0 * (((l + 15) // 16) * 16) / l}}
 
     # ---------------- end to end through the host-buffer entry point ----------------
     e2e = None
@@ -326,7 +329,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl["desc"], "m": m, "n": n, "k": k, "p": wl["p"], "q": wl["q"], "l": l,
-                           "prec": args.prec, "engine": engine, "passes_over_A": passes,
+                           "prec": args.prec, "engine": engine, "engine_requested": args.engine,
+                           "passes_over_A": passes,
                            "l2": "A (%.1f GB) larger than L2; no flush needed" % (a_bytes / 1e9),
                            "parallelism": f"replicas x{world}"},
                 "hbm_roofline": {"time_ms": roof_ms, "frac_of_step": roof_ms / ms_per_step,

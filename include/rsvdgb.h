@@ -92,7 +92,9 @@ typedef struct rsvdgb_info {
     double err2_QB;      /* ||A - Q B||_F^2 = fro2_A - fro2_B                  */
     double err2_k;       /* ||A - U_k S_k V_k^T||_F^2 = fro2_A - sum_k s_i^2   */
     int32_t breakdowns;  /* Cholesky breakdowns met (each retried with a shift) */
-    int32_t reserved[7];
+    int32_t engine;      /* kernel family that ran the passes: RSVDGB_ENGINE_SIMT or _TC */
+    int32_t jacobi_sweeps; /* sweeps of the one-sided Jacobi SVD of the l x l factor */
+    int32_t reserved[5];
 } rsvdgb_info;
 
 /* Create a handle bound to CUDA device `device` and stream `cuda_stream`

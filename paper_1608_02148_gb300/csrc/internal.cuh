@@ -80,10 +80,26 @@ void launch_reduce_splits(cudaStream_t s, const float* part, int splits, int64_t
 // fro2 (optional) accumulates ||A||_F^2.  Device errors go to *status.
 // ---------------------------------------------------------------------------
 bool tc_pass_supported(int64_t m, int64_t n, int64_t lda, int l_pad, const void* A, int a_bf16);
-int launch_tc_pass(cudaStream_t s, int sm_count, bool trans, const float* A, int64_t m, int64_t n, int64_t lda,
+// General form: A is the stored row-major m x n FP32 matrix (lda); with
+// trans = false the kernel forms A P (lanes = rows of A, K = n), with
+// trans = true A^T P (lanes = columns of A, K = m).  The panel P (K x l_pad)
+// is given column-major as TF32 hi/lo parts.  K is split into want_splits
+// ranges (<= 0: automatic).  With one split and out != null the result goes
+// straight to out (column-major, ld_out) and to out_hi/out_lo if given, and
+// *splits_out is 0; otherwise the splits write partials (l_pad x ld_out each,
+// consecutive partials l_pad*ld_out apart) to `partial`, and *splits_out is
+// the count to reduce.  fro2 (optional) accumulates ||A||_F^2.  With
+// out_rowmajor (direct output only) out is written row-major:
+// out[idx * ld_out + j] for j < out_cols.
+int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int64_t m, int64_t n, int64_t lda,
                    const float* Phi, const float* Plo, int64_t ldp, int l_pad, float* out, float* out_hi,
-                   float* out_lo, int64_t ld_out, float* partial, int64_t* splits_out, int* status, double* fro2);
+                   float* out_lo, int64_t ld_out, float* partial, int64_t want_splits, int64_t* splits_out,
+                   int* status, double* fro2, int out_rowmajor = 0, int out_cols = 0);
 int64_t tc_pass_max_splits(int64_t m, int64_t n, int l_pad, int sm_count);
+int64_t tc_split_count(int64_t k_total, int64_t units, int sm_count);
+// l x l row-major T -> column-major L x L TF32 hi/lo panel (zero padded),
+// i.e. out[j * L + c] = T[c * l + j].
+void launch_small_panel(cudaStream_t s, const float* T, int l, int L, float* hi, float* lo);
 // TF32 split of a column-major rows x l matrix (ld) into hi + lo parts over
 // l_pad columns; rows >= rows and columns >= l are written as zero.
 void launch_split_tf32(cudaStream_t s, const float* in, int64_t ld, int64_t rows, int l, int l_pad, float* hi,
@@ -107,14 +123,16 @@ void launch_small_matmul(cudaStream_t s, const float* A, const float* B, float* 
 //   sigma[l] (FP32), Ut (l x l row-major, Ut[:,c] = W[:,c] / sigma_c),
 //   Jt (l x l row-major, the accumulated rotations, column c = right vector).
 // Also writes the first k values to d (float) and sum-of-squares diagnostics.
-void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, float* Ut, float* Jt, float* work);
+void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, float* Ut, float* Jt, float* work,
+                       int* sweeps);
 // FP64 -> FP32 copy of an l x l row-major matrix, optionally transposed.
 void launch_small_d2f(cudaStream_t s, const double* in, float* out, int l, bool transpose);
 // Transpose an l x l row-major matrix: out = in^T.
 void launch_small_transpose(cudaStream_t s, const float* in, float* out, int l);
 // d[0..k) = sigma[0..k); info fields from fro2_A and sigma.
 void launch_finalize_info(cudaStream_t s, const float* sigma, int l, int k, float* d, const double* fro2A,
-                          const int* status, const int* breakdowns, int q, int p_used, rsvdgb_info* info);
+                          const int* status, const int* breakdowns, int q, int p_used, int engine,
+                          const int* sweeps, rsvdgb_info* info);
 // Raise the dynamic shared-memory limit of the one-CTA kernels on the
 // current device (called once per handle).
 int init_small_kernels();

@@ -95,9 +95,10 @@ struct Geom {
 struct Work {
     float *Pt, *Yt, *Qt, *Wt, *Zt, *part;
     float *Pth, *Ptl, *Yth, *Ytl;  // TF32 hi/lo parts of the panels (tensor-core engine)
+    float *Qth, *Qtl, *Th, *Tl;    // hi/lo of the first CholeskyQR2 basis and of a small factor
     double* G;
     float *T1, *T2, *T, *R1, *R2, *RB, *M, *sigma, *Ut, *Jt, *jwork;
-    int *status, *breakdowns;
+    int *status, *breakdowns, *sweeps;
     double* fro2;
 };
 
@@ -126,6 +127,8 @@ size_t partial_floats(const Geom& g, int sm_count)
         // tensor-core A^T-side kernel on the stored matrix: lanes = stored columns
         const int64_t s_tc = tc_pass_max_splits(g.sm(), g.sn(), g.L, sm_count);
         need = std::max<int64_t>(need, s_tc * L * std::max(g.ldm, g.ldn));
+        // tensor-core Gram: at most one split per SM, L x L each
+        need = std::max<int64_t>(need, (int64_t)sm_count * L * L);
     }
     return (size_t)need;
 }
@@ -136,12 +139,16 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w)
     w.Pt = c.take<float>(L * g.ldn);
     w.Yt = c.take<float>(L * g.ldm);
     w.Qt = c.take<float>(L * g.ldm);
-    w.Pth = w.Ptl = w.Yth = w.Ytl = nullptr;
+    w.Pth = w.Ptl = w.Yth = w.Ytl = w.Qth = w.Qtl = w.Th = w.Tl = nullptr;
     if (g.use_tc) {
         w.Pth = c.take<float>(L * g.ldn);
         w.Ptl = c.take<float>(L * g.ldn);
         w.Yth = c.take<float>(L * g.ldm);
         w.Ytl = c.take<float>(L * g.ldm);
+        w.Qth = c.take<float>(L * g.ldm);
+        w.Qtl = c.take<float>(L * g.ldm);
+        w.Th = c.take<float>(L * L);
+        w.Tl = c.take<float>(L * L);
     }
     w.Wt = c.take<float>(L * g.ldn);
     w.Zt = c.take<float>(L * g.ldn);
@@ -160,6 +167,7 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w)
     w.jwork = c.take<float>(2 * (L + 2) * (L + 2));
     w.status = c.take<int>(1);
     w.breakdowns = c.take<int>(1);
+    w.sweeps = c.take<int>(1);
     w.fro2 = c.take<double>(1);
 }
 
@@ -269,16 +277,37 @@ void pass_over_A(rsvdgb_handle* h, const Geom& g, Work& w, bool A_side, const fl
     // Tensor-core engine.  The kernel's lanes are stored rows (A X kernel) or
     // stored columns (A^T X kernel, K split across CTAs, partials reduced).
     const bool stored_atx = (A_side == g.trans);
-    int64_t splits = 1;
+    int64_t splits = 0;
     prof_mark(h, true, 0);
-    launch_tc_pass(s, h->sm_count, stored_atx, (const float*)g.A, g.sm(), g.sn(), g.lda, Ph, Pl, ldP, g.L,
-                   stored_atx ? nullptr : out, stored_atx ? nullptr : out_h, stored_atx ? nullptr : out_l, ldO,
-                   w.part, &splits, w.status, fro2);
+    launch_tc_gemm(s, h->sm_count, stored_atx, (const float*)g.A, g.sm(), g.sn(), g.lda, Ph, Pl, ldP, g.L, out, out_h,
+                   out_l, ldO, w.part, stored_atx ? 0 : 1, &splits, w.status, fro2);
     prof_mark(h, false, a_bytes(g));
-    if (stored_atx) {
+    if (splits > 0) {
         launch_reduce_splits(s, w.part, (int)splits, (int64_t)g.L * ldO, g.l, rows, ldO, out, nullptr, ldO);
         if (out_h) launch_split_tf32(s, out, ldO, rows, g.l, g.L, out_h, out_l);
     }
+}
+
+// G (l x l, FP64) = X^T X for a column-major rows x l matrix given as X and its
+// TF32 hi/lo parts, on the tensor cores (3xTF32, K split over the rows).
+void tc_gram(rsvdgb_handle* h, const Geom& g, Work& w, const float* Xt, const float* Xh, const float* Xl, int64_t ld,
+             int64_t rows)
+{
+    int64_t splits = 0;
+    launch_tc_gemm(h->stream, h->sm_count, false, Xt, g.L, rows, ld, Xh, Xl, ld, g.L, nullptr, nullptr, nullptr, g.L,
+                   w.part, 0, &splits, w.status, nullptr);
+    launch_reduce_splits(h->stream, w.part, (int)splits, (int64_t)g.L * g.L, g.l, g.l, g.L, nullptr, w.G, g.l);
+}
+
+// Z = X T (rows x l, column-major, with TF32 hi/lo parts) for a column-major
+// rows x l matrix X and an l x l row-major T, on the tensor cores.
+void tc_times_small(rsvdgb_handle* h, const Geom& g, Work& w, const float* Xt, int64_t ld, int64_t rows,
+                    const float* T, float* Zt, float* Zh, float* Zl)
+{
+    launch_small_panel(h->stream, T, g.l, g.L, w.Th, w.Tl);
+    int64_t splits = 0;
+    launch_tc_gemm(h->stream, h->sm_count, true, Xt, g.L, rows, ld, w.Th, w.Tl, g.L, g.L, Zt, Zh, Zl, ld, nullptr, 1,
+                   &splits, w.status, nullptr);
 }
 
 // Y = A_logical X with X = Pt (n x l) -> Yt (m x l) [+ TF32 split of Y]
@@ -383,7 +412,10 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
     split_panel(s, g, w);
     // step 3: Y = A Omega, with ||A||_F^2 accumulated on the way
     apply_A(h, g, w, w.fro2);
-    gram(s, sm, w.Yt, g.ldm, g.m, l, w.part, w.G);
+    if (g.use_tc)
+        tc_gram(h, g, w, w.Yt, w.Yth, w.Ytl, g.ldm, g.m);
+    else
+        gram(s, sm, w.Yt, g.ldm, g.m, l, w.part, w.G);
     // step 4: subspace iterations
     for (int it = 0; it < q; ++it) {
         // Q = qr(Y): only the span is carried forward, so one Cholesky step
@@ -396,16 +428,26 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
         split_panel(s, g, w);
         // Y = A Q
         apply_A(h, g, w, nullptr);
-        gram(s, sm, w.Yt, g.ldm, g.m, l, w.part, w.G);
+        if (g.use_tc)
+            tc_gram(h, g, w, w.Yt, w.Yth, w.Ytl, g.ldm, g.m);
+        else
+            gram(s, sm, w.Yt, g.ldm, g.m, l, w.part, w.G);
     }
     // step 9: Q = qr(Y) with CholeskyQR2 (the first Gram is already in G):
     // Y1 = Y T1, G = Y1^T Y1, Q = Y1 T2.  Q ends up in Yt.
     launch_chol_inv(s, w.G, l, 0.f, nullptr, w.T1, w.status, w.breakdowns);
-    times_small(s, sm, w.Yt, g.ldm, g.m, l, w.T1, w.Qt, w.part);
-    gram(s, sm, w.Qt, g.ldm, g.m, l, w.part, w.G);
+    if (g.use_tc) {
+        tc_times_small(h, g, w, w.Yt, g.ldm, g.m, w.T1, w.Qt, w.Qth, w.Qtl);
+        tc_gram(h, g, w, w.Qt, w.Qth, w.Qtl, g.ldm, g.m);
+    } else {
+        times_small(s, sm, w.Yt, g.ldm, g.m, l, w.T1, w.Qt, w.part);
+        gram(s, sm, w.Qt, g.ldm, g.m, l, w.part, w.G);
+    }
     launch_chol_inv(s, w.G, l, 0.f, nullptr, w.T2, w.status, w.breakdowns);
-    times_small(s, sm, w.Qt, g.ldm, g.m, l, w.T2, w.Yt, w.part);
-    if (g.use_tc) launch_split_tf32(s, w.Yt, g.ldm, g.m, l, g.L, w.Yth, w.Ytl);
+    if (g.use_tc)
+        tc_times_small(h, g, w, w.Qt, g.ldm, g.m, w.T2, w.Yt, w.Yth, w.Ytl);
+    else
+        times_small(s, sm, w.Qt, g.ldm, g.m, l, w.T2, w.Yt, w.part);
     // step 10: B^T = A^T Q (n x l, column-major: row j of B is contiguous)
     apply_At(h, g, w);
     if (o.Qrow) launch_colmajor_to_rowmajor(s, w.Yt, g.ldm, g.m, l, o.Qrow, o.ldq);
@@ -420,11 +462,19 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
         cholqr2(s, sm, w, w.Wt, g.ldn, g.n, l, w.Zt, w.Pt);
         cross_gram(s, sm, w.Pt, w.Wt, g.ldn, g.n, l, w.part, w.G);
         launch_small_d2f(s, w.G, w.M, l, true);
-        launch_jacobi_svd(s, w.M, l, w.sigma, w.Ut, w.Jt, w.jwork);
+        launch_jacobi_svd(s, w.M, l, w.sigma, w.Ut, w.Jt, w.jwork, w.sweeps);
         // U = Q Ut (Eq. UQU) and V = Q_B J, truncated
-        if (o.nU > 0)
-            tall_gemm(s, sm, true, false, false, w.Yt, g.ldm, 0, w.Ut, l, o.U, o.ldU, g.m, o.nU, l, w.part,
-                      nullptr);
+        if (o.nU > 0) {
+            if (g.use_tc) {
+                launch_small_panel(s, w.Ut, l, g.L, w.Th, w.Tl);
+                int64_t splits = 0;
+                launch_tc_gemm(s, sm, true, w.Yt, g.L, g.m, g.ldm, w.Th, w.Tl, g.L, g.L, o.U, nullptr, nullptr, o.ldU,
+                               nullptr, 1, &splits, w.status, nullptr, 1, o.nU);
+            } else {
+                tall_gemm(s, sm, true, false, false, w.Yt, g.ldm, 0, w.Ut, l, o.U, o.ldU, g.m, o.nU, l, w.part,
+                          nullptr);
+            }
+        }
         if (o.nV > 0)
             tall_gemm(s, sm, true, false, false, w.Pt, g.ldn, 0, w.Jt, l, o.V, o.ldV, g.n, o.nV, l, w.part,
                       nullptr);
@@ -433,7 +483,7 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
         // through a cheap Gram of B (sigma unused).
     }
     launch_finalize_info(s, o.d ? w.sigma : nullptr, o.d ? l : 0, k, o.d, w.fro2, w.status, w.breakdowns, q,
-                         l - k, o.info);
+                         l - k, g.use_tc ? RSVDGB_ENGINE_TC : RSVDGB_ENGINE_SIMT, o.d ? w.sweeps : nullptr, o.info);
     RSVDGB_CUDA_TRY(cudaGetLastError());
     return RSVDGB_OK;
 }
@@ -748,11 +798,11 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
     RSVDGB_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
     launch_rowmajor_to_colmajor(s, X, ldx, K, l, L, Xc, ldK);
     launch_split_tf32(s, Xc, ldK, K, l, L, Xh, Xl);
-    int64_t used = 1;
-    rc = launch_tc_pass(s, h->sm_count, transpose, (const float*)A, m, n, lda, Xh, Xl, ldK, L,
-                        transpose ? nullptr : Yc, nullptr, nullptr, ldM, part, &used, status, nullptr);
+    int64_t used = 0;
+    rc = launch_tc_gemm(s, h->sm_count, transpose, (const float*)A, m, n, lda, Xh, Xl, ldK, L, Yc, nullptr, nullptr,
+                        ldM, part, transpose ? 0 : 1, &used, status, nullptr);
     if (rc) return rc;
-    if (transpose) launch_reduce_splits(s, part, (int)used, (int64_t)L * ldM, l, M, ldM, Yc, nullptr, ldM);
+    if (used > 0) launch_reduce_splits(s, part, (int)used, (int64_t)L * ldM, l, M, ldM, Yc, nullptr, ldM);
     launch_colmajor_to_rowmajor(s, Yc, ldM, M, l, Y, ldy);
     RSVDGB_CUDA_TRY(cudaGetLastError());
     return RSVDGB_OK;

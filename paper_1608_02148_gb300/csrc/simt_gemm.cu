@@ -149,8 +149,17 @@ __global__ void reduce_splits_kernel(const float* __restrict__ part, int splits,
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= rows * cols) return;
     const int64_t r = e / cols, c = e % cols;
-    double acc = 0.0;
-    for (int sidx = 0; sidx < splits; ++sidx) acc += (double)part[sidx * split_stride + r * ld + c];
+    const float* src = part + r * ld + c;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int sidx = 0;
+    for (; sidx + 3 < splits; sidx += 4) {
+        a0 += (double)src[(sidx + 0) * split_stride];
+        a1 += (double)src[(sidx + 1) * split_stride];
+        a2 += (double)src[(sidx + 2) * split_stride];
+        a3 += (double)src[(sidx + 3) * split_stride];
+    }
+    for (; sidx < splits; ++sidx) a0 += (double)src[sidx * split_stride];
+    const double acc = (a0 + a1) + (a2 + a3);
     if (out32) out32[r * ld_out + c] = (float)acc;
     if (out64) out64[r * ld_out + c] = acc;
 }
@@ -177,7 +186,7 @@ void launch_reduce_splits(cudaStream_t s, const float* part, int splits, int64_t
 {
     const int64_t total = rows * cols;
     if (total == 0) return;
-    reduce_splits_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(part, splits, split_stride, rows, cols, ld,
+    reduce_splits_kernel<<<(unsigned)ceil_div(total, 64), 64, 0, s>>>(part, splits, split_stride, rows, cols, ld,
                                                                           out32, out64, ld_out); count_launches();
 }
 

@@ -24,108 +24,131 @@ constexpr int kSmallThreads = 1024;
 // ---------------------------------------------------------------------------
 // Cholesky by symmetric Gaussian elimination on [G | I].
 //
-// Step j scales pivot row j by 1/sqrt(pivot) and eliminates column j from the
-// rows below.  The G half turns into R (upper triangle) and the I half into
-// R^{-T} (lower triangle), so R^{-1} = (R^{-T})^T comes out of the same l
-// steps.  Both halves share one l x l array: R in the upper triangle
-// including the diagonal, R^{-T} strictly below it, its diagonal in dinv.
+// Step j eliminates column j from the rows below with the pivot row j, then
+// scales row j by 1/sqrt(pivot).  The G half turns into R (upper triangle)
+// and the I half into R^{-T} (lower triangle), so R^{-1} = (R^{-T})^T comes out
+// of the same l steps.  Both halves share one l x l array: R in the upper
+// triangle including the diagonal, R^{-T} strictly below it, its diagonal in
+// dinv.
+//
+// The array lives in registers: 1024 threads form a 32 x 32 grid and thread
+// (ty, tx) owns rows ty + 32 i and columns tx + 32 j (NB x NB elements,
+// NB = ceil(l / 32) <= 7).  Step j publishes the unscaled pivot row through a
+// double-buffered shared vector, so each step costs one barrier.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSmallThreads)
+template <int NB, int TD>  // TD x TD threads, NB x NB elements each (TD * NB >= l)
+__global__ void __launch_bounds__(TD * TD)
     chol_inv_kernel(const double* __restrict__ G, int l, float shift_rel, float* __restrict__ R,
                     float* __restrict__ T, int* status, int* breakdowns)
 {
-    extern __shared__ float S[];  // l * l
+    constexpr int kCholThreads = TD * TD;
+    __shared__ float rowbuf[2][256];
     __shared__ float dinv[256];
-    __shared__ float piv;
     __shared__ float maxdiag;
-    __shared__ int broke;
     const int tid = threadIdx.x;
-    const int nth = blockDim.x;
+    const int tx = tid % TD, ty = tid / TD;
 
-    if (tid == 0) {
+    if (tid < 32) {
         float md = 0.f;
-        for (int a = 0; a < l; ++a) md = fmaxf(md, (float)G[a * l + a]);
-        maxdiag = md;
-        broke = 0;
+        for (int a = tid; a < l; a += 32) md = fmaxf(md, (float)G[a * l + a]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+        if (tid == 0) maxdiag = md;
     }
     __syncthreads();
 
+    float S[NB][NB];
     for (int attempt = 0; attempt < 4; ++attempt) {
         // shift = shift_rel * max diag on the first attempt; after a breakdown
         // the shift grows by 100x per retry (shifted CholeskyQR).
         float shift = shift_rel * maxdiag;
         if (attempt > 0) shift = fmaxf(shift, maxdiag * 1e-6f * powf(100.f, (float)(attempt - 1)));
-        for (int e = tid; e < l * l; e += nth) {
-            const int a = e / l, b = e % l;
-            float v;
-            if (b >= a)
-                v = (float)G[a * l + b] + (a == b ? shift : 0.f);
-            else
-                v = 0.f;  // the I half starts as the identity (diagonal kept in dinv)
-            S[e] = v;
-        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+            for (int jj = 0; jj < NB; ++jj) {
+                const int a = ty + TD * i, b = tx + TD * jj;
+                float v = 0.f;
+                if (a < l && b < l && b >= a) v = (float)G[a * l + b] + (a == b ? shift : 0.f);
+                S[i][jj] = v;
+            }
+        // publish row 0
+        if (ty == 0)
+#pragma unroll
+            for (int jj = 0; jj < NB; ++jj) rowbuf[0][tx + TD * jj] = S[0][jj];
         __syncthreads();
         bool failed = false;
         for (int j = 0; j < l; ++j) {
-            if (tid == 0) {
-                const float p = S[j * l + j];
-                if (!(p > 0.f) || !isfinite(p)) {
-                    broke = 1;
-                    piv = 1.f;
-                } else {
-                    piv = sqrtf(p);
-                }
-            }
-            __syncthreads();
-            if (broke) {
-                failed = true;
+            const float* u = rowbuf[j & 1];
+            const float pv = u[j];
+            if (!(pv > 0.f) || !isfinite(pv)) {
+                failed = true;  // every thread reads the same pivot
                 break;
             }
-            const float r = piv;
-            const float rinv = 1.0f / r;
-            for (int c = tid; c < l; c += nth) {
-                if (c == j)
-                    S[j * l + j] = r;
-                else
-                    S[j * l + c] *= rinv;  // c > j: R(j,c); c < j: R^{-T}(j,c)
+            // one approximate reciprocal square root per step (relative error
+            // a few ulps, far below the FP32 error the factor already carries)
+            const float rinv = rsqrtf(pv);
+            const float r = pv * rinv;
+            const float pinv = rinv * rinv;
+            float ub[NB];
+#pragma unroll
+            for (int jj = 0; jj < NB; ++jj) {
+                const int b = tx + TD * jj;
+                ub[jj] = (b == j) ? 1.0f : ((b < l) ? u[b] : 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                const int a = ty + TD * i;
+                if (a > j && a < l) {
+                    const float f = u[a] * pinv;
+#pragma unroll
+                    for (int jj = 0; jj < NB; ++jj) {
+                        const int b = tx + TD * jj;
+                        if (b >= a || b <= j) S[i][jj] -= f * ub[jj];
+                    }
+                } else if (a == j) {
+                    // scale the pivot row: R(j, b) for b >= j, R^{-T}(j, b) for b < j
+#pragma unroll
+                    for (int jj = 0; jj < NB; ++jj) {
+                        const int b = tx + TD * jj;
+                        S[i][jj] = (b == j) ? r : S[i][jj] * rinv;
+                    }
+                }
             }
             if (tid == 0) dinv[j] = rinv;
-            __syncthreads();
-            // eliminate column j from rows a > j
-            const int rows = l - j - 1;
-            for (int e = tid; e < rows * l; e += nth) {
-                const int a = j + 1 + e / l;
-                const int b = e % l;
-                const float mult = S[j * l + a];  // R(j, a)
-                if (b >= a) {
-                    S[a * l + b] -= mult * S[j * l + b];
-                } else if (b <= j) {
-                    const float lj = (b == j) ? dinv[j] : S[j * l + b];
-                    S[a * l + b] -= mult * lj;
-                }
+            // publish row j + 1 (its owners have just finished their update)
+            if (j + 1 < l && ty == ((j + 1) % TD)) {
+                const int i1 = (j + 1) / TD;
+#pragma unroll
+                for (int i = 0; i < NB; ++i)
+                    if (i == i1)
+#pragma unroll
+                        for (int jj = 0; jj < NB; ++jj) rowbuf[(j + 1) & 1][tx + TD * jj] = S[i][jj];
             }
             __syncthreads();
         }
         if (!failed) break;
         __syncthreads();
         if (tid == 0) {
-            broke = 0;
             if (breakdowns) atomicAdd(breakdowns, 1);
             if (attempt == 3 && status) *status = RSVDGB_ERR_BREAKDOWN;
         }
         __syncthreads();
     }
-    for (int e = tid; e < l * l; e += nth) {
-        const int a = e / l, b = e % l;
-        if (R) R[e] = (b >= a) ? S[e] : 0.f;
-        // T = R^{-1} = (R^{-T})^T: T(a, b) = R^{-T}(b, a) for a <= b
-        float t = 0.f;
-        if (a == b)
-            t = dinv[a];
-        else if (a < b)
-            t = S[b * l + a];
-        T[e] = t;
-    }
+    // R (upper) straight from the registers; T = R^{-1} = (R^{-T})^T needs the
+    // transpose of the lower part, so that goes through global memory order:
+    // T(b, a) = R^{-T}(a, b) for b < a, T(a, a) = dinv[a].
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+        for (int jj = 0; jj < NB; ++jj) {
+            const int a = ty + TD * i, b = tx + TD * jj;
+            if (a >= l || b >= l) continue;
+            if (R) R[a * l + b] = (b >= a) ? S[i][jj] : 0.f;
+            if (b < a) T[b * l + a] = S[i][jj];
+            else if (b == a) T[a * l + a] = dinv[a];
+            else T[b * l + a] = 0.f;  // T is upper triangular: zero below the diagonal
+        }
 }
 
 __global__ void small_matmul_kernel(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C,
@@ -168,9 +191,12 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-__global__ void __launch_bounds__(kSmallThreads)
+// EPL = ceil(L / 16): column elements per half-warp lane, held in registers
+// while a pair is rotated.
+template <int EPL, int NT>
+__global__ void __launch_bounds__(NT)
     jacobi_kernel(const float* __restrict__ M, int l, int L, float* __restrict__ sigma, float* __restrict__ Ut,
-                  float* __restrict__ Jt, float* __restrict__ gwork, int use_smem)
+                  float* __restrict__ Jt, float* __restrict__ gwork, int use_smem, int* sweeps_out)
 {
     extern __shared__ float sm[];
     float* Mc = use_smem ? sm : gwork;
@@ -178,61 +204,85 @@ __global__ void __launch_bounds__(kSmallThreads)
     __shared__ int rotated;
     __shared__ float sv[256];
     __shared__ int rank[256];
+    __shared__ float jn[256];
+    __shared__ float wn[256];
     const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int nwarps = NT / 32;
+    const int half = lane >> 4, hl = lane & 15;  // half-warp: one column pair
 
     // column-major copies, zero padded to L x L
-    for (int e = tid; e < L * L; e += blockDim.x) {
+    for (int e = tid; e < L * L; e += NT) {
         const int c = e / L, i = e % L;
         Mc[e] = (i < l && c < l) ? M[i * l + c] : 0.f;
         Jc[e] = (i == c) ? 1.f : 0.f;
     }
     __syncthreads();
 
-    const float tol = 3e-7f;
-    for (int sweep = 0; sweep < 40; ++sweep) {
+    // rotate a pair only when its cosine exceeds the FP32 noise of the dot
+    // products (about sqrt(L) u32); quadratic convergence does the rest.
+    // Rotations use fast reciprocal / square-root intrinsics: c^2 + s^2 = 1
+    // only to a few ulps, a scaling that hits a column of M and the same
+    // column of J alike and is divided out at the end.
+    const float tol = 4.f * sqrtf((float)L) * 5.9604645e-8f;
+    const int Lm1 = L - 1;
+    int sweep = 0;
+    for (; sweep < 30; ++sweep) {
         if (tid == 0) rotated = 0;
         __syncthreads();
-        for (int round = 0; round < L - 1; ++round) {
-            for (int t = warp; t < L / 2; t += nwarps) {
-                int a, b;
-                if (t == 0) {
-                    a = L - 1;
-                    b = round;
-                } else {
-                    a = (round + t) % (L - 1);
-                    b = (round - t + L - 1) % (L - 1);
+        for (int round = 0; round < Lm1; ++round) {
+            for (int base = 2 * warp; base < L / 2; base += 2 * nwarps) {
+                const int t = base + half;
+                const bool valid = t < L / 2;
+                int a = Lm1, b = round;
+                if (t != 0) {
+                    a = round + t;
+                    if (a >= Lm1) a -= Lm1;
+                    b = round - t;
+                    if (b < 0) b += Lm1;
                 }
-                float* ma = Mc + (size_t)a * L;
-                float* mb = Mc + (size_t)b * L;
+                float xa[EPL], xb[EPL];
                 float al = 0.f, be = 0.f, ga = 0.f;
-                for (int i = lane; i < L; i += 32) {
-                    const float x = ma[i], y = mb[i];
-                    al = fmaf(x, x, al);
-                    be = fmaf(y, y, be);
-                    ga = fmaf(x, y, ga);
-                }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                ga = warp_sum(ga);
-                if (ga != 0.f && fabsf(ga) > tol * sqrtf(al * be)) {
-                    const float zeta = (be - al) / (2.f * ga);
-                    const float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-                    const float c = 1.0f / sqrtf(1.f + tt * tt);
-                    const float s = c * tt;
-                    for (int i = lane; i < L; i += 32) {
-                        const float x = ma[i], y = mb[i];
-                        ma[i] = c * x - s * y;
-                        mb[i] = s * x + c * y;
+                if (valid) {
+                    const float* ma = Mc + (size_t)a * L;
+                    const float* mb = Mc + (size_t)b * L;
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) {
+                        const int i = hl + 16 * e;
+                        xa[e] = (i < L) ? ma[i] : 0.f;
+                        xb[e] = (i < L) ? mb[i] : 0.f;
+                        al = fmaf(xa[e], xa[e], al);
+                        be = fmaf(xb[e], xb[e], be);
+                        ga = fmaf(xa[e], xb[e], ga);
                     }
+                }
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) {
+                    al += __shfl_xor_sync(0xffffffffu, al, o);
+                    be += __shfl_xor_sync(0xffffffffu, be, o);
+                    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                }
+                if (valid && ga != 0.f && fabsf(ga) > tol * sqrtf(al * be)) {
+                    const float zeta = __fdividef(be - al, 2.f * ga);
+                    const float tt = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+                    const float c = rsqrtf(fmaf(tt, tt, 1.f));
+                    const float sn = c * tt;
+                    float* ma = Mc + (size_t)a * L;
+                    float* mb = Mc + (size_t)b * L;
                     float* ja = Jc + (size_t)a * L;
                     float* jb = Jc + (size_t)b * L;
-                    for (int i = lane; i < L; i += 32) {
-                        const float x = ja[i], y = jb[i];
-                        ja[i] = c * x - s * y;
-                        jb[i] = s * x + c * y;
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) {
+                        const int i = hl + 16 * e;
+                        if (i < L) {
+                            ma[i] = c * xa[e] - sn * xb[e];
+                            mb[i] = sn * xa[e] + c * xb[e];
+                            const float ya = ja[i], yb = jb[i];
+                            ja[i] = c * ya - sn * yb;
+                            jb[i] = sn * ya + c * yb;
+                        }
                     }
-                    if (lane == 0) rotated = 1;
+                    if (hl == 0) rotated = 1;
                 }
             }
             __syncthreads();
@@ -240,12 +290,9 @@ __global__ void __launch_bounds__(kSmallThreads)
         if (!rotated) break;
         __syncthreads();
     }
-    // Singular values.  A rotation computed in FP32 is orthogonal only to
-    // rounding, so after many rotations a column of W = M J and the matching
-    // column of J carry the same small scale drift; sigma_c = ||W_c|| / ||J_c||
-    // cancels it, and J_c is renormalised.
-    __shared__ float jn[256];
-    __shared__ float wn[256];
+    if (tid == 0 && sweeps_out) *sweeps_out = sweep + 1;
+    // Singular values.  sigma_c = ||W_c|| / ||J_c|| with W = M J divides out
+    // the common scale drift of a column of W and of J; J_c is renormalised.
     for (int c = warp; c < L; c += nwarps) {
         float s2 = 0.f, j2 = 0.f;
         for (int i = lane; i < L; i += 32) {
@@ -261,13 +308,13 @@ __global__ void __launch_bounds__(kSmallThreads)
         }
     }
     __syncthreads();
-    for (int c = tid; c < L; c += blockDim.x) {
+    for (int c = tid; c < L; c += NT) {
         int r = 0;
         for (int o = 0; o < L; ++o) r += (sv[o] > sv[c]) || (sv[o] == sv[c] && o < c);
         rank[c] = r;
     }
     __syncthreads();
-    for (int e = tid; e < L * L; e += blockDim.x) {
+    for (int e = tid; e < L * L; e += NT) {
         const int c = e / L, i = e % L;
         const int r = rank[c];
         if (r >= l || i >= l) continue;
@@ -275,13 +322,13 @@ __global__ void __launch_bounds__(kSmallThreads)
         Ut[i * l + r] = (w > 0.f) ? Mc[(size_t)c * L + i] / w : 0.f;
         Jt[i * l + r] = (jn[c] > 0.f) ? Jc[(size_t)c * L + i] / jn[c] : 0.f;
     }
-    for (int c = tid; c < L; c += blockDim.x)
+    for (int c = tid; c < L; c += NT)
         if (rank[c] < l) sigma[rank[c]] = sv[c];
 }
 
 __global__ void finalize_info_kernel(const float* __restrict__ sigma, int l, int k, float* __restrict__ d,
                                      const double* fro2A, const int* status, const int* breakdowns, int q,
-                                     int p_used, rsvdgb_info* info)
+                                     int p_used, int engine, const int* sweeps, rsvdgb_info* info)
 {
     const int tid = threadIdx.x;
     if (d && sigma)
@@ -305,6 +352,8 @@ __global__ void finalize_info_kernel(const float* __restrict__ sigma, int l, int
         info->err2_QB = fa - sb;
         info->err2_k = fa - sk;
         info->breakdowns = breakdowns ? *breakdowns : 0;
+        info->engine = engine;
+        info->jacobi_sweeps = sweeps ? *sweeps : 0;
     }
 }
 
@@ -335,6 +384,25 @@ __global__ void split_tf32_kernel(const float* __restrict__ in, int64_t ld, int6
     lo[o] = r;
 }
 
+__global__ void small_panel_kernel(const float* __restrict__ T, int l, int L, float* __restrict__ hi,
+                                   float* __restrict__ lo)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;  // K index (row of T)
+    const int j = blockIdx.y;                             // N index (column of T)
+    if (c >= L || j >= L) return;
+    float h = 0.f, r = 0.f;
+    if (c < l && j < l) {
+        const float x = T[c * l + j];
+        uint32_t hb, rb;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(x));
+        h = __uint_as_float(hb);
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(rb) : "f"(x - h));
+        r = __uint_as_float(rb);
+    }
+    hi[j * L + c] = h;
+    lo[j * L + c] = r;
+}
+
 __global__ void col_to_row_kernel(const float* __restrict__ in, int64_t ld, int64_t rows, int cols,
                                   float* __restrict__ out, int64_t ldo)
 {
@@ -358,8 +426,24 @@ __global__ void row_to_col_kernel(const float* __restrict__ in, int64_t ldi, int
 void launch_chol_inv(cudaStream_t s, const double* G, int l, float shift_rel, float* R, float* T, int* status,
                      int* breakdowns)
 {
-    const size_t smem = (size_t)l * l * sizeof(float);
-    chol_inv_kernel<<<1, kSmallThreads, smem, s>>>(G, l, shift_rel, R, T, status, breakdowns); count_launches();
+    // 16 x 16 threads while the register tile stays small, 32 x 32 beyond
+    if (l <= 16)
+        chol_inv_kernel<1, 16><<<1, 256, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
+    else if (l <= 32)
+        chol_inv_kernel<2, 16><<<1, 256, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
+    else if (l <= 64)
+        chol_inv_kernel<4, 16><<<1, 256, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
+    else if (l <= 96)
+        chol_inv_kernel<6, 16><<<1, 256, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
+    else if (l <= 128)
+        chol_inv_kernel<8, 16><<<1, 256, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
+    else if (l <= 160)
+        chol_inv_kernel<5, 32><<<1, 1024, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
+    else if (l <= 192)
+        chol_inv_kernel<6, 32><<<1, 1024, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
+    else
+        chol_inv_kernel<7, 32><<<1, 1024, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
+    count_launches();
 }
 
 namespace {
@@ -381,9 +465,19 @@ int init_small_kernels()
     if (cudaGetDevice(&dev) != cudaSuccess) return RSVDGB_ERR_CUDA;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return RSVDGB_ERR_CUDA;
-    int rc = raise_smem_limit(chol_inv_kernel, optin);
-    if (rc) return rc;
-    return raise_smem_limit(jacobi_kernel, optin);
+    int rc = RSVDGB_OK;
+    rc |= raise_smem_limit(jacobi_kernel<1, 1024>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<2, 1024>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<3, 1024>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<4, 1024>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<5, 1024>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<6, 1024>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<7, 1024>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<8, 1024>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<10, 512>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<12, 512>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<14, 512>, optin);
+    return rc ? RSVDGB_ERR_CUDA : RSVDGB_OK;
 }
 
 void launch_small_matmul(cudaStream_t s, const float* A, const float* B, float* C, int l)
@@ -408,18 +502,41 @@ void launch_small_transpose(cudaStream_t s, const float* in, float* out, int l)
     small_transpose_kernel<<<grid, block, 0, s>>>(in, out, l); count_launches();
 }
 
-void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, float* Ut, float* Jt, float* work)
+template <int EPL, int NT>
+void launch_jacobi_typed(cudaStream_t s, const float* M, int l, int L, float* sigma, float* Ut, float* Jt,
+                         float* work, int* sweeps)
 {
-    const int L = (int)round_up(l, 2);
     const size_t need = (size_t)2 * L * L * sizeof(float);
     const int use_smem = need <= (size_t)216 * 1024;
-    jacobi_kernel<<<1, kSmallThreads, use_smem ? need : 0, s>>>(M, l, L, sigma, Ut, Jt, work, use_smem); count_launches();
+    jacobi_kernel<EPL, NT><<<1, NT, use_smem ? need : 0, s>>>(M, l, L, sigma, Ut, Jt, work, use_smem, sweeps);
+}
+
+void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, float* Ut, float* Jt, float* work,
+                       int* sweeps)
+{
+    const int L = (int)round_up(l, 2);
+    switch ((L + 15) / 16) {
+        case 1: launch_jacobi_typed<1, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
+        case 2: launch_jacobi_typed<2, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
+        case 3: launch_jacobi_typed<3, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
+        case 4: launch_jacobi_typed<4, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
+        case 5: launch_jacobi_typed<5, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
+        case 6: launch_jacobi_typed<6, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
+        case 7: launch_jacobi_typed<7, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
+        case 8: launch_jacobi_typed<8, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
+        case 9: case 10: launch_jacobi_typed<10, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
+        case 11: case 12: launch_jacobi_typed<12, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
+        default: launch_jacobi_typed<14, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
+    }
+    count_launches();
 }
 
 void launch_finalize_info(cudaStream_t s, const float* sigma, int l, int k, float* d, const double* fro2A,
-                          const int* status, const int* breakdowns, int q, int p_used, rsvdgb_info* info)
+                          const int* status, const int* breakdowns, int q, int p_used, int engine, const int* sweeps,
+                          rsvdgb_info* info)
 {
-    finalize_info_kernel<<<1, 256, 0, s>>>(sigma, l, k, d, fro2A, status, breakdowns, q, p_used, info); count_launches();
+    finalize_info_kernel<<<1, 256, 0, s>>>(sigma, l, k, d, fro2A, status, breakdowns, q, p_used, engine, sweeps,
+                                           info); count_launches();
 }
 
 void launch_clear_scalars(cudaStream_t s, int* status, int* breakdowns, double* fro2)
@@ -432,6 +549,13 @@ void launch_split_tf32(cudaStream_t s, const float* in, int64_t ld, int64_t rows
 {
     dim3 grid((unsigned)ceil_div(ld, 256), (unsigned)l_pad);
     split_tf32_kernel<<<grid, 256, 0, s>>>(in, ld, rows, l, l_pad, hi, lo);
+    count_launches();
+}
+
+void launch_small_panel(cudaStream_t s, const float* T, int l, int L, float* hi, float* lo)
+{
+    dim3 grid((unsigned)ceil_div(L, 128), (unsigned)L);
+    small_panel_kernel<<<grid, 128, 0, s>>>(T, l, L, hi, lo);
     count_launches();
 }
 

@@ -17,10 +17,17 @@
 //     nearest of a, a_lo = TF32 of the remainder) and store both into TMEM,
 //     where the MMA reads its A operand (tcgen05.mma ... [a_tmem]);
 //   * three MMAs per K step, a_hi p_hi + a_hi p_lo + a_lo p_hi, accumulate in
-//     FP32; the dropped a_lo p_lo term and the TF32 rounding of the lo parts
-//     are below 2^-21 relative per product.
-// Roles (192 threads): warp 0 issues TMA, warp 1 allocates TMEM and issues
-// MMAs (one elected lane), warps 2..5 convert A and run the epilogue.  Every
+//     FP32.  a_hi is a with the low 13 mantissa bits cleared (exact TF32) and
+//     a_lo = a - a_hi (exact in FP32, |a_lo| < 2^-10 |a|); whether the tensor
+//     core rounds or truncates a_lo to TF32, and with the dropped a_lo p_lo
+//     term, each product is within 2^-19 |a||p| (p_hi, p_lo are split by
+//     round-to-nearest beforehand).
+// Roles (352 threads): warp 0 issues the TMA loads of A, warp 10 those of the
+// panel, warp 1 allocates TMEM and issues MMAs (one elected lane), warps 2..9
+// convert A and run the epilogue (two warps per TMEM lane quarter, each taking
+// half of the K columns).  A tiles and panel tiles sit in separate shared-
+// memory rings: an A tile is released as soon as it is converted, a panel
+// tile when the MMAs that read it complete.  Every
 // mbarrier wait is bounded; on expiry the kernel records RSVDGB_ERR_TIMEOUT,
 // stops issuing work, waits (bounded) for its copies and MMAs in flight, frees
 // its TMEM and returns.
@@ -34,7 +41,11 @@ namespace {
 
 constexpr int kBK = 32;            // K elements per stage (one 128-byte swizzle row)
 constexpr int kTileRows = 128;     // accumulator lanes
-constexpr int kThreads = 192;      // 6 warps
+constexpr int kConvWarps = 8;      // converter / epilogue warps (two per TMEM lane quarter)
+constexpr int kThreads = 128 + 32 * kConvWarps;  // + TMA(A), 2 x MMA, TMA(panel) warps
+constexpr int kMmaWarp1 = 3 + kConvWarps;        // second MMA issuer (odd groups)
+constexpr int kMaxAStages = 6;
+constexpr int kMaxPStages = 4;
 constexpr int kTmemStages = 2;     // A-operand buffers in TMEM
 constexpr long long kSpinLimit = 4000000000LL;  // clock64 ticks (about 2 s)
 
@@ -44,11 +55,14 @@ struct TcParams {
     int64_t num_tiles;     // 128-wide tiles along the lane dimension
     int64_t k_total;       // extent of K (n for AX, m for AtX)
     int64_t k_per_split;   // AtX: K rows per split (multiple of kBK); AX: k_total
-    int stages;            // shared-memory pipeline depth
+    int a_stages;          // shared-memory ring of A tiles (released by the converters)
+    int p_stages;          // shared-memory ring of panel tiles (released by the MMAs)
     float* out;            // AX: Yt (column-major, ld_out); AtX: partial base
     float* out_hi;         // AX: TF32 hi part of Y (may be null)
     float* out_lo;         // AX: TF32 lo part of Y (may be null)
     int64_t ld_out;
+    int out_rowmajor;      // direct output stored row-major: out[idx * ld_out + j], j < out_cols
+    int out_cols;
     int64_t split_stride;  // AtX: floats between partials
     int* status;
     double* fro2;          // if set: ||A||_F^2 is accumulated by the converters
@@ -169,6 +183,17 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
 }
 
 // 32 lanes x 32 bit, 16 consecutive columns per thread.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+// 32 lanes x 32 bit, 16 consecutive columns per thread.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
 {
     asm volatile(
@@ -184,7 +209,7 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ----------------------------------------------------------------- the kernel
-template <bool TRANS, int G>
+template <bool TRANS, int G, bool SQ>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_pass_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapPhi,
                    const __grid_constant__ CUtensorMap tmapPlo, TcParams p)
@@ -193,7 +218,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // 1024-byte aligned base for the swizzled tiles
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
 
-    __shared__ uint64_t full_bar[4], empty_bar[4];
+    __shared__ uint64_t afull_bar[kMaxAStages], aempty_bar[kMaxAStages];
+    __shared__ uint64_t pfull_bar[kMaxPStages], pempty_bar[kMaxPStages];
     __shared__ uint64_t conv_bar[kTmemStages], tfree_bar[kTmemStages];
     __shared__ uint64_t accf_bar, acce_bar;
     __shared__ uint32_t tmem_base_sh;
@@ -201,19 +227,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int S = p.stages;
+    const int SA = p.a_stages, SP = p.p_stages;
     const int l_pad = p.l_pad;
     const uint32_t a_tile_bytes = kTileRows * kBK * 4;         // 16 KB
     const uint32_t p_tile_bytes = (uint32_t)l_pad * kBK * 4;   // l_pad rows x 128 B
-    const uint32_t stage_bytes = G * a_tile_bytes + 2 * p_tile_bytes;
+    const uint32_t a_stage_bytes = G * a_tile_bytes;
+    const uint32_t p_stage_bytes = 2 * p_tile_bytes;
+    uint8_t* a_ring = smem;
+    uint8_t* p_ring = smem + (size_t)SA * a_stage_bytes;
 
     // ---- work of this CTA: a range of lane tiles and a K range
     int64_t tile_begin, tile_end, k_begin, k_end;
     if (!TRANS) {
         tile_begin = p.num_tiles * blockIdx.x / gridDim.x;
         tile_end = p.num_tiles * (blockIdx.x + 1) / gridDim.x;
-        k_begin = 0;
-        k_end = p.k_total;
+        k_begin = (int64_t)blockIdx.y * p.k_per_split;
+        k_end = min(p.k_total, k_begin + p.k_per_split);
     } else {
         tile_begin = (int64_t)blockIdx.x * G;
         tile_end = min(p.num_tiles, tile_begin + G);
@@ -231,16 +260,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     while (tmem_cols < need) tmem_cols <<= 1;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < S; ++s) {
-            mbar_init(&full_bar[s], 1);
-            mbar_init(&empty_bar[s], 1);
+        for (int s = 0; s < SA; ++s) {
+            mbar_init(&afull_bar[s], 1);
+            mbar_init(&aempty_bar[s], kConvWarps);
+        }
+        for (int s = 0; s < SP; ++s) {
+            mbar_init(&pfull_bar[s], 1);
+            mbar_init(&pempty_bar[s], 2);  // one commit per MMA issuer
         }
         for (int s = 0; s < kTmemStages; ++s) {
-            mbar_init(&conv_bar[s], 4);
-            mbar_init(&tfree_bar[s], 1);
+            mbar_init(&conv_bar[s], kConvWarps);
+            mbar_init(&tfree_bar[s], 2);
         }
-        mbar_init(&accf_bar, 1);
-        mbar_init(&acce_bar, 4);
+        mbar_init(&accf_bar, 2);
+        mbar_init(&acce_bar, kConvWarps);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -256,9 +289,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     tmem_fence_after();
     const uint32_t tmem = tmem_base_sh;
 
-    if (warp == 0) {
-        // =========================== TMA producer
+    if (warp == 0 || warp == 2 + kConvWarps) {
+        // =========================== TMA producers: A tiles (warp 0), panel tiles (last warp)
+        const bool is_a = (warp == 0);
         if (lane == 0) {
+            const int S = is_a ? SA : SP;
+            uint64_t* fullb = is_a ? afull_bar : pfull_bar;
+            uint64_t* emptyb = is_a ? aempty_bar : pempty_bar;
             int64_t it = 0;
             bool ok = true;
             for (int64_t set = 0; set < num_sets && ok; ++set) {
@@ -267,19 +304,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int64_t c = 0; c < nk && ok; ++c, ++it) {
                     const int s = (int)(it % S);
                     const uint32_t ph = (uint32_t)((it / S) & 1);
-                    if (!(ok = mbar_wait(&empty_bar[s], ph ^ 1, &abort_flag, p.status))) break;
-                    uint8_t* st = smem + (size_t)s * stage_bytes;
-                    mbar_expect_tx(&full_bar[s], gv * a_tile_bytes + 2 * p_tile_bytes);
+                    if (!(ok = mbar_wait(&emptyb[s], ph ^ 1, &abort_flag, p.status))) break;
                     const int kc = (int)(k_begin + c * kBK);
-                    for (int g = 0; g < gv; ++g) {
-                        const int lane0 = (int)((t0 + g) * kTileRows);
-                        if (!TRANS)
-                            tma_load_2d(&tmapA, &full_bar[s], st + g * a_tile_bytes, kc, lane0);  // {col k, row}
-                        else
-                            tma_load_2d(&tmapA, &full_bar[s], st + g * a_tile_bytes, lane0, kc);  // {col, row k}
+                    if (is_a) {
+                        uint8_t* st = a_ring + (size_t)s * a_stage_bytes;
+                        mbar_expect_tx(&fullb[s], gv * a_tile_bytes);
+                        for (int g = 0; g < gv; ++g) {
+                            const int lane0 = (int)((t0 + g) * kTileRows);
+                            if (!TRANS)
+                                tma_load_2d(&tmapA, &fullb[s], st + g * a_tile_bytes, kc, lane0);  // {col k, row}
+                            else
+                                tma_load_2d(&tmapA, &fullb[s], st + g * a_tile_bytes, lane0, kc);  // {col, row k}
+                        }
+                    } else {
+                        uint8_t* st = p_ring + (size_t)s * p_stage_bytes;
+                        mbar_expect_tx(&fullb[s], 2 * p_tile_bytes);
+                        tma_load_2d(&tmapPhi, &fullb[s], st, kc, 0);
+                        tma_load_2d(&tmapPlo, &fullb[s], st + p_tile_bytes, kc, 0);
                     }
-                    tma_load_2d(&tmapPhi, &full_bar[s], st + G * a_tile_bytes, kc, 0);
-                    tma_load_2d(&tmapPlo, &full_bar[s], st + G * a_tile_bytes + p_tile_bytes, kc, 0);
                 }
             }
             if (!ok) {
@@ -288,13 +330,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int64_t j = (it > S ? it - S : 0); j < it; ++j) {
                     const int s = (int)(j % S);
                     const uint32_t ph = (uint32_t)((j / S) & 1);
-                    while (!mbar_test(&full_bar[s], ph) && clock64() - t0 < kSpinLimit) {
+                    while (!mbar_test(&fullb[s], ph) && clock64() - t0 < kSpinLimit) {
                     }
                 }
             }
         }
-    } else if (warp == 1) {
-        // =========================== MMA issuer
+    } else if (warp == 1 || warp == kMmaWarp1) {
+        // =========================== MMA issuers: warp 1 even groups, the other odd groups
+        const int gpar = (warp == 1) ? 0 : 1;
         if (lane == 0) {
             const uint32_t idesc = tf32_idesc(kTileRows, l_pad);
             int64_t it = 0;
@@ -305,16 +348,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!(ok = mbar_wait(&acce_bar, ((uint32_t)set & 1) ^ 1, &abort_flag, p.status))) break;
                 tmem_fence_after();
                 for (int64_t c = 0; c < nk; ++c, ++it) {
-                    const int s = (int)(it % S);
-                    const uint32_t ph = (uint32_t)((it / S) & 1);
+                    const int s = (int)(it % SP);
+                    const uint32_t ph = (uint32_t)((it / SP) & 1);
                     const int ts = (int)(it % kTmemStages);
                     const uint32_t tph = (uint32_t)((it / kTmemStages) & 1);
                     if (!(ok = mbar_wait(&conv_bar[ts], tph, &abort_flag, p.status))) break;
-                    if (!(ok = mbar_wait(&full_bar[s], ph, &abort_flag, p.status))) break;
+                    if (!(ok = mbar_wait(&pfull_bar[s], ph, &abort_flag, p.status))) break;
                     tmem_fence_after();
-                    const uint32_t phi = smem_u32(smem + (size_t)s * stage_bytes + G * a_tile_bytes);
+                    const uint32_t phi = smem_u32(p_ring + (size_t)s * p_stage_bytes);
                     const uint32_t plo = phi + p_tile_bytes;
-                    for (int g = 0; g < gv; ++g) {
+                    for (int g = gpar; g < gv; g += 2) {
                         const uint32_t d = tmem + (uint32_t)(g * l_pad);
                         const uint32_t ahi = tmem + a_col0 + (uint32_t)((ts * G + g) * 2 * kBK);
                         const uint32_t alo = ahi + kBK;
@@ -328,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             mma_tf32_tmemA(d, alo + kk * 8, bhi, idesc, 1u);
                         }
                     }
-                    mma_commit(&empty_bar[s]);
+                    mma_commit(&pempty_bar[s]);
                     mma_commit(&tfree_bar[ts]);
                 }
                 if (!ok) break;
@@ -336,20 +379,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!ok) {
                 // wait (bounded) for the MMAs already issued before TMEM is freed
-                __shared__ uint64_t drain_bar;
-                mbar_init(&drain_bar, 1);
+                __shared__ uint64_t drain_bar[2];
+                mbar_init(&drain_bar[gpar], 1);
                 asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-                mma_commit(&drain_bar);
+                mma_commit(&drain_bar[gpar]);
                 const long long t0 = clock64();
-                while (!mbar_test(&drain_bar, 0) && clock64() - t0 < kSpinLimit) {
+                while (!mbar_test(&drain_bar[gpar], 0) && clock64() - t0 < kSpinLimit) {
                 }
             }
         }
     } else {
-        // =========================== converters + epilogue (warps 2..5)
+        // =========================== converters + epilogue (warps 2..9)
         const int q = warp & 3;                 // TMEM lane quarter of this warp
+        const int hk = (warp - 2) >> 2;         // which half of the K columns / output chunks
         const int r = q * 32 + lane;            // lane (row of the tile) of this thread
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        constexpr int KH = kBK / 2;             // K columns converted by this warp
         float sq = 0.f;  // sum of squares of the A elements this thread converted
         int64_t it = 0;
         bool ok = true;
@@ -357,47 +402,57 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t t0 = tile_begin + set * G;
             const int gv = (int)min((int64_t)G, tile_end - t0);
             for (int64_t c = 0; c < nk; ++c, ++it) {
-                const int s = (int)(it % S);
-                const uint32_t ph = (uint32_t)((it / S) & 1);
+                const int s = (int)(it % SA);
+                const uint32_t ph = (uint32_t)((it / SA) & 1);
                 const int ts = (int)(it % kTmemStages);
                 const uint32_t tph = (uint32_t)((it / kTmemStages) & 1);
-                if (!(ok = mbar_wait(&full_bar[s], ph, &abort_flag, p.status))) break;
+                if (!(ok = mbar_wait(&afull_bar[s], ph, &abort_flag, p.status))) break;
                 if (!(ok = mbar_wait(&tfree_bar[ts], tph ^ 1, &abort_flag, p.status))) break;
                 tmem_fence_after();
-                const uint8_t* st = smem + (size_t)s * stage_bytes;
-                for (int g = 0; g < gv; ++g) {
+                const uint8_t* st = a_ring + (size_t)s * a_stage_bytes;
+                uint32_t hi[G][kBK / 2], lo[G][kBK / 2];
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    if (g >= gv) continue;
                     const float* tile = (const float*)(st + g * a_tile_bytes);
-                    uint32_t hi[32], lo[32];
                     if (!TRANS) {
                         // row r of a 128 x 32 tile, 128-byte swizzle: 16-byte chunk c of
-                        // row r sits at chunk (c ^ (r & 7))
+                        // row r sits at chunk (c ^ (r & 7)); this warp takes chunks 4hk..4hk+3
 #pragma unroll
-                        for (int ch = 0; ch < 8; ++ch) {
+                        for (int cc = 0; cc < 4; ++cc) {
+                            const int ch = 4 * hk + cc;
                             const float4 v =
                                 *(const float4*)((const uint8_t*)tile + r * 128 + ((ch ^ (r & 7)) << 4));
                             const float a4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
-                                sq = fmaf(a4[e], a4[e], sq);
-                                const uint32_t h = tf32_rna(a4[e]);
-                                hi[ch * 4 + e] = h;
-                                lo[ch * 4 + e] = tf32_rna(a4[e] - __uint_as_float(h));
+                                if (SQ) sq = fmaf(a4[e], a4[e], sq);
+                                const uint32_t h = __float_as_uint(a4[e]) & 0xFFFFE000u;
+                                hi[g][cc * 4 + e] = h;
+                                lo[g][cc * 4 + e] = __float_as_uint(a4[e] - __uint_as_float(h));
                             }
                         }
                     } else {
                         // column r of a 32 x 128 tile (rows of 512 bytes, no swizzle)
 #pragma unroll
-                        for (int k = 0; k < kBK; ++k) {
-                            const float a = tile[k * kTileRows + r];
-                            sq = fmaf(a, a, sq);
-                            const uint32_t h = tf32_rna(a);
-                            hi[k] = h;
-                            lo[k] = tf32_rna(a - __uint_as_float(h));
+                        for (int kk = 0; kk < KH; ++kk) {
+                            const float a = tile[(KH * hk + kk) * kTileRows + r];
+                            if (SQ) sq = fmaf(a, a, sq);
+                            const uint32_t h = __float_as_uint(a) & 0xFFFFE000u;
+                            hi[g][kk] = h;
+                            lo[g][kk] = __float_as_uint(a - __uint_as_float(h));
                         }
                     }
-                    const uint32_t col = tmem + a_col0 + (uint32_t)((ts * G + g) * 2 * kBK);
-                    tmem_st32(col + lane_off, hi);
-                    tmem_st32(col + kBK + lane_off, lo);
+                }
+                // the A tile is in registers: hand its shared-memory slot back to TMA
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&aempty_bar[s]);
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    if (g >= gv) continue;
+                    const uint32_t col = tmem + a_col0 + (uint32_t)((ts * G + g) * 2 * kBK) + (uint32_t)(KH * hk);
+                    tmem_st16(col + lane_off, hi[g]);
+                    tmem_st16(col + kBK + lane_off, lo[g]);
                 }
                 tmem_wait_st();
                 tmem_fence_before();
@@ -405,27 +460,33 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (lane == 0) mbar_arrive(&conv_bar[ts]);
             }
             if (!ok) break;
-            // ---- epilogue of this tile set
+            // ---- epilogue of this tile set: 16-column chunks alternate between the two warps of a quarter
             if (!(ok = mbar_wait(&accf_bar, (uint32_t)set & 1, &abort_flag, p.status))) break;
             tmem_fence_after();
             for (int g = 0; g < gv; ++g) {
                 const int64_t idx = (t0 + g) * kTileRows + r;  // row (AX) or column (AtX) of A
                 const int64_t lim = TRANS ? p.n : p.m;
-                float* out = p.out + (TRANS ? (int64_t)blockIdx.y * p.split_stride : 0);
-                for (int j0 = 0; j0 < l_pad; j0 += 16) {
+                float* out = p.out + (int64_t)blockIdx.y * p.split_stride;
+                for (int j0 = 16 * hk; j0 < l_pad; j0 += 32) {
                     uint32_t v[16];
                     tmem_ld16(tmem + (uint32_t)(g * l_pad + j0) + lane_off, v);
                     tmem_wait_ld();
                     if (idx < lim) {
+                        if (p.out_rowmajor) {
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) {
-                            const float y = __uint_as_float(v[e]);
-                            const int64_t o = (int64_t)(j0 + e) * p.ld_out + idx;
-                            out[o] = y;
-                            if (!TRANS && p.out_hi) {
-                                const uint32_t h = tf32_rna(y);
-                                p.out_hi[o] = __uint_as_float(h);
-                                p.out_lo[o] = __uint_as_float(tf32_rna(y - __uint_as_float(h)));
+                            for (int e = 0; e < 16; ++e)
+                                if (j0 + e < p.out_cols) out[idx * p.ld_out + j0 + e] = __uint_as_float(v[e]);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) {
+                                const float y = __uint_as_float(v[e]);
+                                const int64_t o = (int64_t)(j0 + e) * p.ld_out + idx;
+                                out[o] = y;
+                                if (p.out_hi) {
+                                    const uint32_t h = tf32_rna(y);
+                                    p.out_hi[o] = __uint_as_float(h);
+                                    p.out_lo[o] = __uint_as_float(tf32_rna(y - __uint_as_float(h)));
+                                }
                             }
                         }
                     }
@@ -435,7 +496,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce_bar);
         }
-        if (p.fro2) {
+        if (SQ && p.fro2) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
             if (lane == 0) atomicAdd(p.fro2, (double)sq);
@@ -484,7 +545,7 @@ template <bool TRANS, int G>
 int launch_typed(cudaStream_t s, const CUtensorMap& mA, const CUtensorMap& mhi, const CUtensorMap& mlo,
                  TcParams p, dim3 grid, size_t smem)
 {
-    auto kern = tc_pass_kernel<TRANS, G>;
+    auto kern = p.fro2 ? tc_pass_kernel<TRANS, G, true> : tc_pass_kernel<TRANS, G, false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return RSVDGB_ERR_CUDA;
     kern<<<grid, kThreads, smem, s>>>(mA, mhi, mlo, p);
@@ -511,16 +572,19 @@ bool tc_pass_supported(int64_t m, int64_t n, int64_t lda, int l_pad, const void*
     return get_encoder() != nullptr;
 }
 
-int launch_tc_pass(cudaStream_t s, int sm_count, bool trans, const float* A, int64_t m, int64_t n, int64_t lda,
+int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int64_t m, int64_t n, int64_t lda,
                    const float* Phi, const float* Plo, int64_t ldp, int l_pad, float* out, float* out_hi,
-                   float* out_lo, int64_t ld_out, float* partial, int64_t* splits_out, int* status, double* fro2)
+                   float* out_lo, int64_t ld_out, float* partial, int64_t want_splits, int64_t* splits_out,
+                   int* status, double* fro2, int out_rowmajor, int out_cols)
 {
     const int G = groups_for(l_pad);
-    const uint32_t stage_bytes = G * kTileRows * kBK * 4 + 2 * (uint32_t)l_pad * kBK * 4;
-    const size_t smem_budget = 225 * 1024;
-    int stages = (int)std::min<size_t>(4, (smem_budget - 1024) / stage_bytes);
-    if (stages < 2) return RSVDGB_ERR_UNSUPPORTED;
-    const size_t smem = (size_t)stages * stage_bytes + 1024;
+    const size_t a_stage = (size_t)G * kTileRows * kBK * 4;
+    const size_t p_stage = 2 * (size_t)l_pad * kBK * 4;
+    const size_t budget = 224 * 1024;  // dynamic shared memory, 1 KB kept for alignment
+    int sp = (3 * p_stage + 2 * a_stage <= budget) ? 3 : 2;
+    int sa = (int)std::min<size_t>(kMaxAStages, (budget - sp * p_stage) / a_stage);
+    if (sa < 2) return RSVDGB_ERR_UNSUPPORTED;
+    const size_t smem = sa * a_stage + sp * p_stage + 1024;
 
     CUtensorMap mA, mhi, mlo;
     const int64_t k_total = trans ? m : n;
@@ -538,31 +602,37 @@ int launch_tc_pass(cudaStream_t s, int sm_count, bool trans, const float* A, int
     p.n = n;
     p.l_pad = l_pad;
     p.k_total = k_total;
-    p.stages = stages;
+    p.a_stages = sa;
+    p.p_stages = sp;
     p.status = status;
     p.fro2 = fro2;
     p.ld_out = ld_out;
-    dim3 grid;
-    if (!trans) {
-        p.num_tiles = ceil_div(m, kTileRows);
-        p.k_per_split = n;
-        p.out = out;
-        p.out_hi = out_hi;
-        p.out_lo = out_lo;
-        grid = dim3((unsigned)std::min<int64_t>(sm_count, p.num_tiles));
-        if (splits_out) *splits_out = 1;
-    } else {
-        p.num_tiles = ceil_div(n, kTileRows);
-        const int64_t sets = ceil_div(p.num_tiles, G);
-        int64_t splits = std::max<int64_t>(1, (int64_t)sm_count / sets);
-        splits = std::min<int64_t>(splits, std::max<int64_t>(1, m / (4 * kBK)));
-        p.k_per_split = round_up(ceil_div(m, splits), kBK);
-        splits = ceil_div(m, p.k_per_split);
-        p.out = partial;
-        p.split_stride = (int64_t)l_pad * ld_out;
-        grid = dim3((unsigned)sets, (unsigned)splits);
-        if (splits_out) *splits_out = splits;
+    p.num_tiles = ceil_div(trans ? n : m, kTileRows);
+    // K splits: fill the GPU when the lane tiles alone do not
+    const int64_t units = trans ? ceil_div(p.num_tiles, G) : p.num_tiles;
+    int64_t splits = want_splits;
+    if (splits <= 0) {
+        splits = std::max<int64_t>(1, (int64_t)sm_count / std::max<int64_t>(units, 1));
+        splits = std::min<int64_t>(splits, std::max<int64_t>(1, k_total / (4 * kBK)));
     }
+    p.k_per_split = round_up(ceil_div(k_total, splits), kBK);
+    splits = ceil_div(k_total, p.k_per_split);
+    const bool direct = (splits == 1) && out != nullptr;
+    if (!direct && !partial) return RSVDGB_ERR_INVALID_ARG;
+    p.out = direct ? out : partial;
+    p.out_hi = direct ? out_hi : nullptr;
+    p.out_lo = direct ? out_lo : nullptr;
+    p.split_stride = direct ? 0 : (int64_t)l_pad * ld_out;
+    p.out_rowmajor = direct ? out_rowmajor : 0;
+    p.out_cols = out_cols > 0 ? out_cols : l_pad;
+    if (out_rowmajor && !direct) return RSVDGB_ERR_INVALID_ARG;
+    dim3 grid;
+    if (!trans)
+        grid = dim3((unsigned)std::min<int64_t>(std::max<int64_t>(sm_count / splits, 1), p.num_tiles),
+                    (unsigned)splits);
+    else
+        grid = dim3((unsigned)units, (unsigned)splits);
+    if (splits_out) *splits_out = direct ? 0 : splits;
     switch ((trans ? 8 : 0) + G) {
         case 1: return launch_typed<false, 1>(s, mA, mhi, mlo, p, grid, smem);
         case 2: return launch_typed<false, 2>(s, mA, mhi, mlo, p, grid, smem);
@@ -576,12 +646,21 @@ int launch_tc_pass(cudaStream_t s, int sm_count, bool trans, const float* A, int
 
 int64_t tc_pass_max_splits(int64_t m, int64_t n, int l_pad, int sm_count)
 {
+    // automatic split count of an A^T X launch on an m x n matrix
     const int G = groups_for(l_pad);
-    const int64_t sets = ceil_div(ceil_div(n, kTileRows), G);
-    int64_t splits = std::max<int64_t>(1, (int64_t)sm_count / sets);
+    const int64_t units = ceil_div(ceil_div(n, kTileRows), G);
+    int64_t splits = std::max<int64_t>(1, (int64_t)sm_count / units);
     splits = std::min<int64_t>(splits, std::max<int64_t>(1, m / (4 * kBK)));
     const int64_t kps = round_up(ceil_div(m, splits), kBK);
     return ceil_div(m, kps);
+}
+
+int64_t tc_split_count(int64_t k_total, int64_t units, int sm_count)
+{
+    int64_t splits = std::max<int64_t>(1, (int64_t)sm_count / std::max<int64_t>(units, 1));
+    splits = std::min<int64_t>(splits, std::max<int64_t>(1, k_total / (4 * kBK)));
+    const int64_t kps = round_up(ceil_div(k_total, splits), kBK);
+    return ceil_div(k_total, kps);
 }
 
 }  // namespace rsvdgb

@@ -43,7 +43,8 @@ class RsvdgbInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("q_used", ctypes.c_int32), ("p_used", ctypes.c_int32),
                 ("l", ctypes.c_int32), ("fro2_A", ctypes.c_double), ("fro2_B", ctypes.c_double),
                 ("err2_QB", ctypes.c_double), ("err2_k", ctypes.c_double), ("breakdowns", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("engine", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
