@@ -90,16 +90,21 @@ bool tc_pass_supported(int64_t m, int64_t n, int64_t lda, int l_pad, const void*
 // consecutive partials l_pad*ld_out apart) to `partial`, and *splits_out is
 // the count to reduce.  fro2 (optional) accumulates ||A||_F^2.  With
 // out_rowmajor (direct output only) out is written row-major:
-// out[idx * ld_out + j] for j < out_cols.
+// out[idx * ld_out + j] for j < out_cols.  With bf16_panel the products run in
+// BF16 (A rounded to nearest BF16, P given as one BF16 panel in Phi with
+// leading dimension ldp elements; Plo unused), one MMA per K step.
 int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int64_t m, int64_t n, int64_t lda,
                    const float* Phi, const float* Plo, int64_t ldp, int l_pad, float* out, float* out_hi,
                    float* out_lo, int64_t ld_out, float* partial, int64_t want_splits, int64_t* splits_out,
-                   int* status, double* fro2, int out_rowmajor = 0, int out_cols = 0);
+                   int* status, double* fro2, int out_rowmajor = 0, int out_cols = 0, int bf16_panel = 0);
 int64_t tc_pass_max_splits(int64_t m, int64_t n, int l_pad, int sm_count);
 int64_t tc_split_count(int64_t k_total, int64_t units, int sm_count);
 // l x l row-major T -> column-major L x L TF32 hi/lo panel (zero padded),
 // i.e. out[j * L + c] = T[c * l + j].
 void launch_small_panel(cudaStream_t s, const float* T, int l, int L, float* hi, float* lo);
+// BF16 (round to nearest) copy of a column-major rows x l matrix over l_pad
+// columns, zero outside rows x l.
+void launch_to_bf16(cudaStream_t s, const float* in, int64_t ld, int64_t rows, int l, int l_pad, void* out);
 // TF32 split of a column-major rows x l matrix (ld) into hi + lo parts over
 // l_pad columns; rows >= rows and columns >= l are written as zero.
 void launch_split_tf32(cudaStream_t s, const float* in, int64_t ld, int64_t rows, int l, int l_pad, float* hi,

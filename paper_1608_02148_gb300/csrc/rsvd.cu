@@ -86,6 +86,7 @@ struct Geom {
     int l;
     int L;         // l rounded up to 16 (tensor-core N granularity)
     bool use_tc;   // passes over A on the tensor cores
+    bool bf16;     // sketch and power passes in BF16 (mixed precision)
     int64_t ldm, ldn;
     // stored matrix dimensions (rows x cols of the row-major S)
     int64_t sm() const { return trans ? n : m; }
@@ -96,6 +97,7 @@ struct Work {
     float *Pt, *Yt, *Qt, *Wt, *Zt, *part;
     float *Pth, *Ptl, *Yth, *Ytl;  // TF32 hi/lo parts of the panels (tensor-core engine)
     float *Qth, *Qtl, *Th, *Tl;    // hi/lo of the first CholeskyQR2 basis and of a small factor
+    void *Ptb, *Ytb;               // BF16 panels (mixed precision)
     double* G;
     float *T1, *T2, *T, *R1, *R2, *RB, *M, *sigma, *Ut, *Jt, *jwork;
     int *status, *breakdowns, *sweeps;
@@ -149,6 +151,11 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w)
         w.Qtl = c.take<float>(L * g.ldm);
         w.Th = c.take<float>(L * L);
         w.Tl = c.take<float>(L * L);
+    }
+    w.Ptb = w.Ytb = nullptr;
+    if (g.bf16) {
+        w.Ptb = c.take<uint16_t>(L * g.ldn);
+        w.Ytb = c.take<uint16_t>(L * g.ldm);
     }
     w.Wt = c.take<float>(L * g.ldn);
     w.Zt = c.take<float>(L * g.ldn);
@@ -260,7 +267,7 @@ double a_bytes(const Geom& g) { return (double)g.m * (double)g.n * (g.a_bf16 ? 2
 // parts (tensor-core engine).  out is column-major (rows x l, ldO); when
 // out_h/out_l are given (tensor-core engine) they receive its TF32 split.
 void pass_over_A(rsvdgb_handle* h, const Geom& g, Work& w, bool A_side, const float* P, const float* Ph,
-                 const float* Pl, float* out, float* out_h, float* out_l, double* fro2)
+                 const float* Pl, float* out, float* out_h, float* out_l, double* fro2, const void* Pbf = nullptr)
 {
     const cudaStream_t s = h->stream;
     const int64_t rows = A_side ? g.m : g.n;
@@ -279,8 +286,13 @@ void pass_over_A(rsvdgb_handle* h, const Geom& g, Work& w, bool A_side, const fl
     const bool stored_atx = (A_side == g.trans);
     int64_t splits = 0;
     prof_mark(h, true, 0);
-    launch_tc_gemm(s, h->sm_count, stored_atx, (const float*)g.A, g.sm(), g.sn(), g.lda, Ph, Pl, ldP, g.L, out, out_h,
-                   out_l, ldO, w.part, stored_atx ? 0 : 1, &splits, w.status, fro2);
+    if (Pbf)
+        launch_tc_gemm(s, h->sm_count, stored_atx, (const float*)g.A, g.sm(), g.sn(), g.lda, (const float*)Pbf,
+                       nullptr, ldP, g.L, out, out_h, out_l, ldO, w.part, stored_atx ? 0 : 1, &splits, w.status, fro2,
+                       0, 0, 1);
+    else
+        launch_tc_gemm(s, h->sm_count, stored_atx, (const float*)g.A, g.sm(), g.sn(), g.lda, Ph, Pl, ldP, g.L, out,
+                       out_h, out_l, ldO, w.part, stored_atx ? 0 : 1, &splits, w.status, fro2);
     prof_mark(h, false, a_bytes(g));
     if (splits > 0) {
         launch_reduce_splits(s, w.part, (int)splits, (int64_t)g.L * ldO, g.l, rows, ldO, out, nullptr, ldO);
@@ -310,22 +322,34 @@ void tc_times_small(rsvdgb_handle* h, const Geom& g, Work& w, const float* Xt, i
                    &splits, w.status, nullptr);
 }
 
-// Y = A_logical X with X = Pt (n x l) -> Yt (m x l) [+ TF32 split of Y]
+// Y = A_logical X with X = Pt (n x l) -> Yt (m x l) [+ TF32 split of Y].
+// In mixed precision the product runs in BF16 on the BF16 copy of the panel.
 void apply_A(rsvdgb_handle* h, const Geom& g, Work& w, double* fro2)
 {
-    pass_over_A(h, g, w, true, w.Pt, w.Pth, w.Ptl, w.Yt, w.Yth, w.Ytl, fro2);
+    pass_over_A(h, g, w, true, w.Pt, w.Pth, w.Ptl, w.Yt, w.Yth, w.Ytl, fro2, g.bf16 ? w.Ptb : nullptr);
 }
 
-// W = A_logical^T Y with Y = Yt (m x l) -> Wt (n x l)
-void apply_At(rsvdgb_handle* h, const Geom& g, Work& w)
+// W = A_logical^T Y with Y = Yt (m x l) -> Wt (n x l).  `accurate` keeps the
+// FP32-accurate 3xTF32 product (the projection B = Q^T A); otherwise mixed
+// precision runs it in BF16.
+void apply_At(rsvdgb_handle* h, const Geom& g, Work& w, bool accurate)
 {
+    if (g.bf16 && !accurate) {
+        launch_to_bf16(h->stream, w.Yt, g.ldm, g.m, g.l, g.L, w.Ytb);
+        pass_over_A(h, g, w, false, w.Yt, nullptr, nullptr, w.Wt, nullptr, nullptr, nullptr, w.Ytb);
+        return;
+    }
     pass_over_A(h, g, w, false, w.Yt, w.Yth, w.Ytl, w.Wt, nullptr, nullptr, nullptr);
 }
 
-// After the panel Pt changed: its TF32 split for the tensor-core engine.
+// After the panel Pt changed: its TF32 split (or BF16 copy) for the
+// tensor-core engine.
 void split_panel(cudaStream_t s, const Geom& g, Work& w)
 {
-    if (g.use_tc) launch_split_tf32(s, w.Pt, g.ldn, g.n, g.l, g.L, w.Pth, w.Ptl);
+    if (g.bf16)
+        launch_to_bf16(s, w.Pt, g.ldn, g.n, g.l, g.L, w.Ptb);
+    else if (g.use_tc)
+        launch_split_tf32(s, w.Pt, g.ldn, g.n, g.l, g.L, w.Pth, w.Ptl);
 }
 
 // G (l x l, FP64) = X^T Z for column-major rows x l matrices X and Z
@@ -421,7 +445,7 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
         // Q = qr(Y): only the span is carried forward, so one Cholesky step
         // (Q = Y T); A^T Q = (A^T Y) T.
         launch_chol_inv(s, w.G, l, 0.f, nullptr, w.T, w.status, w.breakdowns);
-        apply_At(h, g, w);
+        apply_At(h, g, w, false);
         times_small(s, sm, w.Wt, g.ldn, g.n, l, w.T, w.Zt, w.part);
         // Q = qr(A^T Q): CholeskyQR2 on the n side, result in the panel
         cholqr2(s, sm, w, w.Zt, g.ldn, g.n, l, w.Wt, w.Pt);
@@ -449,7 +473,7 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
     else
         times_small(s, sm, w.Qt, g.ldm, g.m, l, w.T2, w.Yt, w.part);
     // step 10: B^T = A^T Q (n x l, column-major: row j of B is contiguous)
-    apply_At(h, g, w);
+    apply_At(h, g, w, true);
     if (o.Qrow) launch_colmajor_to_rowmajor(s, w.Yt, g.ldm, g.m, l, o.Qrow, o.ldq);
     if (o.Brow)
         RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(o.Brow, o.ldb * sizeof(float), w.Wt, g.ldn * sizeof(float),
@@ -506,7 +530,7 @@ int check_handle(rsvdgb_handle* h)
 
 // Validate a user matrix and build the m >= n geometry.
 int make_geom(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int layout, int k, int p, int engine,
-              Geom& g)
+              int prec, Geom& g)
 {
     if (!A || m < 1 || n < 1) return RSVDGB_ERR_INVALID_ARG;
     if (dtype != RSVDGB_F32 && dtype != RSVDGB_BF16) return RSVDGB_ERR_INVALID_ARG;
@@ -536,6 +560,9 @@ int make_geom(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int l
     const bool tc_ok = tc_pass_supported(g.sm(), g.sn(), g.lda, g.L, A, g.a_bf16);
     if (engine == RSVDGB_ENGINE_TC && !tc_ok) return RSVDGB_ERR_UNSUPPORTED;
     g.use_tc = (engine != RSVDGB_ENGINE_SIMT) && tc_ok;
+    if (prec != RSVDGB_PREC_FP32 && prec != RSVDGB_PREC_BF16_SKETCH) return RSVDGB_ERR_INVALID_ARG;
+    g.bf16 = (prec == RSVDGB_PREC_BF16_SKETCH);
+    if (g.bf16 && !g.use_tc) return RSVDGB_ERR_UNSUPPORTED;  // mixed precision runs on the tensor cores
     return RSVDGB_OK;
 }
 
@@ -627,14 +654,13 @@ int rsvdgb_rsvd(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t l
         rsvdgb_default_opts(&o);
     if (o.q < 0 || o.sdist < 0 || o.sdist > 2) return RSVDGB_ERR_INVALID_ARG;
     Geom g{};
-    rc = make_geom(A, m, n, lda, dtype, o.layout, k, o.p, o.engine, g);
+    rc = make_geom(A, m, n, lda, dtype, o.layout, k, o.p, o.engine, o.prec, g);
     if (rc) return rc;
     if (nu < 0) nu = k;
     if (nv < 0) nv = k;
     if (nu > k || nv > k || !d) return RSVDGB_ERR_INVALID_ARG;
     if (nu > 0 && (!U || ldu < nu)) return RSVDGB_ERR_INVALID_ARG;
     if (nv > 0 && (!V || ldv < nv)) return RSVDGB_ERR_INVALID_ARG;
-    if (o.prec != RSVDGB_PREC_FP32) return RSVDGB_ERR_UNSUPPORTED;
     Outputs out{};
     out.d = d;
     out.info = info;
@@ -661,10 +687,9 @@ int rsvdgb_rqb(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t ld
     if (o.q < 0 || o.sdist < 0 || o.sdist > 2) return RSVDGB_ERR_INVALID_ARG;
     if (m < n || o.layout != RSVDGB_ROW_MAJOR) return RSVDGB_ERR_INVALID_ARG;
     Geom g{};
-    rc = make_geom(A, m, n, lda, dtype, o.layout, k, o.p, o.engine, g);
+    rc = make_geom(A, m, n, lda, dtype, o.layout, k, o.p, o.engine, o.prec, g);
     if (rc) return rc;
     if (!Q || !B || ldq < g.l || ldb < n) return RSVDGB_ERR_INVALID_ARG;
-    if (o.prec != RSVDGB_PREC_FP32) return RSVDGB_ERR_UNSUPPORTED;
     Outputs out{};
     out.Qrow = Q;
     out.ldq = ldq;
@@ -760,11 +785,13 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
     if (dtype != RSVDGB_F32 && dtype != RSVDGB_BF16) return RSVDGB_ERR_INVALID_ARG;
     if (ldx < l || ldy < l) return RSVDGB_ERR_INVALID_ARG;
     if (engine < RSVDGB_ENGINE_AUTO || engine > RSVDGB_ENGINE_TC) return RSVDGB_ERR_INVALID_ARG;
-    if (prec != RSVDGB_PREC_FP32) return RSVDGB_ERR_UNSUPPORTED;
+    if (prec != RSVDGB_PREC_FP32 && prec != RSVDGB_PREC_BF16_SKETCH) return RSVDGB_ERR_INVALID_ARG;
+    const bool bf = prec == RSVDGB_PREC_BF16_SKETCH;
     const int64_t M = transpose ? n : m, K = transpose ? m : n;
     const int L = (int)round_up(l, 16);
     const bool tc_ok = l <= 256 && tc_pass_supported(m, n, lda, L, A, dtype == RSVDGB_BF16);
-    if (engine == RSVDGB_ENGINE_TC && !tc_ok) return RSVDGB_ERR_UNSUPPORTED;
+    if ((engine == RSVDGB_ENGINE_TC || bf) && !tc_ok) return RSVDGB_ERR_UNSUPPORTED;
+    if (bf && engine == RSVDGB_ENGINE_SIMT) return RSVDGB_ERR_UNSUPPORTED;
     if (engine == RSVDGB_ENGINE_SIMT || !tc_ok) {
         const int64_t tiles = ceil_div(M, 64) * ceil_div(l, 64);
         const int splits = splits_for(tiles, K, h->sm_count);
@@ -797,10 +824,16 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
     const cudaStream_t s = h->stream;
     RSVDGB_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
     launch_rowmajor_to_colmajor(s, X, ldx, K, l, L, Xc, ldK);
-    launch_split_tf32(s, Xc, ldK, K, l, L, Xh, Xl);
     int64_t used = 0;
-    rc = launch_tc_gemm(s, h->sm_count, transpose, (const float*)A, m, n, lda, Xh, Xl, ldK, L, Yc, nullptr, nullptr,
-                        ldM, part, transpose ? 0 : 1, &used, status, nullptr);
+    if (bf) {
+        launch_to_bf16(s, Xc, ldK, K, l, L, Xh);
+        rc = launch_tc_gemm(s, h->sm_count, transpose, (const float*)A, m, n, lda, Xh, nullptr, ldK, L, Yc, nullptr,
+                            nullptr, ldM, part, transpose ? 0 : 1, &used, status, nullptr, 0, 0, 1);
+    } else {
+        launch_split_tf32(s, Xc, ldK, K, l, L, Xh, Xl);
+        rc = launch_tc_gemm(s, h->sm_count, transpose, (const float*)A, m, n, lda, Xh, Xl, ldK, L, Yc, nullptr,
+                            nullptr, ldM, part, transpose ? 0 : 1, &used, status, nullptr);
+    }
     if (rc) return rc;
     if (used > 0) launch_reduce_splits(s, part, (int)used, (int64_t)L * ldM, l, M, ldM, Yc, nullptr, ldM);
     launch_colmajor_to_rowmajor(s, Yc, ldM, M, l, Y, ldy);

@@ -12,6 +12,7 @@
 // FP64 pipe is far slower than its FP32 pipe, and the Gram matrices they
 // factor carry FP32-level error already, so FP64 here would not change the
 // result beyond that error; CholeskyQR2 recovers orthogonality to FP32 level.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "internal.cuh"
@@ -403,6 +404,16 @@ __global__ void small_panel_kernel(const float* __restrict__ T, int l, int L, fl
     lo[j * L + c] = r;
 }
 
+__global__ void to_bf16_kernel(const float* __restrict__ in, int64_t ld, int64_t rows, int l, int l_pad,
+                               __nv_bfloat16* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= ld || j >= l_pad) return;
+    const int64_t o = (int64_t)j * ld + i;
+    out[o] = __float2bfloat16_rn((i < rows && j < l) ? in[o] : 0.f);
+}
+
 __global__ void col_to_row_kernel(const float* __restrict__ in, int64_t ld, int64_t rows, int cols,
                                   float* __restrict__ out, int64_t ldo)
 {
@@ -556,6 +567,13 @@ void launch_small_panel(cudaStream_t s, const float* T, int l, int L, float* hi,
 {
     dim3 grid((unsigned)ceil_div(L, 128), (unsigned)L);
     small_panel_kernel<<<grid, 128, 0, s>>>(T, l, L, hi, lo);
+    count_launches();
+}
+
+void launch_to_bf16(cudaStream_t s, const float* in, int64_t ld, int64_t rows, int l, int l_pad, void* out)
+{
+    dim3 grid((unsigned)ceil_div(ld, 256), (unsigned)l_pad);
+    to_bf16_kernel<<<grid, 256, 0, s>>>(in, ld, rows, l, l_pad, (__nv_bfloat16*)out);
     count_launches();
 }
 

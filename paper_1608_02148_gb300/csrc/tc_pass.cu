@@ -140,6 +140,50 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
     return d;
 }
 
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 64 bytes),
+// 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;  // 64-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::f16 with BF16 A and B (both K-major), D FP32.
+__device__ __forceinline__ uint32_t bf16_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16_tmemA(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                               uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 32 lanes x 32 bit, 8 consecutive columns per thread.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem)
+{
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi_elem), "f"(lo_elem));
+    return r;
+}
+
 // Instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major.
 __device__ __forceinline__ uint32_t tf32_idesc(int M, int N)
 {
@@ -209,7 +253,7 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ----------------------------------------------------------------- the kernel
-template <bool TRANS, int G, bool SQ>
+template <bool TRANS, int G, bool SQ, bool BF>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_pass_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapPhi,
                    const __grid_constant__ CUtensorMap tmapPlo, TcParams p)
@@ -230,9 +274,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int SA = p.a_stages, SP = p.p_stages;
     const int l_pad = p.l_pad;
     const uint32_t a_tile_bytes = kTileRows * kBK * 4;         // 16 KB
-    const uint32_t p_tile_bytes = (uint32_t)l_pad * kBK * 4;   // l_pad rows x 128 B
+    // panel tile: l_pad rows x kBK elements (TF32 hi + lo: 128 B rows each; BF16: one 64 B row)
+    const uint32_t p_tile_bytes = (uint32_t)l_pad * kBK * (BF ? 2 : 4);
     const uint32_t a_stage_bytes = G * a_tile_bytes;
-    const uint32_t p_stage_bytes = 2 * p_tile_bytes;
+    const uint32_t p_stage_bytes = (BF ? 1 : 2) * p_tile_bytes;
+    constexpr uint32_t kAcols = BF ? kBK / 2 : 2 * kBK;  // TMEM columns of one converted A tile
     uint8_t* a_ring = smem;
     uint8_t* p_ring = smem + (size_t)SA * a_stage_bytes;
 
@@ -255,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---- TMEM columns: G accumulators of l_pad, then A buffers
     const uint32_t acc_cols = (uint32_t)G * l_pad;
     const uint32_t a_col0 = (acc_cols + 31) & ~31u;
-    const uint32_t need = a_col0 + kTmemStages * G * 2 * kBK;
+    const uint32_t need = a_col0 + kTmemStages * G * kAcols;
     uint32_t tmem_cols = 32;
     while (tmem_cols < need) tmem_cols <<= 1;
 
@@ -318,9 +364,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     } else {
                         uint8_t* st = p_ring + (size_t)s * p_stage_bytes;
-                        mbar_expect_tx(&fullb[s], 2 * p_tile_bytes);
+                        mbar_expect_tx(&fullb[s], p_stage_bytes);
                         tma_load_2d(&tmapPhi, &fullb[s], st, kc, 0);
-                        tma_load_2d(&tmapPlo, &fullb[s], st + p_tile_bytes, kc, 0);
+                        if (!BF) tma_load_2d(&tmapPlo, &fullb[s], st + p_tile_bytes, kc, 0);
                     }
                 }
             }
@@ -339,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // =========================== MMA issuers: warp 1 even groups, the other odd groups
         const int gpar = (warp == 1) ? 0 : 1;
         if (lane == 0) {
-            const uint32_t idesc = tf32_idesc(kTileRows, l_pad);
+            const uint32_t idesc = BF ? bf16_idesc(kTileRows, l_pad) : tf32_idesc(kTileRows, l_pad);
             int64_t it = 0;
             bool ok = true;
             for (int64_t set = 0; set < num_sets && ok; ++set) {
@@ -359,8 +405,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t plo = phi + p_tile_bytes;
                     for (int g = gpar; g < gv; g += 2) {
                         const uint32_t d = tmem + (uint32_t)(g * l_pad);
-                        const uint32_t ahi = tmem + a_col0 + (uint32_t)((ts * G + g) * 2 * kBK);
+                        const uint32_t ahi = tmem + a_col0 + (uint32_t)(ts * G + g) * kAcols;
                         const uint32_t alo = ahi + kBK;
+                        if (BF) {
+                            // one BF16 product per K step of 16 (8 TMEM columns, 32 bytes of panel row)
+#pragma unroll
+                            for (int kk = 0; kk < kBK / 16; ++kk) {
+                                const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+                                mma_bf16_tmemA(d, ahi + kk * 8, sw64_desc(phi + kk * 32), idesc, acc);
+                            }
+                            continue;
+                        }
 #pragma unroll
                         for (int kk = 0; kk < kBK / 8; ++kk) {
                             const uint64_t bhi = sw128_desc(phi + kk * 32);
@@ -415,6 +470,31 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int g = 0; g < G; ++g) {
                     if (g >= gv) continue;
                     const float* tile = (const float*)(st + g * a_tile_bytes);
+                    if (BF) {
+                        // BF16 (round to nearest) of this warp's 16 K values, packed in pairs
+                        float a16[KH];
+                        if (!TRANS) {
+#pragma unroll
+                            for (int cc = 0; cc < 4; ++cc) {
+                                const int ch = 4 * hk + cc;
+                                const float4 v =
+                                    *(const float4*)((const uint8_t*)tile + r * 128 + ((ch ^ (r & 7)) << 4));
+                                a16[cc * 4 + 0] = v.x;
+                                a16[cc * 4 + 1] = v.y;
+                                a16[cc * 4 + 2] = v.z;
+                                a16[cc * 4 + 3] = v.w;
+                            }
+                        } else {
+#pragma unroll
+                            for (int kk = 0; kk < KH; ++kk) a16[kk] = tile[(KH * hk + kk) * kTileRows + r];
+                        }
+#pragma unroll
+                        for (int e = 0; e < KH / 2; ++e) {
+                            if (SQ) sq = fmaf(a16[2 * e], a16[2 * e], fmaf(a16[2 * e + 1], a16[2 * e + 1], sq));
+                            hi[g][e] = pack_bf16(a16[2 * e], a16[2 * e + 1]);
+                        }
+                        continue;
+                    }
                     if (!TRANS) {
                         // row r of a 128 x 32 tile, 128-byte swizzle: 16-byte chunk c of
                         // row r sits at chunk (c ^ (r & 7)); this warp takes chunks 4hk..4hk+3
@@ -450,7 +530,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
                     if (g >= gv) continue;
-                    const uint32_t col = tmem + a_col0 + (uint32_t)((ts * G + g) * 2 * kBK) + (uint32_t)(KH * hk);
+                    if (BF) {
+                        const uint32_t col = tmem + a_col0 + (uint32_t)(ts * G + g) * kAcols + (uint32_t)(8 * hk);
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) pk[e] = hi[g][e];
+                        tmem_st8(col + lane_off, pk);
+                        continue;
+                    }
+                    const uint32_t col = tmem + a_col0 + (uint32_t)(ts * G + g) * kAcols + (uint32_t)(KH * hk);
                     tmem_st16(col + lane_off, hi[g]);
                     tmem_st16(col + kBK + lane_off, lo[g]);
                 }
@@ -528,7 +616,8 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder()
 }
 
 bool encode_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
-               uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz)
+               uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz,
+               CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32)
 {
     auto enc = get_encoder();
     if (!enc) return false;
@@ -536,16 +625,16 @@ bool encode_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t oute
     const cuuint64_t strides[1] = {row_bytes};
     const cuuint32_t box[2] = {box_inner, box_outer};
     const cuuint32_t estr[2] = {1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+    return enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <bool TRANS, int G>
+template <bool TRANS, int G, bool BF>
 int launch_typed(cudaStream_t s, const CUtensorMap& mA, const CUtensorMap& mhi, const CUtensorMap& mlo,
                  TcParams p, dim3 grid, size_t smem)
 {
-    auto kern = p.fro2 ? tc_pass_kernel<TRANS, G, true> : tc_pass_kernel<TRANS, G, false>;
+    auto kern = p.fro2 ? tc_pass_kernel<TRANS, G, true, BF> : tc_pass_kernel<TRANS, G, false, BF>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return RSVDGB_ERR_CUDA;
     kern<<<grid, kThreads, smem, s>>>(mA, mhi, mlo, p);
@@ -553,11 +642,12 @@ int launch_typed(cudaStream_t s, const CUtensorMap& mA, const CUtensorMap& mhi, 
     return cudaGetLastError() == cudaSuccess ? RSVDGB_OK : RSVDGB_ERR_CUDA;
 }
 
-int groups_for(int l_pad)
+int groups_for(int l_pad, bool bf)
 {
-    // TMEM: G accumulators of l_pad columns + 2 stages x G x 64 A columns <= 512
+    // TMEM: G accumulators of l_pad columns + 2 stages x G converted A tiles <= 512
+    const int acols = bf ? kBK / 2 : 2 * kBK;
     int g = 3;
-    while (g > 1 && ((g * l_pad + 31) / 32 * 32 + kTmemStages * g * 2 * kBK) > 512) --g;
+    while (g > 1 && ((g * l_pad + 31) / 32 * 32 + kTmemStages * g * acols) > 512) --g;
     return g;
 }
 
@@ -575,11 +665,12 @@ bool tc_pass_supported(int64_t m, int64_t n, int64_t lda, int l_pad, const void*
 int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int64_t m, int64_t n, int64_t lda,
                    const float* Phi, const float* Plo, int64_t ldp, int l_pad, float* out, float* out_hi,
                    float* out_lo, int64_t ld_out, float* partial, int64_t want_splits, int64_t* splits_out,
-                   int* status, double* fro2, int out_rowmajor, int out_cols)
+                   int* status, double* fro2, int out_rowmajor, int out_cols, int bf16_panel)
 {
-    const int G = groups_for(l_pad);
+    const bool bf = bf16_panel != 0;
+    const int G = groups_for(l_pad, bf);
     const size_t a_stage = (size_t)G * kTileRows * kBK * 4;
-    const size_t p_stage = 2 * (size_t)l_pad * kBK * 4;
+    const size_t p_stage = (bf ? 2 : 8) * (size_t)l_pad * kBK;
     const size_t budget = 224 * 1024;  // dynamic shared memory, 1 KB kept for alignment
     int sp = (3 * p_stage + 2 * a_stage <= budget) ? 3 : 2;
     int sa = (int)std::min<size_t>(kMaxAStages, (budget - sp * p_stage) / a_stage);
@@ -593,8 +684,14 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
         ok = encode_2d(&mA, A, n, m, lda * 4, kBK, kTileRows, CU_TENSOR_MAP_SWIZZLE_128B);
     else
         ok = encode_2d(&mA, A, n, m, lda * 4, kTileRows, kBK, CU_TENSOR_MAP_SWIZZLE_NONE);
-    ok = ok && encode_2d(&mhi, Phi, k_total, l_pad, ldp * 4, kBK, l_pad, CU_TENSOR_MAP_SWIZZLE_128B);
-    ok = ok && encode_2d(&mlo, Plo, k_total, l_pad, ldp * 4, kBK, l_pad, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (bf) {
+        ok = ok && encode_2d(&mhi, Phi, k_total, l_pad, ldp * 2, kBK, l_pad, CU_TENSOR_MAP_SWIZZLE_64B,
+                             CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+        mlo = mhi;
+    } else {
+        ok = ok && encode_2d(&mhi, Phi, k_total, l_pad, ldp * 4, kBK, l_pad, CU_TENSOR_MAP_SWIZZLE_128B);
+        ok = ok && encode_2d(&mlo, Plo, k_total, l_pad, ldp * 4, kBK, l_pad, CU_TENSOR_MAP_SWIZZLE_128B);
+    }
     if (!ok) return RSVDGB_ERR_CUDA;
 
     TcParams p{};
@@ -633,21 +730,28 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
     else
         grid = dim3((unsigned)units, (unsigned)splits);
     if (splits_out) *splits_out = direct ? 0 : splits;
-    switch ((trans ? 8 : 0) + G) {
-        case 1: return launch_typed<false, 1>(s, mA, mhi, mlo, p, grid, smem);
-        case 2: return launch_typed<false, 2>(s, mA, mhi, mlo, p, grid, smem);
-        case 3: return launch_typed<false, 3>(s, mA, mhi, mlo, p, grid, smem);
-        case 9: return launch_typed<true, 1>(s, mA, mhi, mlo, p, grid, smem);
-        case 10: return launch_typed<true, 2>(s, mA, mhi, mlo, p, grid, smem);
-        case 11: return launch_typed<true, 3>(s, mA, mhi, mlo, p, grid, smem);
+    switch ((bf ? 16 : 0) + (trans ? 8 : 0) + G) {
+        case 1: return launch_typed<false, 1, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 2: return launch_typed<false, 2, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 3: return launch_typed<false, 3, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 9: return launch_typed<true, 1, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 10: return launch_typed<true, 2, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 11: return launch_typed<true, 3, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 17: return launch_typed<false, 1, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 18: return launch_typed<false, 2, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 19: return launch_typed<false, 3, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 25: return launch_typed<true, 1, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 26: return launch_typed<true, 2, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 27: return launch_typed<true, 3, true>(s, mA, mhi, mlo, p, grid, smem);
         default: return RSVDGB_ERR_UNSUPPORTED;
     }
 }
 
+
 int64_t tc_pass_max_splits(int64_t m, int64_t n, int l_pad, int sm_count)
 {
     // automatic split count of an A^T X launch on an m x n matrix
-    const int G = groups_for(l_pad);
+    const int G = std::max(groups_for(l_pad, false), groups_for(l_pad, true));
     const int64_t units = ceil_div(ceil_div(n, kTileRows), G);
     int64_t splits = std::max<int64_t>(1, (int64_t)sm_count / units);
     splits = std::min<int64_t>(splits, std::max<int64_t>(1, m / (4 * kBK)));

@@ -92,3 +92,47 @@ def test_tc_and_simt_engines_agree(rs, handle):
     d2, U2, V2, _ = rs.rsvdgb_rsvd(handle, Ad, 30, opts=rs.make_opts(engine="simt"))
     d1, d2 = d1.cpu().numpy(), d2.cpu().numpy()
     assert np.max(np.abs(d1 - d2)) <= 2e-5 * d2[0]
+
+
+@pytest.mark.parametrize("m,n,l", [(300, 200, 30), (1030, 516, 220), (4096, 256, 100), (520, 332, 8)])
+def test_bf16_passes_match_oracle_products(rs, handle, m, n, l):
+    """BF16 products: both operands rounded to nearest BF16 (relative error
+    <= 2^-9 each), FP32 accumulation: |Y - Y_o| <= (2^-8 + 2 K u32) |A||X|."""
+    rng = np.random.default_rng(11 * m + n + l)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    X = rng.standard_normal((n, l)).astype(np.float32)
+    W = rng.standard_normal((m, l)).astype(np.float32)
+    Ad = to_dev(A)
+    Y = rs.rsvdgb_pass_ax(handle, Ad, to_dev(X), engine="tc", prec="bf16_sketch").cpu().numpy().astype(np.float64)
+    Z = rs.rsvdgb_pass_atx(handle, Ad, to_dev(W), engine="tc", prec="bf16_sketch").cpu().numpy().astype(np.float64)
+    Yo = oracle.gemm_ax(A, X.astype(np.float64))
+    Zo = oracle.gemm_atx(A, W.astype(np.float64))
+    Aa = np.abs(A).astype(np.float64)
+    by = (2.0 ** -8 + 2 * n * 2.0 ** -24) * (Aa @ np.abs(X))
+    bz = (2.0 ** -8 + 2 * m * 2.0 ** -24) * (Aa.T @ np.abs(W))
+    assert np.all(np.abs(Y - Yo) <= by)
+    assert np.all(np.abs(Z - Zo) <= bz)
+    # and it is not secretly FP32-accurate: BF16 rounding is visible
+    assert np.max(np.abs(Y - Yo) / by) > 1e-3
+
+
+@pytest.mark.parametrize("m,n,k,p,q", [(2000, 1000, 20, 10, 2), (3000, 512, 100, 10, 2), (800, 300, 16, 8, 1)])
+def test_bf16_sketch_rsvd_equal_error(rs, handle, m, n, k, p, q):
+    """Mixed precision (BF16 sketch and power passes, FP32-accurate projection):
+    ||A - U S V^T||_F <= 1.01 x the oracle's at the same (k, p, q)."""
+    import torch
+    if (m, n) == (2000, 1000):
+        A = inputs.small_planted()
+    else:
+        A = inputs.planted(m, n, inputs.exp_spectrum(min(m, n), 2.0 / k), seed=m + n)
+    d_o, U_o, V_o = oracle.rsvd(A, k, p=p, q=q, seed=3)
+    err_o = np.sqrt(oracle.residual_fro2(A, U_o, d_o, V_o))
+    d, U, V, info = rs.rsvdgb_rsvd(handle, to_dev(A), k,
+                                   opts=rs.make_opts(p=p, q=q, seed=3, prec="bf16_sketch"))
+    torch.cuda.synchronize()
+    assert info.status == 0 and info.engine == 2
+    err = np.sqrt(oracle.residual_fro2(A, U.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.float64),
+                                       V.cpu().numpy().astype(np.float64)))
+    assert err <= 1.01 * err_o, (err, err_o)
+    # the device's own estimate of the rank-k error agrees with the explicit residual
+    assert abs(np.sqrt(max(info.err2_k, 0.0)) - err) <= 1e-3 * np.sqrt(oracle.fro2(A)) + 1e-3 * err
