@@ -295,6 +295,33 @@ def main():
                     "tensor_view": {"achieved_tflops_algorithmic": achieved_tflops,
                                     "tf32_flops_issued_per_algorithmic": 3.0 * (((l + 15) // 16) * 16) / l}}
 
+    # ---------------- the other precision at equal error (same A, same Omega) ----------------
+    variants = {}
+    other = "bf16_sketch" if args.prec == "fp32" else "fp32"
+    try:
+        o2 = rs.make_opts(p=wl["p"], q=wl["q"], seed=rank, prec=other, engine=args.engine)
+        for _ in range(2):
+            rs.rsvdgb_rsvd(h, A, k, opts=o2, out=bufs, sync_info=False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nv = max(3, args.steps // 2)
+        for _ in range(nv):
+            rs.rsvdgb_rsvd(h, A, k, opts=o2, out=bufs, sync_info=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        info2 = rs._info_from(bufs[3])
+        err_main = float(np.sqrt(max(info.err2_k, 0.0)))
+        err_other = float(np.sqrt(max(info2.err2_k, 0.0)))
+        variants = {
+            args.prec: {"ms": ms_per_step, "err_k_fro": err_main},
+            other: {"ms": e0.elapsed_time(e1) / nv, "err_k_fro": err_other,
+                    "err_ratio_vs_" + args.prec: err_other / err_main if err_main > 0 else None},
+        }
+    except Exception as exc:  # a variant the build does not serve
+        variants = {other: {"unavailable": str(exc)}}
+
     # ---------------- end to end through the host-buffer entry point ----------------
     e2e = None
     if args.e2e_steps > 0:
@@ -338,6 +365,7 @@ def main():
                 "roofline": roofline,
                 "pass_kernels": {"launches": pass_n, "avg_ms": pass_avg_ms, "share_of_step":
                                  pass_ms / max(elapsed, 1e-9) if world == 1 else None},
+                "variants": variants,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                 "info": info.as_dict()}
         print(json.dumps(line), flush=True)

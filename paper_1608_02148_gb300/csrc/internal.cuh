@@ -126,10 +126,9 @@ void launch_small_matmul(cudaStream_t s, const float* A, const float* B, float* 
 // One-sided Jacobi SVD of the l x l FP32 matrix M (row-major): M J = W with
 // orthogonal columns.  Outputs (sorted by descending sigma):
 //   sigma[l] (FP32), Ut (l x l row-major, Ut[:,c] = W[:,c] / sigma_c),
-//   Jt (l x l row-major, the accumulated rotations, column c = right vector).
-// Also writes the first k values to d (float) and sum-of-squares diagnostics.
+//   Jt (l x l row-major, right vectors; only the first kv columns written).
 void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, float* Ut, float* Jt, float* work,
-                       int* sweeps);
+                       int* sweeps, int kv);
 // FP64 -> FP32 copy of an l x l row-major matrix, optionally transposed.
 void launch_small_d2f(cudaStream_t s, const double* in, float* out, int l, bool transpose);
 // Transpose an l x l row-major matrix: out = in^T.

@@ -394,10 +394,10 @@ void times_small(cudaStream_t s, int sm, const float* Xt, int64_t ld, int64_t ro
 void cholqr2(cudaStream_t s, int sm, Work& w, const float* Xt, int64_t ld, int64_t rows, int l, float* tmp, float* Qt)
 {
     gram(s, sm, Xt, ld, rows, l, w.part, w.G);
-    launch_chol_inv(s, w.G, l, 0.f, nullptr, w.T1, w.status, w.breakdowns);
+    launch_chol_inv(s, w.G, l, 0.f, w.R1, w.T1, w.status, w.breakdowns);
     times_small(s, sm, Xt, ld, rows, l, w.T1, tmp, w.part);
     gram(s, sm, tmp, ld, rows, l, w.part, w.G);
-    launch_chol_inv(s, w.G, l, 0.f, nullptr, w.T2, w.status, w.breakdowns);
+    launch_chol_inv(s, w.G, l, 0.f, w.R2, w.T2, w.status, w.breakdowns);
     times_small(s, sm, tmp, ld, rows, l, w.T2, Qt, w.part);
 }
 
@@ -444,7 +444,7 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
     for (int it = 0; it < q; ++it) {
         // Q = qr(Y): only the span is carried forward, so one Cholesky step
         // (Q = Y T); A^T Q = (A^T Y) T.
-        launch_chol_inv(s, w.G, l, 0.f, nullptr, w.T, w.status, w.breakdowns);
+        launch_chol_inv(s, w.G, l, 0.f, w.R1, w.T, w.status, w.breakdowns);
         apply_At(h, g, w, false);
         times_small(s, sm, w.Wt, g.ldn, g.n, l, w.T, w.Zt, w.part);
         // Q = qr(A^T Q): CholeskyQR2 on the n side, result in the panel
@@ -459,7 +459,7 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
     }
     // step 9: Q = qr(Y) with CholeskyQR2 (the first Gram is already in G):
     // Y1 = Y T1, G = Y1^T Y1, Q = Y1 T2.  Q ends up in Yt.
-    launch_chol_inv(s, w.G, l, 0.f, nullptr, w.T1, w.status, w.breakdowns);
+    launch_chol_inv(s, w.G, l, 0.f, w.R1, w.T1, w.status, w.breakdowns);
     if (g.use_tc) {
         tc_times_small(h, g, w, w.Yt, g.ldm, g.m, w.T1, w.Qt, w.Qth, w.Qtl);
         tc_gram(h, g, w, w.Qt, w.Qth, w.Qtl, g.ldm, g.m);
@@ -467,7 +467,7 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
         times_small(s, sm, w.Yt, g.ldm, g.m, l, w.T1, w.Qt, w.part);
         gram(s, sm, w.Qt, g.ldm, g.m, l, w.part, w.G);
     }
-    launch_chol_inv(s, w.G, l, 0.f, nullptr, w.T2, w.status, w.breakdowns);
+    launch_chol_inv(s, w.G, l, 0.f, w.R2, w.T2, w.status, w.breakdowns);
     if (g.use_tc)
         tc_times_small(h, g, w, w.Qt, g.ldm, g.m, w.T2, w.Yt, w.Yth, w.Ytl);
     else
@@ -486,7 +486,7 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
         cholqr2(s, sm, w, w.Wt, g.ldn, g.n, l, w.Zt, w.Pt);
         cross_gram(s, sm, w.Pt, w.Wt, g.ldn, g.n, l, w.part, w.G);
         launch_small_d2f(s, w.G, w.M, l, true);
-        launch_jacobi_svd(s, w.M, l, w.sigma, w.Ut, w.Jt, w.jwork, w.sweeps);
+        launch_jacobi_svd(s, w.M, l, w.sigma, w.Ut, w.Jt, w.jwork, w.sweeps, o.nV);
         // U = Q Ut (Eq. UQU) and V = Q_B J, truncated
         if (o.nU > 0) {
             if (g.use_tc) {

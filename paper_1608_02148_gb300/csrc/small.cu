@@ -194,17 +194,25 @@ __device__ __forceinline__ float warp_sum(float v)
 
 // EPL = ceil(L / 16): column elements per half-warp lane, held in registers
 // while a pair is rotated.
+//
+// The right singular vectors J are needed for kv columns only.  The sweeps
+// first run on M alone (half the shared-memory traffic); when the spectrum
+// allows it, J_c = M^T U_c / sigma_c for the kv leading columns (its error is
+// about u32 sigma_1 / sigma_c, accepted while sigma_kv >= 1e-3 sigma_1).
+// Otherwise the sweeps are repeated from the original M with J accumulated.
 template <int EPL, int NT>
 __global__ void __launch_bounds__(NT)
     jacobi_kernel(const float* __restrict__ M, int l, int L, float* __restrict__ sigma, float* __restrict__ Ut,
-                  float* __restrict__ Jt, float* __restrict__ gwork, int use_smem, int* sweeps_out)
+                  float* __restrict__ Jt, float* __restrict__ gwork, int use_smem, int* sweeps_out, int kv)
 {
     extern __shared__ float sm[];
     float* Mc = use_smem ? sm : gwork;
     float* Jc = use_smem ? sm + (size_t)L * L : gwork + (size_t)L * L;
     __shared__ int rotated;
+    __shared__ int need_j;
     __shared__ float sv[256];
     __shared__ int rank[256];
+    __shared__ int col_of_rank[256];
     __shared__ float jn[256];
     __shared__ float wn[256];
     const int tid = threadIdx.x;
@@ -212,119 +220,169 @@ __global__ void __launch_bounds__(NT)
     constexpr int nwarps = NT / 32;
     const int half = lane >> 4, hl = lane & 15;  // half-warp: one column pair
 
-    // column-major copies, zero padded to L x L
-    for (int e = tid; e < L * L; e += NT) {
-        const int c = e / L, i = e % L;
-        Mc[e] = (i < l && c < l) ? M[i * l + c] : 0.f;
-        Jc[e] = (i == c) ? 1.f : 0.f;
-    }
-    __syncthreads();
-
     // rotate a pair only when its cosine exceeds the FP32 noise of the dot
     // products (about sqrt(L) u32); quadratic convergence does the rest.
-    // Rotations use fast reciprocal / square-root intrinsics: c^2 + s^2 = 1
-    // only to a few ulps, a scaling that hits a column of M and the same
-    // column of J alike and is divided out at the end.
+    // c = 1 / sqrt(1 + t^2) in IEEE arithmetic keeps c^2 + s^2 - 1 at the
+    // rounding level, so column norms drift only by a random walk of ulps.
     const float tol = 4.f * sqrtf((float)L) * 5.9604645e-8f;
     const int Lm1 = L - 1;
     int sweep = 0;
-    for (; sweep < 30; ++sweep) {
-        if (tid == 0) rotated = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool accj = (pass == 1);
+        // column-major copies, zero padded to L x L
+        for (int e = tid; e < L * L; e += NT) {
+            const int c = e / L, i = e % L;
+            Mc[e] = (i < l && c < l) ? M[i * l + c] : 0.f;
+            if (accj) Jc[e] = (i == c) ? 1.f : 0.f;
+        }
         __syncthreads();
-        for (int round = 0; round < Lm1; ++round) {
-            for (int base = 2 * warp; base < L / 2; base += 2 * nwarps) {
-                const int t = base + half;
-                const bool valid = t < L / 2;
-                int a = Lm1, b = round;
-                if (t != 0) {
-                    a = round + t;
-                    if (a >= Lm1) a -= Lm1;
-                    b = round - t;
-                    if (b < 0) b += Lm1;
-                }
-                float xa[EPL], xb[EPL];
-                float al = 0.f, be = 0.f, ga = 0.f;
-                if (valid) {
-                    const float* ma = Mc + (size_t)a * L;
-                    const float* mb = Mc + (size_t)b * L;
-#pragma unroll
-                    for (int e = 0; e < EPL; ++e) {
-                        const int i = hl + 16 * e;
-                        xa[e] = (i < L) ? ma[i] : 0.f;
-                        xb[e] = (i < L) ? mb[i] : 0.f;
-                        al = fmaf(xa[e], xa[e], al);
-                        be = fmaf(xb[e], xb[e], be);
-                        ga = fmaf(xa[e], xb[e], ga);
+        for (sweep = 0; sweep < 30; ++sweep) {
+            if (tid == 0) rotated = 0;
+            __syncthreads();
+            for (int round = 0; round < Lm1; ++round) {
+                for (int base = 2 * warp; base < L / 2; base += 2 * nwarps) {
+                    const int t = base + half;
+                    const bool valid = t < L / 2;
+                    int a = Lm1, b = round;
+                    if (t != 0) {
+                        a = round + t;
+                        if (a >= Lm1) a -= Lm1;
+                        b = round - t;
+                        if (b < 0) b += Lm1;
                     }
-                }
+                    float xa[EPL], xb[EPL];
+                    float al = 0.f, be = 0.f, ga = 0.f;
+                    if (valid) {
+                        const float* ma = Mc + (size_t)a * L;
+                        const float* mb = Mc + (size_t)b * L;
 #pragma unroll
-                for (int o = 8; o > 0; o >>= 1) {
-                    al += __shfl_xor_sync(0xffffffffu, al, o);
-                    be += __shfl_xor_sync(0xffffffffu, be, o);
-                    ga += __shfl_xor_sync(0xffffffffu, ga, o);
-                }
-                if (valid && ga != 0.f && fabsf(ga) > tol * sqrtf(al * be)) {
-                    const float zeta = __fdividef(be - al, 2.f * ga);
-                    const float tt = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-                    const float c = rsqrtf(fmaf(tt, tt, 1.f));
-                    const float sn = c * tt;
-                    float* ma = Mc + (size_t)a * L;
-                    float* mb = Mc + (size_t)b * L;
-                    float* ja = Jc + (size_t)a * L;
-                    float* jb = Jc + (size_t)b * L;
-#pragma unroll
-                    for (int e = 0; e < EPL; ++e) {
-                        const int i = hl + 16 * e;
-                        if (i < L) {
-                            ma[i] = c * xa[e] - sn * xb[e];
-                            mb[i] = sn * xa[e] + c * xb[e];
-                            const float ya = ja[i], yb = jb[i];
-                            ja[i] = c * ya - sn * yb;
-                            jb[i] = sn * ya + c * yb;
+                        for (int e = 0; e < EPL; ++e) {
+                            const int i = hl + 16 * e;
+                            xa[e] = (i < L) ? ma[i] : 0.f;
+                            xb[e] = (i < L) ? mb[i] : 0.f;
+                            al = fmaf(xa[e], xa[e], al);
+                            be = fmaf(xb[e], xb[e], be);
+                            ga = fmaf(xa[e], xb[e], ga);
                         }
                     }
-                    if (hl == 0) rotated = 1;
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1) {
+                        al += __shfl_xor_sync(0xffffffffu, al, o);
+                        be += __shfl_xor_sync(0xffffffffu, be, o);
+                        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                    }
+                    if (valid && ga != 0.f && fabsf(ga) > tol * sqrtf(al * be)) {
+                        const float zeta = (be - al) / (2.f * ga);
+                        const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+                        const float c = 1.0f / sqrtf(fmaf(tt, tt, 1.f));
+                        const float sn = c * tt;
+                        float* ma = Mc + (size_t)a * L;
+                        float* mb = Mc + (size_t)b * L;
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) {
+                            const int i = hl + 16 * e;
+                            if (i < L) {
+                                ma[i] = c * xa[e] - sn * xb[e];
+                                mb[i] = sn * xa[e] + c * xb[e];
+                            }
+                        }
+                        if (accj) {
+                            float* ja = Jc + (size_t)a * L;
+                            float* jb = Jc + (size_t)b * L;
+#pragma unroll
+                            for (int e = 0; e < EPL; ++e) {
+                                const int i = hl + 16 * e;
+                                if (i < L) {
+                                    const float ya = ja[i], yb = jb[i];
+                                    ja[i] = c * ya - sn * yb;
+                                    jb[i] = sn * ya + c * yb;
+                                }
+                            }
+                        }
+                        if (hl == 0) rotated = 1;
+                    }
+                }
+                __syncthreads();
+            }
+            if (!rotated) break;
+            __syncthreads();
+        }
+        // singular values.  Rounding in the rotations scales each column of
+        // W = M J by a factor close to 1 that accumulates over the sweeps.
+        // With J accumulated, sigma_c = ||W_c|| / ||J_c|| cancels it.  Without
+        // J, the direction u_c = W_c / ||W_c|| is unaffected and
+        // sigma_c = ||M^T u_c||, J_c = M^T u_c / sigma_c (stored in Jc).
+        for (int c = warp; c < L; c += nwarps) {
+            float s2 = 0.f, j2 = 0.f;
+            for (int i = lane; i < L; i += 32) {
+                s2 = fmaf(Mc[(size_t)c * L + i], Mc[(size_t)c * L + i], s2);
+                if (accj) j2 = fmaf(Jc[(size_t)c * L + i], Jc[(size_t)c * L + i], j2);
+            }
+            s2 = warp_sum(s2);
+            j2 = warp_sum(j2);
+            if (lane == 0) {
+                wn[c] = sqrtf(s2);
+                jn[c] = accj ? sqrtf(j2) : 1.f;
+                sv[c] = accj ? ((j2 > 0.f) ? sqrtf(s2) / sqrtf(j2) : 0.f) : sqrtf(s2);
+            }
+        }
+        __syncthreads();
+        if (!accj) {
+            for (int e = tid; e < L * L; e += NT) {
+                const int c = e / L, i = e % L;
+                float acc = 0.f;
+                if (i < l && c < l && wn[c] > 0.f) {
+                    const float* w = Mc + (size_t)c * L;
+                    for (int t = 0; t < l; ++t) acc = fmaf(M[t * l + i], w[t], acc);
+                    acc /= wn[c];
+                }
+                Jc[e] = acc;  // x_c = M^T u_c
+            }
+            __syncthreads();
+            for (int c = warp; c < L; c += nwarps) {
+                float x2 = 0.f;
+                for (int i = lane; i < L; i += 32) x2 = fmaf(Jc[(size_t)c * L + i], Jc[(size_t)c * L + i], x2);
+                x2 = warp_sum(x2);
+                if (lane == 0) {
+                    sv[c] = sqrtf(x2);
+                    jn[c] = sqrtf(x2);
                 }
             }
             __syncthreads();
         }
-        if (!rotated) break;
+        for (int c = tid; c < L; c += NT) {
+            int r = 0;
+            for (int o = 0; o < L; ++o) r += (sv[o] > sv[c]) || (sv[o] == sv[c] && o < c);
+            rank[c] = r;
+            col_of_rank[r] = c;
+        }
         __syncthreads();
+        if (tid == 0 && !accj) {
+            const float s1 = sv[col_of_rank[0]];
+            const float skv = kv > 0 ? sv[col_of_rank[min(kv, l) - 1]] : s1;
+            need_j = (kv > 0 && !(skv >= 1e-3f * s1)) ? 1 : 0;  // stays set after the J pass
+        }
+        __syncthreads();
+        if (!need_j || accj) break;
     }
     if (tid == 0 && sweeps_out) *sweeps_out = sweep + 1;
-    // Singular values.  sigma_c = ||W_c|| / ||J_c|| with W = M J divides out
-    // the common scale drift of a column of W and of J; J_c is renormalised.
-    for (int c = warp; c < L; c += nwarps) {
-        float s2 = 0.f, j2 = 0.f;
-        for (int i = lane; i < L; i += 32) {
-            s2 = fmaf(Mc[(size_t)c * L + i], Mc[(size_t)c * L + i], s2);
-            j2 = fmaf(Jc[(size_t)c * L + i], Jc[(size_t)c * L + i], j2);
-        }
-        s2 = warp_sum(s2);
-        j2 = warp_sum(j2);
-        if (lane == 0) {
-            wn[c] = sqrtf(s2);
-            jn[c] = sqrtf(j2);
-            sv[c] = (j2 > 0.f) ? sqrtf(s2) / sqrtf(j2) : 0.f;
-        }
-    }
-    __syncthreads();
-    for (int c = tid; c < L; c += NT) {
-        int r = 0;
-        for (int o = 0; o < L; ++o) r += (sv[o] > sv[c]) || (sv[o] == sv[c] && o < c);
-        rank[c] = r;
-    }
-    __syncthreads();
     for (int e = tid; e < L * L; e += NT) {
         const int c = e / L, i = e % L;
         const int r = rank[c];
         if (r >= l || i >= l) continue;
         const float w = wn[c];
         Ut[i * l + r] = (w > 0.f) ? Mc[(size_t)c * L + i] / w : 0.f;
-        Jt[i * l + r] = (jn[c] > 0.f) ? Jc[(size_t)c * L + i] / jn[c] : 0.f;
     }
     for (int c = tid; c < L; c += NT)
         if (rank[c] < l) sigma[rank[c]] = sv[c];
+    if (kv <= 0) return;
+    // right vectors for the kv leading ranks: accumulated J, or M^T u_c normalised
+    for (int e = tid; e < L * L; e += NT) {
+        const int c = e / L, i = e % L;
+        const int r = rank[c];
+        if (r >= kv || r >= l || i >= l) continue;
+        Jt[i * l + r] = (jn[c] > 0.f) ? Jc[(size_t)c * L + i] / jn[c] : 0.f;
+    }
 }
 
 __global__ void finalize_info_kernel(const float* __restrict__ sigma, int l, int k, float* __restrict__ d,
@@ -515,29 +573,29 @@ void launch_small_transpose(cudaStream_t s, const float* in, float* out, int l)
 
 template <int EPL, int NT>
 void launch_jacobi_typed(cudaStream_t s, const float* M, int l, int L, float* sigma, float* Ut, float* Jt,
-                         float* work, int* sweeps)
+                         float* work, int* sweeps, int kv)
 {
     const size_t need = (size_t)2 * L * L * sizeof(float);
     const int use_smem = need <= (size_t)216 * 1024;
-    jacobi_kernel<EPL, NT><<<1, NT, use_smem ? need : 0, s>>>(M, l, L, sigma, Ut, Jt, work, use_smem, sweeps);
+    jacobi_kernel<EPL, NT><<<1, NT, use_smem ? need : 0, s>>>(M, l, L, sigma, Ut, Jt, work, use_smem, sweeps, kv);
 }
 
 void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, float* Ut, float* Jt, float* work,
-                       int* sweeps)
+                       int* sweeps, int kv)
 {
     const int L = (int)round_up(l, 2);
     switch ((L + 15) / 16) {
-        case 1: launch_jacobi_typed<1, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
-        case 2: launch_jacobi_typed<2, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
-        case 3: launch_jacobi_typed<3, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
-        case 4: launch_jacobi_typed<4, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
-        case 5: launch_jacobi_typed<5, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
-        case 6: launch_jacobi_typed<6, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
-        case 7: launch_jacobi_typed<7, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
-        case 8: launch_jacobi_typed<8, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
-        case 9: case 10: launch_jacobi_typed<10, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
-        case 11: case 12: launch_jacobi_typed<12, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
-        default: launch_jacobi_typed<14, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps); break;
+        case 1: launch_jacobi_typed<1, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
+        case 2: launch_jacobi_typed<2, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
+        case 3: launch_jacobi_typed<3, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
+        case 4: launch_jacobi_typed<4, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
+        case 5: launch_jacobi_typed<5, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
+        case 6: launch_jacobi_typed<6, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
+        case 7: launch_jacobi_typed<7, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
+        case 8: launch_jacobi_typed<8, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
+        case 9: case 10: launch_jacobi_typed<10, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
+        case 11: case 12: launch_jacobi_typed<12, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
+        default: launch_jacobi_typed<14, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
     }
     count_launches();
 }
