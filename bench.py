@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=40000, help="row sample for the oracle baseline")
+    ap.add_argument("--batched", type=int, default=4096, help="matrices in the batched workload (0 = skip)")
     return ap.parse_args()
 
 
@@ -159,6 +160,49 @@ def make_matrix(wl, seed, device):
         return inputs.spiked_noise(m, n, sigma, wl["noise"], seed, device=device)
     import torch
     return torch.from_numpy(inputs.planted(m, n, inputs.exp_spectrum(n, 1.0 / 20.0), seed)).to(device)
+
+
+def run_batched(rs, h, dev, stream, count, steps, peaks):
+    """Batched rSVD of `count` matrices, m log-uniform in [256, 4096], n in
+    [64, 1024], exponential spectra with rates uniform in [0.05, 0.5];
+    k = 16, p = 8, q = 1; one graph launch per step."""
+    import torch
+    from paper_1608_02148_gb300 import inputs
+    k, p, q = 16, 8, 1
+    t0 = time.perf_counter()
+    mats, _ = inputs.ragged_batch(count, seed=0x160802148 + 4000, device=dev)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    call = rs.BatchedCall(mats, k)
+    opts = rs.make_opts(p=p, q=q, seed=3)
+    t0 = time.perf_counter()
+    rs.rsvdgb_rsvd_batched(h, call, opts)  # plan, tuning, graph capture
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    for _ in range(2):
+        rs.rsvdgb_rsvd_batched(h, call, opts)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n = max(3, steps // 2)
+    l0 = rs.rsvdgb_kernel_launches()
+    e0.record(stream)
+    for _ in range(n):
+        rs.rsvdgb_rsvd_batched(h, call, opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    launches = (rs.rsvdgb_kernel_launches() - l0) / n
+    a_bytes = sum(A.numel() * 4 for A in mats)
+    passes = 2 * q + 2
+    roof_ms = passes * a_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3
+    bad = sum(1 for b in range(0, count, max(1, count // 64)) if call.info(b).status != 0)
+    return {"workload": f"batched rsvd of {count} matrices, m in [256,4096], n in [64,1024] log-uniform, "
+                        f"exp spectra rate U[0.05,0.5], k={k} p={p} q={q}, fp32",
+            "ms": ms, "matrices_per_s": count / (ms * 1e-3), "a_bytes": a_bytes, "passes_over_A": passes,
+            "hbm_roofline_ms": roof_ms, "hbm_frac": roof_ms / ms, "graph_launches_per_step": 1,
+            "kernels_per_step": launches, "plan_build_s": plan_s, "input_generation_s": gen_s,
+            "status_nonzero_sampled": bad}
 
 
 def cpu_oracle_time(A_host_rows, wl, seed_omega):
@@ -322,6 +366,14 @@ def main():
     except Exception as exc:  # a variant the build does not serve
         variants = {other: {"unavailable": str(exc)}}
 
+    # ---------------- batched workload: 4096 ragged matrices, one graph launch ----------------
+    batched = None
+    if args.batched > 0 and rank == 0:
+        try:
+            batched = run_batched(rs, h, dev, stream, args.batched, args.steps, peaks)
+        except Exception as exc:
+            batched = {"unavailable": str(exc)}
+
     # ---------------- end to end through the host-buffer entry point ----------------
     e2e = None
     if args.e2e_steps > 0:
@@ -366,6 +418,7 @@ def main():
                 "pass_kernels": {"launches": pass_n, "avg_ms": pass_avg_ms, "share_of_step":
                                  pass_ms / max(elapsed, 1e-9) if world == 1 else None},
                 "variants": variants,
+                "batched": batched,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                 "info": info.as_dict()}
         print(json.dumps(line), flush=True)

@@ -150,6 +150,45 @@ int rsvdgb_rsvd_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int6
                      int nv, const rsvdgb_opts* opts, float* d, float* U, int64_t ldu, float* V, int64_t ldv,
                      rsvdgb_info* info);
 
+/* One matrix of a batch: device pointer to A (m x n row-major, lda >= n). */
+typedef struct rsvdgb_matrix_desc {
+    const void* A;
+    int64_t m;
+    int64_t n;
+    int64_t lda;
+    int32_t dtype;     /* RSVDGB_F32 (the batched path reads FP32 only) */
+    int32_t reserved;
+} rsvdgb_matrix_desc;
+
+/* Outputs of one matrix of a batch (device pointers; U or V may be NULL). */
+typedef struct rsvdgb_result_desc {
+    float* d;          /* k singular values, descending            */
+    float* U;          /* m x k row-major, leading dimension ldu    */
+    int64_t ldu;
+    float* V;          /* n x k row-major, leading dimension ldv    */
+    int64_t ldv;
+} rsvdgb_result_desc;
+
+/*
+ * Algorithm rSVD (Sec. 3.3) on a batch of `batch` matrices of uneven shapes
+ * with one target rank k and one set of options (p, q, sdist, seed; each
+ * matrix uses l = min(k + p, min(m, n)), which must be <= 32).
+ *   descs, outs  HOST arrays of `batch` descriptors holding device pointers.
+ *   infos        device array of `batch` rsvdgb_info, or NULL.
+ * Every step of the method runs as one grouped kernel over the whole batch
+ * (work items: matrix x row block / column block); the steps are captured in
+ * a CUDA graph per batch layout and replayed with one graph launch.  The
+ * first call with a new layout (descriptor contents, k, options) builds a plan
+ * (device descriptor and work-item tables, scratch pools), tunes the grid of
+ * the grouped kernels with a few timed runs and captures the graph; it
+ * synchronises the handle's stream once.  Later calls with the same layout
+ * are asynchronous.  FP32 arithmetic (FMA); Omega as in rsvdgb_omega per
+ * matrix.  Returns RSVDGB_OK, RSVDGB_ERR_INVALID_ARG, RSVDGB_ERR_UNSUPPORTED
+ * (l > 32 or non-FP32 data), RSVDGB_ERR_NOMEM or RSVDGB_ERR_CUDA.
+ */
+int rsvdgb_rsvd_batched(rsvdgb_handle* h, int batch, const rsvdgb_matrix_desc* descs, int k, const rsvdgb_opts* opts,
+                        const rsvdgb_result_desc* outs, rsvdgb_info* infos);
+
 /*
  * Algorithm rqb (Sec. 3.3): A ~ Q B with Q (m x l) orthonormal and
  * B = Q^T A (l x n), Eq. BQA.  Q is written row-major m x l (ldq >= l), B

@@ -150,4 +150,11 @@ void launch_colmajor_to_rowmajor(cudaStream_t s, const float* in, int64_t ld, in
 void launch_rowmajor_to_colmajor(cudaStream_t s, const float* in, int64_t ldi, int64_t rows, int cols, int cols_pad,
                                  float* out, int64_t ld);
 
+// Batched rSVD (batched.cu): plan cache owned by the handle.
+struct BatchedPlan;
+void destroy_plan(BatchedPlan* pl);
+int batched_rsvd(BatchedPlan** cache, int device, int sm_count, cudaStream_t stream, int B,
+                 const rsvdgb_matrix_desc* descs, int k, const rsvdgb_opts& o, const rsvdgb_result_desc* outs,
+                 rsvdgb_info* infos);
+
 }  // namespace rsvdgb

@@ -53,6 +53,7 @@ struct rsvdgb_handle {
     void* host_stage = nullptr;  // device buffers for the *_host entry points
     size_t host_stage_bytes = 0;
     PassProfile prof;
+    BatchedPlan* batched = nullptr;  // plan of the last batch layout
 };
 
 namespace {
@@ -631,6 +632,7 @@ int rsvdgb_destroy(rsvdgb_handle* h)
     if (h->ws) cudaFree(h->ws);
     if (h->host_stage) cudaFree(h->host_stage);
     for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
+    destroy_plan(h->batched);
     delete h;
     return RSVDGB_OK;
 }
@@ -851,6 +853,31 @@ int rsvdgb_pass_atx(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64
                     int64_t ldx, int l, float* Z, int64_t ldz, int engine, int prec)
 {
     return pass_common(h, A, m, n, lda, dtype, X, ldx, l, Z, ldz, engine, prec, true);
+}
+
+int rsvdgb_rsvd_batched(rsvdgb_handle* h, int batch, const rsvdgb_matrix_desc* descs, int k, const rsvdgb_opts* opts,
+                        const rsvdgb_result_desc* outs, rsvdgb_info* infos)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (batch < 1 || !descs || !outs || k < 1) return RSVDGB_ERR_INVALID_ARG;
+    rsvdgb_opts o;
+    if (opts)
+        o = *opts;
+    else
+        rsvdgb_default_opts(&o);
+    if (o.p < 0 || o.q < 0 || o.q > 8 || o.sdist < 0 || o.sdist > 2) return RSVDGB_ERR_INVALID_ARG;
+    if (o.layout != RSVDGB_ROW_MAJOR) return RSVDGB_ERR_UNSUPPORTED;
+    for (int b = 0; b < batch; ++b) {
+        const rsvdgb_matrix_desc& d = descs[b];
+        const rsvdgb_result_desc& r = outs[b];
+        if (!d.A || d.m < 1 || d.n < 1 || d.lda < d.n || !aligned(d.A, 4)) return RSVDGB_ERR_INVALID_ARG;
+        if (d.dtype != RSVDGB_F32) return RSVDGB_ERR_UNSUPPORTED;
+        if (k >= std::min(d.m, d.n)) return RSVDGB_ERR_INVALID_ARG;
+        if (std::min<int64_t>((int64_t)k + o.p, std::min(d.m, d.n)) > 32) return RSVDGB_ERR_UNSUPPORTED;
+        if (!r.d || (r.U && r.ldu < k) || (r.V && r.ldv < k)) return RSVDGB_ERR_INVALID_ARG;
+    }
+    return batched_rsvd(&h->batched, h->device, h->sm_count, h->stream, batch, descs, k, o, outs, infos);
 }
 
 int rsvdgb_profile_passes(rsvdgb_handle* h, int enable)

@@ -117,3 +117,40 @@ def ragged_shapes(count: int, m_range, n_range, seed: int):
     ns = np.rint(np.exp(ln)).astype(np.int64)
     rates = rng.uniform(0.05, 0.5, count)
     return ms, ns, rates
+
+
+def ragged_batch(count: int, m_range=(256, 4096), n_range=(64, 1024), seed: int = 0, device="cpu",
+                 shapes=None):
+    """Many matrices A_b = H_U S_b H_V with an exponential spectrum
+    sigma_i = exp(-r_b i) (r_b uniform in [0.05, 0.5]) and log-uniform shapes.
+
+    S_b holds sigma on a random partial permutation; H_U, H_V are products of
+    two random Householder reflectors, so A_b has exactly the planted singular
+    values (rotational invariance of the Gaussian sketch makes the choice of
+    orthogonal factors immaterial).  Built with torch on any device; returns
+    (list of float32 tensors, decay rates)."""
+    import torch
+
+    if shapes is None:
+        ms, ns, rates = ragged_shapes(count, m_range, n_range, seed)
+    else:
+        ms, ns, rates = shapes
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+    mats = []
+    for m, n, r in zip(ms.tolist(), ns.tolist(), rates.tolist()):
+        mn = min(m, n)
+        sig = torch.exp(-r * torch.arange(1, mn + 1, dtype=torch.float64, device=device))
+        pm = torch.randperm(m, generator=gen, device=device)[:mn]
+        pn = torch.randperm(n, generator=gen, device=device)[:mn]
+        A = torch.zeros(m, n, dtype=torch.float64, device=device)
+        A[pm, pn] = sig
+        for _ in range(2):
+            u = torch.randn(m, 1, generator=gen, device=device, dtype=torch.float64)
+            u /= u.norm()
+            A -= 2.0 * u @ (u.T @ A)
+            v = torch.randn(n, 1, generator=gen, device=device, dtype=torch.float64)
+            v /= v.norm()
+            A -= 2.0 * (A @ v) @ v.T
+        mats.append(A.to(torch.float32).contiguous())
+    return mats, rates

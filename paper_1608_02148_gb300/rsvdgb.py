@@ -27,7 +27,7 @@ LAYOUT = {"row": 0, "col": 1}
 EXPORTS = ["rsvdgb_create", "rsvdgb_destroy", "rsvdgb_set_stream", "rsvdgb_default_opts", "rsvdgb_status_string",
            "rsvdgb_sketch_width", "rsvdgb_rsvd", "rsvdgb_rsvd_host", "rsvdgb_rqb", "rsvdgb_omega",
            "rsvdgb_pass_ax", "rsvdgb_pass_atx", "rsvdgb_profile_passes", "rsvdgb_profile_read",
-           "rsvdgb_kernel_launches", "rsvdgb_pass_atx_noalloc"]
+           "rsvdgb_kernel_launches", "rsvdgb_pass_atx_noalloc", "rsvdgb_rsvd_batched"]
 
 # Static scratch of rsvdgb_pass_atx_noalloc (RSVDGB_NOALLOC_SCRATCH_BYTES).
 NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -51,6 +51,16 @@ class RsvdgbInfo(ctypes.Structure):
 
 
 INFO_BYTES = ctypes.sizeof(RsvdgbInfo)
+
+
+class RsvdgbMatrixDesc(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("lda", ctypes.c_int64),
+                ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class RsvdgbResultDesc(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_void_p), ("U", ctypes.c_void_p), ("ldu", ctypes.c_int64), ("V", ctypes.c_void_p),
+                ("ldv", ctypes.c_int64)]
 
 _lib = None
 
@@ -90,6 +100,8 @@ def load(path: Path | str | None = None):
     lib.rsvdgb_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64),
                                         ctypes.POINTER(ctypes.c_double)]
     lib.rsvdgb_pass_atx_noalloc.argtypes = [P, P, I64, I64, I64, I, P, I64, I, P, I64]
+    lib.rsvdgb_rsvd_batched.argtypes = [P, I, ctypes.POINTER(RsvdgbMatrixDesc), I, ctypes.POINTER(RsvdgbOpts),
+                                        ctypes.POINTER(RsvdgbResultDesc), P]
     lib.rsvdgb_kernel_launches.argtypes = []
     lib.rsvdgb_kernel_launches.restype = I64
     _lib = lib
@@ -315,3 +327,48 @@ def rsvdgb_pass_atx_noalloc(A, X, Z=None, stream=None):
                                         _dtype_code(A), X.data_ptr(), _rowmajor_ld(X), l, Z.data_ptr(), Z.stride(0))
     _check("rsvdgb_pass_atx_noalloc", rc)
     return Z
+
+
+class BatchedCall:
+    """Descriptors and output buffers of one batch, reusable across calls (the
+    library caches its plan and CUDA graph per batch layout)."""
+
+    def __init__(self, mats, k, with_uv=True):
+        torch = _torch()
+        self.mats = mats
+        self.k = k
+        B = len(mats)
+        self.descs = (RsvdgbMatrixDesc * B)()
+        self.outs = (RsvdgbResultDesc * B)()
+        self.d, self.U, self.V = [], [], []
+        dev = mats[0].device
+        for b, A in enumerate(mats):
+            m, n = A.shape
+            self.descs[b].A = A.data_ptr()
+            self.descs[b].m, self.descs[b].n, self.descs[b].lda = m, n, _rowmajor_ld(A)
+            self.descs[b].dtype = _dtype_code(A)
+            d = torch.empty(k, dtype=torch.float32, device=dev)
+            U = torch.empty(m, k, dtype=torch.float32, device=dev) if with_uv else None
+            V = torch.empty(n, k, dtype=torch.float32, device=dev) if with_uv else None
+            self.outs[b].d = d.data_ptr()
+            self.outs[b].U = U.data_ptr() if U is not None else None
+            self.outs[b].ldu = k
+            self.outs[b].V = V.data_ptr() if V is not None else None
+            self.outs[b].ldv = k
+            self.d.append(d)
+            self.U.append(U)
+            self.V.append(V)
+        self.infos = torch.zeros(B * INFO_BYTES, dtype=torch.uint8, device=dev)
+
+    def info(self, b):
+        raw = self.infos[b * INFO_BYTES:(b + 1) * INFO_BYTES]
+        return _info_from(raw)
+
+
+def rsvdgb_rsvd_batched(h: Handle, call: BatchedCall, opts: RsvdgbOpts | None = None):
+    """Batched rSVD of call.mats (k, opts shared); results land in call.d/U/V."""
+    opts = opts or make_opts()
+    rc = load().rsvdgb_rsvd_batched(h.ptr, len(call.mats), call.descs, call.k, ctypes.byref(opts), call.outs,
+                                    call.infos.data_ptr())
+    _check("rsvdgb_rsvd_batched", rc)
+    return call
