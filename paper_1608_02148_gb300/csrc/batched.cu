@@ -110,7 +110,7 @@ __device__ __forceinline__ void tile_cross(const float* Xs, const float* Ys, int
 // ------------------------------------------------------------------ Y = A_log P  (row-block items)
 // Y[i][:] = sum_j A_log(i, j) P[j][:] for RB logical rows; optional Gram partial
 // of the tile and ||A||_F^2 accumulation (per matrix, FP64 atomics).
-__global__ void __launch_bounds__(NT) pass_a_kernel(const MatDev* __restrict__ D, const Item* __restrict__ items,
+__global__ void __launch_bounds__(NT, 3) pass_a_kernel(const MatDev* __restrict__ D, const Item* __restrict__ items,
                                                     int nitems, int* cursor, const float* __restrict__ P,
                                                     float* __restrict__ Y, float* __restrict__ part,
                                                     double* __restrict__ fro2)
@@ -133,9 +133,13 @@ __global__ void __launch_bounds__(NT) pass_a_kernel(const MatDev* __restrict__ D
         const int rows = (int)min((int64_t)RB, Mt.M - r0);
         float acc[4][4] = {};
         float sq = 0.f;
-        for (int64_t k0 = 0; k0 < Mt.N; k0 += 32) {
-            // A chunk: RB rows x 32 columns of the logical matrix, k-major in smem
-            for (int e = tid; e < RB * 32; e += NT) {
+        // next chunk in registers while the current one is multiplied
+        constexpr int EA = RB * 32 / NT, EP = 32 * LB / NT;
+        float ra[EA], rp[EP];
+        auto load_chunk = [&](int64_t k0) {
+#pragma unroll
+            for (int q = 0; q < EA; ++q) {
+                const int e = tid + q * NT;
                 int i, kk;
                 if (Mt.trans) {  // logical row i = stored column: contiguous over i
                     i = e % RB;
@@ -144,16 +148,39 @@ __global__ void __launch_bounds__(NT) pass_a_kernel(const MatDev* __restrict__ D
                     kk = e % 32;
                     i = e / 32;
                 }
-                float v = 0.f;
-                if (i < rows && k0 + kk < Mt.N) v = aget(Mt, r0 + i, k0 + kk);
-                As[kk][i] = v;
-                sq = fmaf(v, v, sq);
+                ra[q] = (i < rows && k0 + kk < Mt.N) ? aget(Mt, r0 + i, k0 + kk) : 0.f;
             }
-            for (int e = tid; e < 32 * LB; e += NT) {
+#pragma unroll
+            for (int q = 0; q < EP; ++q) {
+                const int e = tid + q * NT;
                 const int kk = e >> 5, c = e & 31;
-                Ps[kk][c] = (k0 + kk < Mt.N) ? P[(Mt.offN + k0 + kk) * LB + c] : 0.f;
+                rp[q] = (k0 + kk < Mt.N) ? P[(Mt.offN + k0 + kk) * LB + c] : 0.f;
+            }
+        };
+        load_chunk(0);
+        for (int64_t k0 = 0; k0 < Mt.N; k0 += 32) {
+            // A chunk: RB rows x 32 columns of the logical matrix, k-major in smem
+#pragma unroll
+            for (int q = 0; q < EA; ++q) {
+                const int e = tid + q * NT;
+                int i, kk;
+                if (Mt.trans) {
+                    i = e % RB;
+                    kk = e / RB;
+                } else {
+                    kk = e % 32;
+                    i = e / 32;
+                }
+                As[kk][i] = ra[q];
+                sq = fmaf(ra[q], ra[q], sq);
+            }
+#pragma unroll
+            for (int q = 0; q < EP; ++q) {
+                const int e = tid + q * NT;
+                Ps[e >> 5][e & 31] = rp[q];
             }
             __syncthreads();
+            if (k0 + 32 < Mt.N) load_chunk(k0 + 32);
 #pragma unroll 8
             for (int kk = 0; kk < 32; ++kk) {
                 const float4 a4 = *(const float4*)&As[kk][4 * ty];
@@ -214,8 +241,12 @@ __global__ void __launch_bounds__(NT) pass_at_kernel(const MatDev* __restrict__ 
         const int64_t c0 = (int64_t)item.blk * CB;
         const int cols = (int)min((int64_t)CB, Mt.N - c0);
         float acc[2][4] = {};
-        for (int64_t i0 = 0; i0 < Mt.M; i0 += 32) {
-            for (int e = tid; e < 32 * CB; e += NT) {
+        constexpr int EA = 32 * CB / NT, EY = 32 * LB / NT;
+        float ra[EA], ry[EY];
+        auto load_chunk = [&](int64_t i0) {
+#pragma unroll
+            for (int q = 0; q < EA; ++q) {
+                const int e = tid + q * NT;
                 int ii, c;
                 if (Mt.trans) {  // A_log(i, c) = S[c][i]: contiguous over i
                     ii = e % 32;
@@ -224,15 +255,37 @@ __global__ void __launch_bounds__(NT) pass_at_kernel(const MatDev* __restrict__ 
                     c = e % CB;
                     ii = e / CB;
                 }
-                float v = 0.f;
-                if (c < cols && i0 + ii < Mt.M) v = aget(Mt, i0 + ii, c0 + c);
-                As[ii][c] = v;
+                ra[q] = (c < cols && i0 + ii < Mt.M) ? aget(Mt, i0 + ii, c0 + c) : 0.f;
             }
-            for (int e = tid; e < 32 * LB; e += NT) {
+#pragma unroll
+            for (int q = 0; q < EY; ++q) {
+                const int e = tid + q * NT;
                 const int ii = e >> 5, c = e & 31;
-                Ys[ii][c] = (i0 + ii < Mt.M) ? Y[(Mt.offM + i0 + ii) * LB + c] : 0.f;
+                ry[q] = (i0 + ii < Mt.M) ? Y[(Mt.offM + i0 + ii) * LB + c] : 0.f;
+            }
+        };
+        load_chunk(0);
+        for (int64_t i0 = 0; i0 < Mt.M; i0 += 32) {
+#pragma unroll
+            for (int q = 0; q < EA; ++q) {
+                const int e = tid + q * NT;
+                int ii, c;
+                if (Mt.trans) {
+                    ii = e % 32;
+                    c = e / 32;
+                } else {
+                    c = e % CB;
+                    ii = e / CB;
+                }
+                As[ii][c] = ra[q];
+            }
+#pragma unroll
+            for (int q = 0; q < EY; ++q) {
+                const int e = tid + q * NT;
+                Ys[e >> 5][e & 31] = ry[q];
             }
             __syncthreads();
+            if (i0 + 32 < Mt.M) load_chunk(i0 + 32);
 #pragma unroll 8
             for (int ii = 0; ii < 32; ++ii) {
                 const float2 a2 = *(const float2*)&As[ii][2 * ty];
@@ -256,6 +309,7 @@ __global__ void __launch_bounds__(NT) pass_at_kernel(const MatDev* __restrict__ 
         if (T) {
             // Z = W T, row by row (CB x 32 times 32 x 32)
             float z[8];
+#pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int e = tid + q * NT;
                 const int r = e >> 5, c = e & 31;
@@ -264,6 +318,7 @@ __global__ void __launch_bounds__(NT) pass_at_kernel(const MatDev* __restrict__ 
                 z[q] = s;
             }
             __syncthreads();
+#pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int e = tid + q * NT;
                 Ts[(e >> 5) * 33 + (e & 31)] = z[q];
@@ -880,7 +935,7 @@ int batched_rsvd(BatchedPlan** cache, int device, int sm_count, cudaStream_t str
         cudaEventCreate(&e1);
         float best = 1e30f;
         int best_c = 2;
-        const int cands[3] = {1, 2, 4};
+        const int cands[3] = {2, 3, 4};
         for (int ci = 0; ci < 3; ++ci) {
             pl->ctas_per_sm = cands[ci];
             enqueue(pl, ts, sm_count, pl->infos_dev);  // warm
