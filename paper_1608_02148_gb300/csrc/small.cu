@@ -152,6 +152,186 @@ __global__ void __launch_bounds__(TD * TD)
         }
 }
 
+// ---------------------------------------------------------------------------
+// Blocked form of the same elimination on [G | I], for l <= kCholBlockedMax.
+//
+// Both halves live in shared memory (row-major, stride ld, the whole
+// symmetric G and the whole I half).  For each block of 16 pivot rows
+// k0 .. k0 + 15:
+//   1. one warp factors the 16 x 16 diagonal block D = R_kk^T R_kk of the
+//      current Schur complement in registers (lane c holds column c; the
+//      pivot column is broadcast by shuffles) and forms R_kk^{-T};
+//   2. the block rows are scaled, S_k = R_kk^{-T} [G | I](block rows): their
+//      G half becomes rows k0.. of R, their I half rows k0.. of R^{-T};
+//   3. the rows below are updated with the scaled block rows,
+//      [G | I](r, :) -= sum_m R(k0 + m, r) S_k(m, :),
+//      a rank-16 update (packed FP32x2 FMAs, 4 x 4 outputs per thread).
+// Only the G columns right of the block and the I columns left of its end
+// can be nonzero, so steps 2 and 3 touch exactly those.  A pivot that is not
+// positive and finite restarts the factorization with a larger shift.
+// ---------------------------------------------------------------------------
+constexpr int kCholBlockedMax = 160;
+constexpr int kCholBlockedThreads = 256;
+
+__global__ void __launch_bounds__(kCholBlockedThreads)
+    chol_blocked_kernel(const double* __restrict__ G, int l, int ld, float shift_rel, float* __restrict__ R,
+                        float* __restrict__ T, int* status, int* breakdowns)
+{
+    extern __shared__ __align__(16) float csm[];
+    float* Gs = csm;                  // l x ld
+    float* Is = csm + (size_t)l * ld;  // l x ld
+    __shared__ float Ls[16][17];      // R_kk^{-T} of the current block
+    __shared__ float maxdiag;
+    __shared__ int failed;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int NT = kCholBlockedThreads;
+
+    if (tid < 32) {
+        float md = 0.f;
+        for (int a = tid; a < l; a += 32) md = fmaxf(md, (float)G[a * l + a]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+        if (tid == 0) maxdiag = md;
+    }
+    __syncthreads();
+
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        // shift = shift_rel * max diag on the first attempt; after a breakdown
+        // the shift grows by 100x per retry (shifted CholeskyQR).
+        float shift = shift_rel * maxdiag;
+        if (attempt > 0) shift = fmaxf(shift, maxdiag * 1e-6f * powf(100.f, (float)(attempt - 1)));
+        for (int e = tid; e < l * ld; e += NT) {
+            const int a = e / ld, b = e % ld;
+            float g = 0.f;
+            if (b < l) g = (float)G[min(a, b) * l + max(a, b)] + (a == b ? shift : 0.f);
+            Gs[e] = g;
+            Is[e] = (a == b) ? 1.f : 0.f;
+        }
+        if (tid == 0) failed = 0;
+        __syncthreads();
+
+        for (int k0 = 0; k0 < l; k0 += 16) {
+            const int bk = min(16, l - k0);
+            // 1. diagonal block (identity beyond bk)
+            if (warp == 0) {
+                const int c = lane & 15;
+                float d[16], e[16];
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    d[r] = (r < bk && c < bk) ? Gs[(k0 + r) * ld + k0 + c] : (r == c ? 1.f : 0.f);
+                    e[r] = (r == c) ? 1.f : 0.f;
+                }
+                bool bad = false;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float pv = __shfl_sync(0xffffffffu, d[j], j);
+                    if (!(pv > 0.f) || !isfinite(pv)) bad = true;
+                    const float rinv = rsqrtf(pv);
+                    const float pinv = rinv * rinv;
+#pragma unroll
+                    for (int r = j + 1; r < 16; ++r) {
+                        // D(r, j) from the pivot column's owner
+                        const float f = -__shfl_sync(0xffffffffu, d[r], j) * pinv;
+                        d[r] = fmaf(f, d[j], d[r]);
+                        e[r] = fmaf(f, e[j], e[r]);
+                    }
+                    d[j] *= rinv;
+                    e[j] *= rinv;
+                }
+                if (lane < 16) {
+                    if (c < bk)
+#pragma unroll
+                        for (int r = 0; r < 16; ++r)
+                            if (r < bk) Gs[(k0 + r) * ld + k0 + c] = d[r];
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) Ls[r][c] = e[r];
+                }
+                if (bad && lane == 0) failed = 1;
+            }
+            __syncthreads();
+            if (failed) break;
+            // 2. scale the block rows: columns right of the block (G half) and
+            //    left of its end (I half), one column per thread
+            const int c_end = k0 + bk;
+            const int wG = l - c_end;
+            for (int t = tid; t < wG + c_end; t += NT) {
+                float* X = (t < wG) ? Gs + c_end + t : Is + (t - wG);
+                float x[16];
+#pragma unroll
+                for (int m = 0; m < 16; ++m) x[m] = (m < bk) ? X[(size_t)(k0 + m) * ld] : 0.f;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int m = 0; m <= r; ++m) acc = fmaf(Ls[r][m], x[m], acc);
+                    if (r < bk) X[(size_t)(k0 + r) * ld] = acc;
+                }
+            }
+            __syncthreads();
+            // 3. rank-16 update of the rows below (none after the last block)
+            const int h = l - c_end;
+            if (h > 0) {
+                const int nrt = (h + 3) / 4;
+                const int ntG = (wG + 3) / 4, ntI = c_end / 4;
+                for (int tile = tid; tile < nrt * (ntG + ntI); tile += NT) {
+                    const int rt = tile / (ntG + ntI), ct = tile % (ntG + ntI);
+                    const int r0 = c_end + 4 * rt;
+                    float* X;
+                    int cbase;
+                    if (ct < ntG) {
+                        X = Gs;
+                        cbase = c_end + 4 * ct;
+                    } else {
+                        X = Is;
+                        cbase = 4 * (ct - ntG);
+                    }
+                    float2 acc[4][2];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) {
+                        if (m < bk) {
+                            const float4 rv = *reinterpret_cast<const float4*>(Gs + (size_t)(k0 + m) * ld + r0);
+                            const float4 cv = *reinterpret_cast<const float4*>(X + (size_t)(k0 + m) * ld + cbase);
+                            const float2 c01 = make_float2(cv.x, cv.y), c23 = make_float2(cv.z, cv.w);
+                            const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const float2 r2 = make_float2(rr[i], rr[i]);
+                                acc[i][0] = __ffma2_rn(r2, c01, acc[i][0]);
+                                acc[i][1] = __ffma2_rn(r2, c23, acc[i][1]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = r0 + i;
+                        if (r >= l) continue;
+                        float* row = X + (size_t)r * ld + cbase;
+                        const float a4[4] = {acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) row[q] -= a4[q];
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (!failed) break;
+        if (tid == 0) {
+            if (breakdowns) atomicAdd(breakdowns, 1);
+            if (attempt == 3 && status) *status = RSVDGB_ERR_BREAKDOWN;
+        }
+        __syncthreads();
+    }
+    // R = upper triangle of the G half; T = R^{-1} = (R^{-T})^T from the I half
+    for (int e = tid; e < l * l; e += NT) {
+        const int a = e / l, b = e % l;
+        if (R) R[e] = (b >= a) ? Gs[(size_t)a * ld + b] : 0.f;
+        T[(size_t)b * l + a] = (b <= a) ? Is[(size_t)a * ld + b] : 0.f;
+    }
+}
+
 __global__ void small_matmul_kernel(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C,
                                     int l)
 {
@@ -182,8 +362,11 @@ __global__ void small_transpose_kernel(const float* __restrict__ in, float* __re
 // ---------------------------------------------------------------------------
 // One-sided Jacobi SVD of an l x l matrix, parallel (round-robin) ordering:
 // in each of the L-1 rounds of a sweep the L/2 disjoint column pairs are
-// rotated at once, one warp per pair.  Columns live column-major in Mc and Jc
-// (shared memory when they fit, else the global work buffer).
+// rotated at once, eight lanes per pair.  Columns live column-major with a
+// padded stride Lp = 8 E (zero rows beyond l) in Mc and Jc (shared memory
+// when they fit, else the global work buffer); lane g of a pair holds the E
+// contiguous elements [g E, g E + E) of both columns as float2 pairs, so
+// loads, dot products and updates run on packed FP32x2 instructions.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float warp_sum(float v)
 {
@@ -192,22 +375,22 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-// EPL = ceil(L / 16): column elements per half-warp lane, held in registers
-// while a pair is rotated.
-//
 // The right singular vectors J are needed for kv columns only.  The sweeps
 // first run on M alone (half the shared-memory traffic); when the spectrum
 // allows it, J_c = M^T U_c / sigma_c for the kv leading columns (its error is
 // about u32 sigma_1 / sigma_c, accepted while sigma_kv >= 1e-3 sigma_1).
 // Otherwise the sweeps are repeated from the original M with J accumulated.
-template <int EPL, int NT>
+template <int E, int NT>
 __global__ void __launch_bounds__(NT)
     jacobi_kernel(const float* __restrict__ M, int l, int L, float* __restrict__ sigma, float* __restrict__ Ut,
                   float* __restrict__ Jt, float* __restrict__ gwork, int use_smem, int* sweeps_out, int kv)
 {
-    extern __shared__ float sm[];
+    static_assert(E % 2 == 0, "E float2 pairs");
+    constexpr int Lp = 8 * E;
+    constexpr int E2 = E / 2;
+    extern __shared__ __align__(16) float sm[];
     float* Mc = use_smem ? sm : gwork;
-    float* Jc = use_smem ? sm + (size_t)L * L : gwork + (size_t)L * L;
+    float* Jc = use_smem ? sm + (size_t)L * Lp : gwork + (size_t)L * Lp;
     __shared__ int rotated;
     __shared__ int need_j;
     __shared__ float sv[256];
@@ -218,20 +401,20 @@ __global__ void __launch_bounds__(NT)
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     constexpr int nwarps = NT / 32;
-    const int half = lane >> 4, hl = lane & 15;  // half-warp: one column pair
+    constexpr int ngrp = NT / 8;
+    const int grp = tid >> 3, gl = tid & 7;  // pair group, lane in the group
+    const int P = L / 2;
 
     // rotate a pair only when its cosine exceeds the FP32 noise of the dot
     // products (about sqrt(L) u32); quadratic convergence does the rest.
-    // c = 1 / sqrt(1 + t^2) in IEEE arithmetic keeps c^2 + s^2 - 1 at the
-    // rounding level, so column norms drift only by a random walk of ulps.
     const float tol = 4.f * sqrtf((float)L) * 5.9604645e-8f;
     const int Lm1 = L - 1;
     int sweep = 0;
     for (int pass = 0; pass < 2; ++pass) {
         const bool accj = (pass == 1);
-        // column-major copies, zero padded to L x L
-        for (int e = tid; e < L * L; e += NT) {
-            const int c = e / L, i = e % L;
+        // column-major copies, zero padded to Lp rows
+        for (int e = tid; e < L * Lp; e += NT) {
+            const int c = e / Lp, i = e % Lp;
             Mc[e] = (i < l && c < l) ? M[i * l + c] : 0.f;
             if (accj) Jc[e] = (i == c) ? 1.f : 0.f;
         }
@@ -240,9 +423,9 @@ __global__ void __launch_bounds__(NT)
             if (tid == 0) rotated = 0;
             __syncthreads();
             for (int round = 0; round < Lm1; ++round) {
-                for (int base = 2 * warp; base < L / 2; base += 2 * nwarps) {
-                    const int t = base + half;
-                    const bool valid = t < L / 2;
+                for (int t0 = 0; t0 < P; t0 += ngrp) {
+                    const int t = t0 + grp;
+                    const bool valid = t < P;
                     int a = Lm1, b = round;
                     if (t != 0) {
                         a = round + t;
@@ -250,56 +433,69 @@ __global__ void __launch_bounds__(NT)
                         b = round - t;
                         if (b < 0) b += Lm1;
                     }
-                    float xa[EPL], xb[EPL];
-                    float al = 0.f, be = 0.f, ga = 0.f;
+                    float2 xa[E2], xb[E2];
+                    float2 al2 = make_float2(0.f, 0.f), be2 = al2, ga2 = al2;
                     if (valid) {
-                        const float* ma = Mc + (size_t)a * L;
-                        const float* mb = Mc + (size_t)b * L;
+                        const float2* ma = reinterpret_cast<const float2*>(Mc + (size_t)a * Lp + gl * E);
+                        const float2* mb = reinterpret_cast<const float2*>(Mc + (size_t)b * Lp + gl * E);
 #pragma unroll
-                        for (int e = 0; e < EPL; ++e) {
-                            const int i = hl + 16 * e;
-                            xa[e] = (i < L) ? ma[i] : 0.f;
-                            xb[e] = (i < L) ? mb[i] : 0.f;
-                            al = fmaf(xa[e], xa[e], al);
-                            be = fmaf(xb[e], xb[e], be);
-                            ga = fmaf(xa[e], xb[e], ga);
+                        for (int e = 0; e < E2; ++e) {
+                            xa[e] = ma[e];
+                            xb[e] = mb[e];
+                            al2 = __ffma2_rn(xa[e], xa[e], al2);
+                            be2 = __ffma2_rn(xb[e], xb[e], be2);
+                            ga2 = __ffma2_rn(xa[e], xb[e], ga2);
                         }
                     }
+                    float al = al2.x + al2.y, be = be2.x + be2.y, ga = ga2.x + ga2.y;
 #pragma unroll
-                    for (int o = 8; o > 0; o >>= 1) {
+                    for (int o = 4; o > 0; o >>= 1) {
                         al += __shfl_xor_sync(0xffffffffu, al, o);
                         be += __shfl_xor_sync(0xffffffffu, be, o);
                         ga += __shfl_xor_sync(0xffffffffu, ga, o);
                     }
-                    if (valid && ga != 0.f && fabsf(ga) > tol * sqrtf(al * be)) {
-                        const float zeta = (be - al) / (2.f * ga);
-                        const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-                        const float c = 1.0f / sqrtf(fmaf(tt, tt, 1.f));
+                    // al, be > 0 whenever ga != 0, so the rsqrt factors are finite
+                    if (valid && ga != 0.f && fabsf(ga) * rsqrtf(al) * rsqrtf(be) > tol) {
+                        // Rutishauser's rotation: zeta = cot(2 theta), t = tan(theta)
+                        // = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2).
+                        // The angle may be off by a few ulps (hardware reciprocal
+                        // and rsqrt), which only moves the pair's off-diagonal a
+                        // little; what must hold to rounding level is
+                        // c^2 (1 + t^2) = 1, so c gets one Newton step for
+                        // x^(-1/2) (r <- r + r (1 - x r^2) / 2) after the rsqrt.
+                        const float zeta = __fdividef(be - al, 2.f * ga);
+                        const float az = fabsf(zeta);
+                        float tt;
+                        if (az < 1e18f) {
+                            const float h2 = fmaf(az, az, 1.f);
+                            tt = __fdividef(1.f, az + h2 * rsqrtf(h2));
+                        } else {
+                            tt = __fdividef(0.5f, az);
+                        }
+                        tt = copysignf(tt, zeta);
+                        const float x = fmaf(tt, tt, 1.f);
+                        const float r0 = rsqrtf(x);
+                        const float c = fmaf(0.5f * r0, fmaf(-x * r0, r0, 1.f), r0);
                         const float sn = c * tt;
-                        float* ma = Mc + (size_t)a * L;
-                        float* mb = Mc + (size_t)b * L;
+                        const float2 c2 = make_float2(c, c), s2 = make_float2(sn, sn), ns2 = make_float2(-sn, -sn);
+                        float2* ma = reinterpret_cast<float2*>(Mc + (size_t)a * Lp + gl * E);
+                        float2* mb = reinterpret_cast<float2*>(Mc + (size_t)b * Lp + gl * E);
 #pragma unroll
-                        for (int e = 0; e < EPL; ++e) {
-                            const int i = hl + 16 * e;
-                            if (i < L) {
-                                ma[i] = c * xa[e] - sn * xb[e];
-                                mb[i] = sn * xa[e] + c * xb[e];
-                            }
+                        for (int e = 0; e < E2; ++e) {
+                            ma[e] = __ffma2_rn(ns2, xb[e], __fmul2_rn(c2, xa[e]));
+                            mb[e] = __ffma2_rn(s2, xa[e], __fmul2_rn(c2, xb[e]));
                         }
                         if (accj) {
-                            float* ja = Jc + (size_t)a * L;
-                            float* jb = Jc + (size_t)b * L;
+                            float2* ja = reinterpret_cast<float2*>(Jc + (size_t)a * Lp + gl * E);
+                            float2* jb = reinterpret_cast<float2*>(Jc + (size_t)b * Lp + gl * E);
 #pragma unroll
-                            for (int e = 0; e < EPL; ++e) {
-                                const int i = hl + 16 * e;
-                                if (i < L) {
-                                    const float ya = ja[i], yb = jb[i];
-                                    ja[i] = c * ya - sn * yb;
-                                    jb[i] = sn * ya + c * yb;
-                                }
+                            for (int e = 0; e < E2; ++e) {
+                                const float2 ya = ja[e], yb = jb[e];
+                                ja[e] = __ffma2_rn(ns2, yb, __fmul2_rn(c2, ya));
+                                jb[e] = __ffma2_rn(s2, ya, __fmul2_rn(c2, yb));
                             }
                         }
-                        if (hl == 0) rotated = 1;
+                        if (gl == 0) rotated = 1;
                     }
                 }
                 __syncthreads();
@@ -315,8 +511,8 @@ __global__ void __launch_bounds__(NT)
         for (int c = warp; c < L; c += nwarps) {
             float s2 = 0.f, j2 = 0.f;
             for (int i = lane; i < L; i += 32) {
-                s2 = fmaf(Mc[(size_t)c * L + i], Mc[(size_t)c * L + i], s2);
-                if (accj) j2 = fmaf(Jc[(size_t)c * L + i], Jc[(size_t)c * L + i], j2);
+                s2 = fmaf(Mc[(size_t)c * Lp + i], Mc[(size_t)c * Lp + i], s2);
+                if (accj) j2 = fmaf(Jc[(size_t)c * Lp + i], Jc[(size_t)c * Lp + i], j2);
             }
             s2 = warp_sum(s2);
             j2 = warp_sum(j2);
@@ -328,20 +524,67 @@ __global__ void __launch_bounds__(NT)
         }
         __syncthreads();
         if (!accj) {
-            for (int e = tid; e < L * L; e += NT) {
-                const int c = e / L, i = e % L;
-                float acc = 0.f;
-                if (i < l && c < l && wn[c] > 0.f) {
-                    const float* w = Mc + (size_t)c * L;
-                    for (int t = 0; t < l; ++t) acc = fmaf(M[t * l + i], w[t], acc);
-                    acc /= wn[c];
+            // x_c = M^T u_c for all columns at once, 4 x 4 outputs per thread;
+            // M row-major, staged in shared memory (rows padded to Lq) when
+            // there is room, else read from global memory.
+            const int Lq = (L + 3) & ~3;
+            const float* Ms = M;
+            int ldm = l;
+            if (use_smem == 2) {
+                float* st = sm + 2 * (size_t)L * Lp;
+                for (int e = tid; e < l * Lq; e += NT) {
+                    const int t = e / Lq, i = e % Lq;
+                    st[e] = (i < l) ? M[t * l + i] : 0.f;
                 }
-                Jc[e] = acc;  // x_c = M^T u_c
+                __syncthreads();
+                Ms = st;
+                ldm = Lq;
+            }
+            const int nb = Lq / 4;
+            for (int blk = tid; blk < nb * nb; blk += NT) {
+                const int ib = blk % nb, cb = blk / nb;
+                float acc[4][4] = {};
+                for (int t = 0; t < l; ++t) {
+                    float mv[4], wv[4];
+                    if (use_smem == 2) {
+                        const float4 m4 = *(const float4*)&Ms[(size_t)t * ldm + 4 * ib];
+                        mv[0] = m4.x;
+                        mv[1] = m4.y;
+                        mv[2] = m4.z;
+                        mv[3] = m4.w;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int i = 4 * ib + k;
+                            mv[k] = (i < l) ? Ms[(size_t)t * ldm + i] : 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int c = 4 * cb + k;
+                        wv[k] = (c < L) ? Mc[(size_t)c * Lp + t] : 0.f;
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(mv[a], wv[b], acc[a][b]);
+                }
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int c = 4 * cb + b;
+                    if (c >= L) continue;
+                    const float rw = (c < l && wn[c] > 0.f) ? 1.f / wn[c] : 0.f;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int i = 4 * ib + a;
+                        if (i < L) Jc[(size_t)c * Lp + i] = (i < l) ? acc[a][b] * rw : 0.f;
+                    }
+                }
             }
             __syncthreads();
             for (int c = warp; c < L; c += nwarps) {
                 float x2 = 0.f;
-                for (int i = lane; i < L; i += 32) x2 = fmaf(Jc[(size_t)c * L + i], Jc[(size_t)c * L + i], x2);
+                for (int i = lane; i < L; i += 32) x2 = fmaf(Jc[(size_t)c * Lp + i], Jc[(size_t)c * Lp + i], x2);
                 x2 = warp_sum(x2);
                 if (lane == 0) {
                     sv[c] = sqrtf(x2);
@@ -371,7 +614,7 @@ __global__ void __launch_bounds__(NT)
         const int r = rank[c];
         if (r >= l || i >= l) continue;
         const float w = wn[c];
-        Ut[i * l + r] = (w > 0.f) ? Mc[(size_t)c * L + i] / w : 0.f;
+        Ut[i * l + r] = (w > 0.f) ? Mc[(size_t)c * Lp + i] / w : 0.f;
     }
     for (int c = tid; c < L; c += NT)
         if (rank[c] < l) sigma[rank[c]] = sv[c];
@@ -381,7 +624,7 @@ __global__ void __launch_bounds__(NT)
         const int c = e / L, i = e % L;
         const int r = rank[c];
         if (r >= kv || r >= l || i >= l) continue;
-        Jt[i * l + r] = (jn[c] > 0.f) ? Jc[(size_t)c * L + i] / jn[c] : 0.f;
+        Jt[i * l + r] = (jn[c] > 0.f) ? Jc[(size_t)c * Lp + i] / jn[c] : 0.f;
     }
 }
 
@@ -495,6 +738,14 @@ __global__ void row_to_col_kernel(const float* __restrict__ in, int64_t ldi, int
 void launch_chol_inv(cudaStream_t s, const double* G, int l, float shift_rel, float* R, float* T, int* status,
                      int* breakdowns)
 {
+    if (l <= kCholBlockedMax) {
+        // rows padded to a multiple of 4 (+4 to spread banks) for float4 tiles
+        const int ld = ((l + 3) & ~3) + 4;
+        const size_t bytes = (size_t)2 * l * ld * sizeof(float);
+        chol_blocked_kernel<<<1, kCholBlockedThreads, bytes, s>>>(G, l, ld, shift_rel, R, T, status, breakdowns);
+        count_launches();
+        return;
+    }
     // 16 x 16 threads while the register tile stays small, 32 x 32 beyond
     if (l <= 16)
         chol_inv_kernel<1, 16><<<1, 256, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
@@ -535,17 +786,18 @@ int init_small_kernels()
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return RSVDGB_ERR_CUDA;
     int rc = RSVDGB_OK;
-    rc |= raise_smem_limit(jacobi_kernel<1, 1024>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<2, 1024>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<3, 1024>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<4, 1024>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<5, 1024>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<6, 1024>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<7, 1024>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<8, 1024>, optin);
+    rc |= raise_smem_limit(chol_blocked_kernel, optin);
+    rc |= raise_smem_limit(jacobi_kernel<2, 512>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<4, 512>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<6, 512>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<8, 512>, optin);
     rc |= raise_smem_limit(jacobi_kernel<10, 512>, optin);
     rc |= raise_smem_limit(jacobi_kernel<12, 512>, optin);
     rc |= raise_smem_limit(jacobi_kernel<14, 512>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<16, 512>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<20, 512>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<24, 512>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<28, 512>, optin);
     return rc ? RSVDGB_ERR_CUDA : RSVDGB_OK;
 }
 
@@ -571,32 +823,39 @@ void launch_small_transpose(cudaStream_t s, const float* in, float* out, int l)
     small_transpose_kernel<<<grid, block, 0, s>>>(in, out, l); count_launches();
 }
 
-template <int EPL, int NT>
+template <int E, int NT>
 void launch_jacobi_typed(cudaStream_t s, const float* M, int l, int L, float* sigma, float* Ut, float* Jt,
                          float* work, int* sweeps, int kv)
 {
-    const size_t need = (size_t)2 * L * L * sizeof(float);
-    const int use_smem = need <= (size_t)216 * 1024;
-    jacobi_kernel<EPL, NT><<<1, NT, use_smem ? need : 0, s>>>(M, l, L, sigma, Ut, Jt, work, use_smem, sweeps, kv);
+    // 0: columns in the global work buffer; 1: columns in shared memory;
+    // 2: also a staged copy of M (rows padded to a multiple of 4)
+    const size_t Lp = 8 * E;
+    const size_t need = (size_t)2 * L * Lp * sizeof(float);
+    const size_t staged = need + (size_t)l * ((L + 3) & ~3) * sizeof(float);
+    const size_t cap = (size_t)216 * 1024;
+    const int use_smem = staged <= cap ? 2 : (need <= cap ? 1 : 0);
+    const size_t bytes = use_smem == 2 ? staged : (use_smem == 1 ? need : 0);
+    jacobi_kernel<E, NT><<<1, NT, bytes, s>>>(M, l, L, sigma, Ut, Jt, work, use_smem, sweeps, kv);
 }
 
+// Columns of L = l rounded up to even rows; E elements per lane of the eight
+// lanes of a pair, so the padded column stride 8 E covers L.
 void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, float* Ut, float* Jt, float* work,
                        int* sweeps, int kv)
 {
     const int L = (int)round_up(l, 2);
-    switch ((L + 15) / 16) {
-        case 1: launch_jacobi_typed<1, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
-        case 2: launch_jacobi_typed<2, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
-        case 3: launch_jacobi_typed<3, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
-        case 4: launch_jacobi_typed<4, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
-        case 5: launch_jacobi_typed<5, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
-        case 6: launch_jacobi_typed<6, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
-        case 7: launch_jacobi_typed<7, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
-        case 8: launch_jacobi_typed<8, 1024>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
-        case 9: case 10: launch_jacobi_typed<10, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
-        case 11: case 12: launch_jacobi_typed<12, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
-        default: launch_jacobi_typed<14, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv); break;
-    }
+    const int e = (int)round_up(ceil_div(L, 8), 2);
+    if (e <= 2) launch_jacobi_typed<2, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 4) launch_jacobi_typed<4, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 6) launch_jacobi_typed<6, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 8) launch_jacobi_typed<8, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 10) launch_jacobi_typed<10, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 12) launch_jacobi_typed<12, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 14) launch_jacobi_typed<14, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 16) launch_jacobi_typed<16, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 20) launch_jacobi_typed<20, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 24) launch_jacobi_typed<24, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else launch_jacobi_typed<28, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
     count_launches();
 }
 
