@@ -113,13 +113,14 @@ void launch_split_tf32(cudaStream_t s, const float* in, int64_t ld, int64_t rows
 // ---------------------------------------------------------------------------
 // Small l x l kernels (one CTA)
 // ---------------------------------------------------------------------------
-// Cholesky G + shift*I = R^T R of a symmetric l x l Gram matrix (FP64 input,
-// row-major, ld = l) by Gaussian elimination that also produces R^{-T};
-// writes R (if non-null) and T = R^{-1} as FP32 row-major l x l (upper
-// triangular, zero below).  A non-positive or non-finite pivot sets
-// *status = RSVDGB_ERR_BREAKDOWN and increments *breakdowns; the pivot is then
-// replaced so that the factor stays finite.
-void launch_chol_inv(cudaStream_t s, const double* G, int l, float shift_rel, float* R, float* T, int* status,
+// Cholesky G + shift*I = R^T R of a symmetric l x l Gram matrix (FP32,
+// row-major, ld = l, 16-byte aligned) by Gaussian elimination that also
+// produces R^{-T}; writes R (if non-null) and T = R^{-1} as FP32 row-major
+// l x l (upper triangular, zero below).  A pivot that is not positive and
+// finite restarts the factorization with a larger diagonal shift (three
+// retries, each counted in *breakdowns); if the last attempt fails too,
+// *status = RSVDGB_ERR_BREAKDOWN.
+void launch_chol_inv(cudaStream_t s, const float* G, int l, float shift_rel, float* R, float* T, int* status,
                      int* breakdowns);
 // C = A B for l x l FP32 row-major matrices (used for T1 T2 and R2 R1).
 void launch_small_matmul(cudaStream_t s, const float* A, const float* B, float* C, int l);
@@ -130,7 +131,6 @@ void launch_small_matmul(cudaStream_t s, const float* A, const float* B, float* 
 void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, float* Ut, float* Jt, float* work,
                        int* sweeps, int kv);
 // FP64 -> FP32 copy of an l x l row-major matrix, optionally transposed.
-void launch_small_d2f(cudaStream_t s, const double* in, float* out, int l, bool transpose);
 // Transpose an l x l row-major matrix: out = in^T.
 void launch_small_transpose(cudaStream_t s, const float* in, float* out, int l);
 // d[0..k) = sigma[0..k); info fields from fro2_A and sigma.

@@ -99,7 +99,7 @@ struct Work {
     float *Pth, *Ptl, *Yth, *Ytl;  // TF32 hi/lo parts of the panels (tensor-core engine)
     float *Qth, *Qtl, *Th, *Tl;    // hi/lo of the first CholeskyQR2 basis and of a small factor
     void *Ptb, *Ytb;               // BF16 panels (mixed precision)
-    double* G;
+    float* G;  // l x l Gram (FP64 sums of FP32 partials, stored FP32)
     float *T1, *T2, *T, *R1, *R2, *RB, *M, *sigma, *Ut, *Jt, *jwork;
     int *status, *breakdowns, *sweeps;
     double* fro2;
@@ -161,7 +161,7 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w)
     w.Wt = c.take<float>(L * g.ldn);
     w.Zt = c.take<float>(L * g.ldn);
     w.part = c.take<float>(partial_floats(g, sm_count));
-    w.G = c.take<double>(L * L);
+    w.G = c.take<float>(L * L);
     w.T1 = c.take<float>(L * L);
     w.T2 = c.take<float>(L * L);
     w.T = c.take<float>(L * L);
@@ -309,7 +309,7 @@ void tc_gram(rsvdgb_handle* h, const Geom& g, Work& w, const float* Xt, const fl
     int64_t splits = 0;
     launch_tc_gemm(h->stream, h->sm_count, false, Xt, g.L, rows, ld, Xh, Xl, ld, g.L, nullptr, nullptr, nullptr, g.L,
                    w.part, 0, &splits, w.status, nullptr);
-    launch_reduce_splits(h->stream, w.part, (int)splits, (int64_t)g.L * g.L, g.l, g.l, g.L, nullptr, w.G, g.l);
+    launch_reduce_splits(h->stream, w.part, (int)splits, (int64_t)g.L * g.L, g.l, g.l, g.L, w.G, nullptr, g.l);
 }
 
 // Z = X T (rows x l, column-major, with TF32 hi/lo parts) for a column-major
@@ -356,7 +356,7 @@ void split_panel(cudaStream_t s, const Geom& g, Work& w)
 // G (l x l, FP64) = X^T Z for column-major rows x l matrices X and Z
 // (Z = X gives the Gram matrix).
 void cross_gram(cudaStream_t s, int sm, const float* Xt, const float* Zt, int64_t ld, int64_t rows, int l,
-                float* part, double* G)
+                float* part, float* G)
 {
     GemmArgs a{};
     a.A = Xt;
@@ -373,10 +373,10 @@ void cross_gram(cudaStream_t s, int sm, const float* Xt, const float* Zt, int64_
     a.splits = splits;
     a.split_stride = (int64_t)l * l;
     launch_simt_gemm(s, false, true, false, a);
-    launch_reduce_splits(s, part, splits, (int64_t)l * l, l, l, l, nullptr, G, l);
+    launch_reduce_splits(s, part, splits, (int64_t)l * l, l, l, l, G, nullptr, l);
 }
 
-void gram(cudaStream_t s, int sm, const float* Xt, int64_t ld, int64_t rows, int l, float* part, double* G)
+void gram(cudaStream_t s, int sm, const float* Xt, int64_t ld, int64_t rows, int l, float* part, float* G)
 {
     cross_gram(s, sm, Xt, Xt, ld, rows, l, part, G);
 }
@@ -486,7 +486,7 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
         // factors (R2 R1 would carry the inverse's error l u kappa).
         cholqr2(s, sm, w, w.Wt, g.ldn, g.n, l, w.Zt, w.Pt);
         cross_gram(s, sm, w.Pt, w.Wt, g.ldn, g.n, l, w.part, w.G);
-        launch_small_d2f(s, w.G, w.M, l, true);
+        launch_small_transpose(s, w.G, w.M, l);
         launch_jacobi_svd(s, w.M, l, w.sigma, w.Ut, w.Jt, w.jwork, w.sweeps, o.nV);
         // U = Q Ut (Eq. UQU) and V = Q_B J, truncated
         if (o.nU > 0) {

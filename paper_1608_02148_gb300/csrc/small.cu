@@ -39,7 +39,7 @@ constexpr int kSmallThreads = 1024;
 // ---------------------------------------------------------------------------
 template <int NB, int TD>  // TD x TD threads, NB x NB elements each (TD * NB >= l)
 __global__ void __launch_bounds__(TD * TD)
-    chol_inv_kernel(const double* __restrict__ G, int l, float shift_rel, float* __restrict__ R,
+    chol_inv_kernel(const float* __restrict__ G, int l, float shift_rel, float* __restrict__ R,
                     float* __restrict__ T, int* status, int* breakdowns)
 {
     constexpr int kCholThreads = TD * TD;
@@ -159,22 +159,95 @@ __global__ void __launch_bounds__(TD * TD)
 // symmetric G and the whole I half).  For each block of 16 pivot rows
 // k0 .. k0 + 15:
 //   1. one warp factors the 16 x 16 diagonal block D = R_kk^T R_kk of the
-//      current Schur complement in registers (lane c holds column c; the
-//      pivot column is broadcast by shuffles) and forms R_kk^{-T};
+//      current Schur complement in registers and forms R_kk^{-T};
 //   2. the block rows are scaled, S_k = R_kk^{-T} [G | I](block rows): their
 //      G half becomes rows k0.. of R, their I half rows k0.. of R^{-T};
 //   3. the rows below are updated with the scaled block rows,
 //      [G | I](r, :) -= sum_m R(k0 + m, r) S_k(m, :),
 //      a rank-16 update (packed FP32x2 FMAs, 4 x 4 outputs per thread).
 // Only the G columns right of the block and the I columns left of its end
-// can be nonzero, so steps 2 and 3 touch exactly those.  A pivot that is not
-// positive and finite restarts the factorization with a larger shift.
+// can be nonzero, so steps 2 and 3 touch exactly those.  Step 1 of the next
+// block runs during step 3: warp 0 first updates the next diagonal block
+// (16 tiles) and factors it while the other warps update everything else.
+// A pivot that is not positive and finite restarts the factorization with a
+// larger shift.
 // ---------------------------------------------------------------------------
 constexpr int kCholBlockedMax = 160;
-constexpr int kCholBlockedThreads = 256;
+constexpr int kCholBlockedThreads = 512;
 
-__global__ void __launch_bounds__(kCholBlockedThreads)
-    chol_blocked_kernel(const double* __restrict__ G, int l, int ld, float shift_rel, float* __restrict__ R,
+// Step 1 for the block at (k0, k0): lanes 0..15 hold columns of the G half,
+// lanes 16..31 the same columns of the I half (identity beyond bk).  The
+// pivot column D(:, j) is broadcast from lane j.  Writes R_kk into Gs and
+// R_kk^{-T} into Ls; returns true (on every lane) after a bad pivot.
+__device__ __noinline__ bool chol_diag_block(float* Gs, int ld, int k0, int bk, float (*Ls)[17], int lane)
+{
+    const int c = lane & 15;
+    const bool gpart = lane < 16;
+    float v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+        v[r] = (gpart && r < bk && c < bk) ? Gs[(size_t)(k0 + r) * ld + k0 + c] : (r == c ? 1.f : 0.f);
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const float pv = __shfl_sync(0xffffffffu, v[j], j);
+        if (!(pv > 0.f) || !isfinite(pv)) bad = true;
+        const float rinv = rsqrtf(pv);
+        const float npinv = -rinv * rinv;
+#pragma unroll
+        for (int r = j + 1; r < 16; ++r) v[r] = fmaf(__shfl_sync(0xffffffffu, v[r], j) * npinv, v[j], v[r]);
+        v[j] *= rinv;
+    }
+    if (gpart) {
+        if (c < bk)
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                if (r < bk) Gs[(size_t)(k0 + r) * ld + k0 + c] = v[r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) Ls[r][c] = v[r];
+    }
+    return bad;
+}
+
+// Step 3 for one 4 x 4 tile: rows r0..r0+3 (>= the block's end) of X (Gs or
+// Is), columns cbase..cbase+3, minus sum_m R(k0 + m, r) X(k0 + m, c).
+__device__ __forceinline__ void chol_update_tile(const float* Gs, float* X, int ld, int k0, int bk, int r0,
+                                                 int cbase, int l)
+{
+    float2 acc[4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        if (m < bk) {
+            const float4 rv = *reinterpret_cast<const float4*>(Gs + (size_t)(k0 + m) * ld + r0);
+            const float4 cv = *reinterpret_cast<const float4*>(X + (size_t)(k0 + m) * ld + cbase);
+            const float2 c01 = make_float2(cv.x, cv.y), c23 = make_float2(cv.z, cv.w);
+            const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 r2 = make_float2(rr[i], rr[i]);
+                acc[i][0] = __ffma2_rn(r2, c01, acc[i][0]);
+                acc[i][1] = __ffma2_rn(r2, c23, acc[i][1]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (r0 + i >= l) continue;
+        float4* row = reinterpret_cast<float4*>(X + (size_t)(r0 + i) * ld + cbase);
+        float4 x = *row;
+        x.x -= acc[i][0].x;
+        x.y -= acc[i][0].y;
+        x.z -= acc[i][1].x;
+        x.w -= acc[i][1].y;
+        *row = x;
+    }
+}
+
+__global__ void __launch_bounds__(kCholBlockedThreads, 1)
+    chol_blocked_kernel(const float* __restrict__ G, int l, int ld, float shift_rel, float* __restrict__ R,
                         float* __restrict__ T, int* status, int* breakdowns)
 {
     extern __shared__ __align__(16) float csm[];
@@ -186,86 +259,90 @@ __global__ void __launch_bounds__(kCholBlockedThreads)
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     constexpr int NT = kCholBlockedThreads;
+    constexpr int NW = NT / 32;
 
-    if (tid < 32) {
-        float md = 0.f;
-        for (int a = tid; a < l; a += 32) md = fmaxf(md, (float)G[a * l + a]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
-        if (tid == 0) maxdiag = md;
-    }
-    __syncthreads();
+    // zero padding of the G rows (shared memory only)
+    for (int a = warp; a < l; a += NW)
+        for (int b = l + lane; b < ld; b += 32) Gs[(size_t)a * ld + b] = 0.f;
 
     for (int attempt = 0; attempt < 4; ++attempt) {
-        // shift = shift_rel * max diag on the first attempt; after a breakdown
-        // the shift grows by 100x per retry (shifted CholeskyQR).
-        float shift = shift_rel * maxdiag;
-        if (attempt > 0) shift = fmaxf(shift, maxdiag * 1e-6f * powf(100.f, (float)(attempt - 1)));
-        for (int e = tid; e < l * ld; e += NT) {
-            const int a = e / ld, b = e % ld;
-            float g = 0.f;
-            if (b < l) g = (float)G[min(a, b) * l + max(a, b)] + (a == b ? shift : 0.f);
-            Gs[e] = g;
-            Is[e] = (a == b) ? 1.f : 0.f;
+        // G (l x l, contiguous) lands in the I half by 16-byte asynchronous
+        // copies, all in flight at once; the upper triangle (+ shift) goes to
+        // the G half, the lower triangle is mirrored from it (an exactly
+        // symmetric matrix), then the I half is reset to the identity
+        {
+            const int chunks = (l * l + 3) / 4;
+            for (int q = tid; q < chunks; q += NT)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                                 (uint32_t)__cvta_generic_to_shared(Is + 4 * q)),
+                             "l"(G + 4 * q)
+                             : "memory");
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncthreads();
+            // shift = shift_rel * max diag on the first attempt; after a
+            // breakdown the shift grows by 100x per retry (shifted CholeskyQR)
+            float shift = 0.f;
+            if (shift_rel > 0.f || attempt > 0) {
+                if (warp == 0) {
+                    float md = 0.f;
+                    for (int a = lane; a < l; a += 32) md = fmaxf(md, Is[a * l + a]);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+                    if (lane == 0) maxdiag = md;
+                }
+                __syncthreads();
+                shift = shift_rel * maxdiag;
+                if (attempt > 0) shift = fmaxf(shift, maxdiag * 1e-6f * powf(100.f, (float)(attempt - 1)));
+            }
+            for (int a = warp; a < l; a += NW)
+                for (int b = a + lane; b < l; b += 32)
+                    Gs[(size_t)a * ld + b] = Is[a * l + b] + (a == b ? shift : 0.f);
+            __syncthreads();
+            for (int a = warp; a < l; a += NW)
+                for (int b = lane; b < ld; b += 32) Is[(size_t)a * ld + b] = (a == b) ? 1.f : 0.f;
         }
         if (tid == 0) failed = 0;
         __syncthreads();
+        for (int a = warp; a < l; a += NW)
+            for (int b = lane; b < a; b += 32) Gs[(size_t)a * ld + b] = Gs[(size_t)b * ld + a];
+        __syncthreads();
+        if (warp == 0 && chol_diag_block(Gs, ld, 0, min(16, l), Ls, lane) && lane == 0) failed = 1;
+        __syncthreads();
 
         for (int k0 = 0; k0 < l; k0 += 16) {
-            const int bk = min(16, l - k0);
-            // 1. diagonal block (identity beyond bk)
-            if (warp == 0) {
-                const int c = lane & 15;
-                float d[16], e[16];
-#pragma unroll
-                for (int r = 0; r < 16; ++r) {
-                    d[r] = (r < bk && c < bk) ? Gs[(k0 + r) * ld + k0 + c] : (r == c ? 1.f : 0.f);
-                    e[r] = (r == c) ? 1.f : 0.f;
-                }
-                bool bad = false;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float pv = __shfl_sync(0xffffffffu, d[j], j);
-                    if (!(pv > 0.f) || !isfinite(pv)) bad = true;
-                    const float rinv = rsqrtf(pv);
-                    const float pinv = rinv * rinv;
-#pragma unroll
-                    for (int r = j + 1; r < 16; ++r) {
-                        // D(r, j) from the pivot column's owner
-                        const float f = -__shfl_sync(0xffffffffu, d[r], j) * pinv;
-                        d[r] = fmaf(f, d[j], d[r]);
-                        e[r] = fmaf(f, e[j], e[r]);
-                    }
-                    d[j] *= rinv;
-                    e[j] *= rinv;
-                }
-                if (lane < 16) {
-                    if (c < bk)
-#pragma unroll
-                        for (int r = 0; r < 16; ++r)
-                            if (r < bk) Gs[(k0 + r) * ld + k0 + c] = d[r];
-#pragma unroll
-                    for (int r = 0; r < 16; ++r) Ls[r][c] = e[r];
-                }
-                if (bad && lane == 0) failed = 1;
-            }
-            __syncthreads();
             if (failed) break;
-            // 2. scale the block rows: columns right of the block (G half) and
-            //    left of its end (I half), one column per thread
+            const int bk = min(16, l - k0);
             const int c_end = k0 + bk;
             const int wG = l - c_end;
-            for (int t = tid; t < wG + c_end; t += NT) {
+            // 2. scale the block rows: columns right of the block (G half) and
+            //    left of its end (I half); thread = (column, half of the rows)
+            {
+                const int task = tid;
+                const bool active = task < 2 * l;
+                const int half = task / l, t = task - half * l;
                 float* X = (t < wG) ? Gs + c_end + t : Is + (t - wG);
                 float x[16];
 #pragma unroll
-                for (int m = 0; m < 16; ++m) x[m] = (m < bk) ? X[(size_t)(k0 + m) * ld] : 0.f;
+                for (int m = 0; m < 16; ++m) x[m] = (active && m < bk) ? X[(size_t)(k0 + m) * ld] : 0.f;
+                __syncthreads();
+                if (active) {
+                    if (half == 0) {
 #pragma unroll
-                for (int r = 0; r < 16; ++r) {
-                    float acc = 0.f;
+                        for (int r = 0; r < 8; ++r) {
+                            float acc = 0.f;
 #pragma unroll
-                    for (int m = 0; m <= r; ++m) acc = fmaf(Ls[r][m], x[m], acc);
-                    if (r < bk) X[(size_t)(k0 + r) * ld] = acc;
+                            for (int m = 0; m <= r; ++m) acc = fmaf(Ls[r][m], x[m], acc);
+                            if (r < bk) X[(size_t)(k0 + r) * ld] = acc;
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 8; r < 16; ++r) {
+                            float acc = 0.f;
+#pragma unroll
+                            for (int m = 0; m <= r; ++m) acc = fmaf(Ls[r][m], x[m], acc);
+                            if (r < bk) X[(size_t)(k0 + r) * ld] = acc;
+                        }
+                    }
                 }
             }
             __syncthreads();
@@ -274,44 +351,22 @@ __global__ void __launch_bounds__(kCholBlockedThreads)
             if (h > 0) {
                 const int nrt = (h + 3) / 4;
                 const int ntG = (wG + 3) / 4, ntI = c_end / 4;
-                for (int tile = tid; tile < nrt * (ntG + ntI); tile += NT) {
-                    const int rt = tile / (ntG + ntI), ct = tile % (ntG + ntI);
-                    const int r0 = c_end + 4 * rt;
-                    float* X;
-                    int cbase;
-                    if (ct < ntG) {
-                        X = Gs;
-                        cbase = c_end + 4 * ct;
-                    } else {
-                        X = Is;
-                        cbase = 4 * (ct - ntG);
+                const int nd = min(4, ntG);  // tiles of the next diagonal block per row
+                if (warp == 0) {
+                    if (lane < 16) {
+                        const int rt = lane >> 2, ct = lane & 3;
+                        if (rt < nrt && ct < nd) chol_update_tile(Gs, Gs, ld, k0, bk, c_end + 4 * rt, c_end + 4 * ct, l);
                     }
-                    float2 acc[4][2];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int m = 0; m < 16; ++m) {
-                        if (m < bk) {
-                            const float4 rv = *reinterpret_cast<const float4*>(Gs + (size_t)(k0 + m) * ld + r0);
-                            const float4 cv = *reinterpret_cast<const float4*>(X + (size_t)(k0 + m) * ld + cbase);
-                            const float2 c01 = make_float2(cv.x, cv.y), c23 = make_float2(cv.z, cv.w);
-                            const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                const float2 r2 = make_float2(rr[i], rr[i]);
-                                acc[i][0] = __ffma2_rn(r2, c01, acc[i][0]);
-                                acc[i][1] = __ffma2_rn(r2, c23, acc[i][1]);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int r = r0 + i;
-                        if (r >= l) continue;
-                        float* row = X + (size_t)r * ld + cbase;
-                        const float a4[4] = {acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y};
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) row[q] -= a4[q];
+                    __syncwarp();
+                    if (chol_diag_block(Gs, ld, c_end, min(16, h), Ls, lane) && lane == 0) failed = 1;
+                } else {
+                    for (int tile = tid - 32; tile < nrt * (ntG + ntI); tile += NT - 32) {
+                        const int rt = tile / (ntG + ntI), ct = tile - rt * (ntG + ntI);
+                        if (rt < 4 && ct < nd) continue;  // warp 0's
+                        if (ct < ntG)
+                            chol_update_tile(Gs, Gs, ld, k0, bk, c_end + 4 * rt, c_end + 4 * ct, l);
+                        else
+                            chol_update_tile(Gs, Is, ld, k0, bk, c_end + 4 * rt, 4 * (ct - ntG), l);
                     }
                 }
                 __syncthreads();
@@ -325,11 +380,11 @@ __global__ void __launch_bounds__(kCholBlockedThreads)
         __syncthreads();
     }
     // R = upper triangle of the G half; T = R^{-1} = (R^{-T})^T from the I half
-    for (int e = tid; e < l * l; e += NT) {
-        const int a = e / l, b = e % l;
-        if (R) R[e] = (b >= a) ? Gs[(size_t)a * ld + b] : 0.f;
-        T[(size_t)b * l + a] = (b <= a) ? Is[(size_t)a * ld + b] : 0.f;
-    }
+    for (int a = warp; a < l; a += NW)
+        for (int b = lane; b < l; b += 32) {
+            if (R) R[(size_t)a * l + b] = (b >= a) ? Gs[(size_t)a * ld + b] : 0.f;
+            T[(size_t)a * l + b] = (a <= b) ? Is[(size_t)b * ld + a] : 0.f;  // T(a, b) = R^{-T}(b, a)
+        }
 }
 
 __global__ void small_matmul_kernel(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C,
@@ -341,14 +396,6 @@ __global__ void small_matmul_kernel(const float* __restrict__ A, const float* __
     float acc = 0.f;
     for (int t = 0; t < l; ++t) acc = fmaf(A[i * l + t], B[t * l + j], acc);
     C[i * l + j] = acc;
-}
-
-__global__ void small_d2f_kernel(const double* __restrict__ in, float* __restrict__ out, int l, int transpose)
-{
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= l || j >= l) return;
-    out[transpose ? j * l + i : i * l + j] = (float)in[i * l + j];
 }
 
 __global__ void small_transpose_kernel(const float* __restrict__ in, float* __restrict__ out, int l)
@@ -380,17 +427,22 @@ __device__ __forceinline__ float warp_sum(float v)
 // allows it, J_c = M^T U_c / sigma_c for the kv leading columns (its error is
 // about u32 sigma_1 / sigma_c, accepted while sigma_kv >= 1e-3 sigma_1).
 // Otherwise the sweeps are repeated from the original M with J accumulated.
-template <int E, int NT>
-__global__ void __launch_bounds__(NT)
+//
+// MODE 0: columns in the global work buffer; 1: columns in shared memory;
+// 2: also a staged copy of M (rows padded to a multiple of 4).  MODE is a
+// template parameter so that shared-memory columns get shared-memory loads.
+template <int E, int NT, int MODE>
+__global__ void __launch_bounds__(NT, 1)
     jacobi_kernel(const float* __restrict__ M, int l, int L, float* __restrict__ sigma, float* __restrict__ Ut,
-                  float* __restrict__ Jt, float* __restrict__ gwork, int use_smem, int* sweeps_out, int kv)
+                  float* __restrict__ Jt, float* __restrict__ gwork, int* sweeps_out, int kv)
 {
     static_assert(E % 2 == 0, "E float2 pairs");
     constexpr int Lp = 8 * E;
     constexpr int E2 = E / 2;
+    constexpr int use_smem = MODE;
     extern __shared__ __align__(16) float sm[];
-    float* Mc = use_smem ? sm : gwork;
-    float* Jc = use_smem ? sm + (size_t)L * Lp : gwork + (size_t)L * Lp;
+    float* Mc = MODE ? sm : gwork;
+    float* Jc = MODE ? sm + (size_t)L * Lp : gwork + (size_t)L * Lp;
     __shared__ int rotated;
     __shared__ int need_j;
     __shared__ float sv[256];
@@ -412,12 +464,13 @@ __global__ void __launch_bounds__(NT)
     int sweep = 0;
     for (int pass = 0; pass < 2; ++pass) {
         const bool accj = (pass == 1);
-        // column-major copies, zero padded to Lp rows
-        for (int e = tid; e < L * Lp; e += NT) {
-            const int c = e / Lp, i = e % Lp;
-            Mc[e] = (i < l && c < l) ? M[i * l + c] : 0.f;
-            if (accj) Jc[e] = (i == c) ? 1.f : 0.f;
-        }
+        // column-major copies, zero padded to Lp rows (rows of M read
+        // contiguously, one warp per row)
+        for (int i = warp; i < Lp; i += nwarps)
+            for (int c = lane; c < L; c += 32) {
+                Mc[(size_t)c * Lp + i] = (i < l && c < l) ? M[i * l + c] : 0.f;
+                if (accj) Jc[(size_t)c * Lp + i] = (i == c) ? 1.f : 0.f;
+            }
         __syncthreads();
         for (sweep = 0; sweep < 30; ++sweep) {
             if (tid == 0) rotated = 0;
@@ -609,23 +662,23 @@ __global__ void __launch_bounds__(NT)
         if (!need_j || accj) break;
     }
     if (tid == 0 && sweeps_out) *sweeps_out = sweep + 1;
-    for (int e = tid; e < L * L; e += NT) {
-        const int c = e / L, i = e % L;
-        const int r = rank[c];
-        if (r >= l || i >= l) continue;
-        const float w = wn[c];
-        Ut[i * l + r] = (w > 0.f) ? Mc[(size_t)c * Lp + i] / w : 0.f;
-    }
+    // outputs row by row (contiguous stores): Ut(i, r) = u_c(i), c of rank r
+    for (int i = warp; i < l; i += nwarps)
+        for (int r = lane; r < l; r += 32) {
+            const int c = col_of_rank[r];
+            const float w = wn[c];
+            Ut[i * l + r] = (w > 0.f) ? Mc[(size_t)c * Lp + i] / w : 0.f;
+        }
     for (int c = tid; c < L; c += NT)
         if (rank[c] < l) sigma[rank[c]] = sv[c];
     if (kv <= 0) return;
     // right vectors for the kv leading ranks: accumulated J, or M^T u_c normalised
-    for (int e = tid; e < L * L; e += NT) {
-        const int c = e / L, i = e % L;
-        const int r = rank[c];
-        if (r >= kv || r >= l || i >= l) continue;
-        Jt[i * l + r] = (jn[c] > 0.f) ? Jc[(size_t)c * Lp + i] / jn[c] : 0.f;
-    }
+    const int kr = min(kv, l);
+    for (int i = warp; i < l; i += nwarps)
+        for (int r = lane; r < kr; r += 32) {
+            const int c = col_of_rank[r];
+            Jt[i * l + r] = (jn[c] > 0.f) ? Jc[(size_t)c * Lp + i] / jn[c] : 0.f;
+        }
 }
 
 __global__ void finalize_info_kernel(const float* __restrict__ sigma, int l, int k, float* __restrict__ d,
@@ -735,7 +788,7 @@ __global__ void row_to_col_kernel(const float* __restrict__ in, int64_t ldi, int
 
 }  // namespace
 
-void launch_chol_inv(cudaStream_t s, const double* G, int l, float shift_rel, float* R, float* T, int* status,
+void launch_chol_inv(cudaStream_t s, const float* G, int l, float shift_rel, float* R, float* T, int* status,
                      int* breakdowns)
 {
     if (l <= kCholBlockedMax) {
@@ -746,20 +799,8 @@ void launch_chol_inv(cudaStream_t s, const double* G, int l, float shift_rel, fl
         count_launches();
         return;
     }
-    // 16 x 16 threads while the register tile stays small, 32 x 32 beyond
-    if (l <= 16)
-        chol_inv_kernel<1, 16><<<1, 256, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
-    else if (l <= 32)
-        chol_inv_kernel<2, 16><<<1, 256, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
-    else if (l <= 64)
-        chol_inv_kernel<4, 16><<<1, 256, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
-    else if (l <= 96)
-        chol_inv_kernel<6, 16><<<1, 256, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
-    else if (l <= 128)
-        chol_inv_kernel<8, 16><<<1, 256, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
-    else if (l <= 160)
-        chol_inv_kernel<5, 32><<<1, 1024, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
-    else if (l <= 192)
+    // wider sketches: the register-tile elimination on 32 x 32 threads
+    if (l <= 192)
         chol_inv_kernel<6, 32><<<1, 1024, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
     else
         chol_inv_kernel<7, 32><<<1, 1024, 0, s>>>(G, l, shift_rel, R, T, status, breakdowns);
@@ -787,17 +828,15 @@ int init_small_kernels()
         return RSVDGB_ERR_CUDA;
     int rc = RSVDGB_OK;
     rc |= raise_smem_limit(chol_blocked_kernel, optin);
-    rc |= raise_smem_limit(jacobi_kernel<2, 512>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<4, 512>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<6, 512>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<8, 512>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<10, 512>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<12, 512>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<14, 512>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<16, 512>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<20, 512>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<24, 512>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<28, 512>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<2, 512, 2>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<4, 512, 2>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<6, 512, 2>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<8, 512, 2>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<10, 512, 2>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<12, 512, 2>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<14, 512, 2>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<16, 512, 2>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<20, 512, 1>, optin);
     return rc ? RSVDGB_ERR_CUDA : RSVDGB_OK;
 }
 
@@ -808,14 +847,6 @@ void launch_small_matmul(cudaStream_t s, const float* A, const float* B, float* 
     small_matmul_kernel<<<grid, block, 0, s>>>(A, B, C, l); count_launches();
 }
 
-void launch_small_d2f(cudaStream_t s, const double* in, float* out, int l, bool transpose)
-{
-    dim3 block(16, 16);
-    dim3 grid((unsigned)ceil_div(l, 16), (unsigned)ceil_div(l, 16));
-    small_d2f_kernel<<<grid, block, 0, s>>>(in, out, l, transpose ? 1 : 0);
-    count_launches();
-}
-
 void launch_small_transpose(cudaStream_t s, const float* in, float* out, int l)
 {
     dim3 block(16, 16);
@@ -823,39 +854,36 @@ void launch_small_transpose(cudaStream_t s, const float* in, float* out, int l)
     small_transpose_kernel<<<grid, block, 0, s>>>(in, out, l); count_launches();
 }
 
-template <int E, int NT>
+template <int E, int NT, int MODE>
 void launch_jacobi_typed(cudaStream_t s, const float* M, int l, int L, float* sigma, float* Ut, float* Jt,
                          float* work, int* sweeps, int kv)
 {
-    // 0: columns in the global work buffer; 1: columns in shared memory;
-    // 2: also a staged copy of M (rows padded to a multiple of 4)
     const size_t Lp = 8 * E;
-    const size_t need = (size_t)2 * L * Lp * sizeof(float);
-    const size_t staged = need + (size_t)l * ((L + 3) & ~3) * sizeof(float);
-    const size_t cap = (size_t)216 * 1024;
-    const int use_smem = staged <= cap ? 2 : (need <= cap ? 1 : 0);
-    const size_t bytes = use_smem == 2 ? staged : (use_smem == 1 ? need : 0);
-    jacobi_kernel<E, NT><<<1, NT, bytes, s>>>(M, l, L, sigma, Ut, Jt, work, use_smem, sweeps, kv);
+    const size_t cols = (size_t)2 * L * Lp * sizeof(float);
+    const size_t bytes = MODE == 2 ? cols + (size_t)l * ((L + 3) & ~3) * sizeof(float) : (MODE == 1 ? cols : 0);
+    jacobi_kernel<E, NT, MODE><<<1, NT, bytes, s>>>(M, l, L, sigma, Ut, Jt, work, sweeps, kv);
 }
 
 // Columns of L = l rounded up to even rows; E elements per lane of the eight
-// lanes of a pair, so the padded column stride 8 E covers L.
+// lanes of a pair, so the padded column stride 8 E covers L.  Up to L = 128
+// the columns and a staged M fit in shared memory (MODE 2), up to 160 the
+// columns alone (MODE 1); wider sketches keep the columns in global memory.
 void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, float* Ut, float* Jt, float* work,
                        int* sweeps, int kv)
 {
     const int L = (int)round_up(l, 2);
     const int e = (int)round_up(ceil_div(L, 8), 2);
-    if (e <= 2) launch_jacobi_typed<2, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
-    else if (e <= 4) launch_jacobi_typed<4, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
-    else if (e <= 6) launch_jacobi_typed<6, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
-    else if (e <= 8) launch_jacobi_typed<8, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
-    else if (e <= 10) launch_jacobi_typed<10, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
-    else if (e <= 12) launch_jacobi_typed<12, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
-    else if (e <= 14) launch_jacobi_typed<14, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
-    else if (e <= 16) launch_jacobi_typed<16, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
-    else if (e <= 20) launch_jacobi_typed<20, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
-    else if (e <= 24) launch_jacobi_typed<24, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
-    else launch_jacobi_typed<28, 512>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    if (e <= 2) launch_jacobi_typed<2, 512, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 4) launch_jacobi_typed<4, 512, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 6) launch_jacobi_typed<6, 512, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 8) launch_jacobi_typed<8, 512, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 10) launch_jacobi_typed<10, 512, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 12) launch_jacobi_typed<12, 512, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 14) launch_jacobi_typed<14, 512, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 16) launch_jacobi_typed<16, 512, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 20) launch_jacobi_typed<20, 512, 1>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 24) launch_jacobi_typed<24, 512, 0>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else launch_jacobi_typed<28, 512, 0>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
     count_launches();
 }
 
