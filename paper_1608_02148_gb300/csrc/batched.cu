@@ -572,10 +572,13 @@ __global__ void jacobi_kernel(const MatDev* __restrict__ D, int B, const float* 
     wn = sqrtf(wn);
     jn = sqrtf(jn);
     const float sv = (jn > 0.f) ? wn / jn : 0.f;
+    // ranks by descending sigma, ties by column; NaN ranks as -1 so the ranks
+    // form a permutation
+    const float key = (sv == sv) ? sv : -1.f;
     int rank = 0;
     for (int o = 0; o < LB; ++o) {
-        const float so = __shfl_sync(0xffffffffu, sv, o);
-        rank += (so > sv) || (so == sv && o < lane);
+        const float so = __shfl_sync(0xffffffffu, key, o);
+        rank += (so > key) || (so == key && o < lane);
     }
     float* sg = sigma + (int64_t)b * LB;
     float* ut = Ut + (int64_t)b * LB * LB;

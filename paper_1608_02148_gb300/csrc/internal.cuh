@@ -64,10 +64,20 @@ struct GemmArgs {
 void launch_simt_gemm(cudaStream_t s, bool AT, bool BT, bool CT, const GemmArgs& g);
 
 // Sum `splits` partial matrices (each rows x cols with leading dimension ld,
-// consecutive partials split_stride apart) in FP64 and write FP32 (out32) or
-// FP64 (out64) with leading dimension ld_out.
+// consecutive partials split_stride apart) in FP32, in a fixed order, and
+// Tensor-core Gram G = X^T X (Z == nullptr or Z == X) or cross product
+// G = X^T Z (l x l, row-major, ld l) of column-major rows x l matrices with
+// leading dimension ld (columns l..l_pad-1 zero), FP32-accurate (3xTF32).
+// part receives up to tc_gram_max_ctas(sm_count) partials of l_pad x l_pad.
+// Returns RSVDGB_ERR_UNSUPPORTED when tc_gram_supported() is false.
+bool tc_gram_supported(const float* X, const float* Z, int64_t ld, int l_pad);
+int64_t tc_gram_max_ctas(int sm_count);
+int launch_tc_gram(cudaStream_t s, int sm_count, const float* X, const float* Z, int64_t rows, int64_t ld, int l,
+                   int l_pad, float* part, float* G, int* status);
+
+// write out with leading dimension ld_out.
 void launch_reduce_splits(cudaStream_t s, const float* part, int splits, int64_t split_stride, int64_t rows,
-                          int64_t cols, int64_t ld, float* out32, double* out64, int64_t ld_out);
+                          int64_t cols, int64_t ld, float* out, int64_t ld_out);
 
 // ---------------------------------------------------------------------------
 // Tensor-core passes over A (tcgen05 + TMA, 3xTF32, FP32 A only)
@@ -130,7 +140,6 @@ void launch_small_matmul(cudaStream_t s, const float* A, const float* B, float* 
 //   Jt (l x l row-major, right vectors; only the first kv columns written).
 void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, float* Ut, float* Jt, float* work,
                        int* sweeps, int kv);
-// FP64 -> FP32 copy of an l x l row-major matrix, optionally transposed.
 // Transpose an l x l row-major matrix: out = in^T.
 void launch_small_transpose(cudaStream_t s, const float* in, float* out, int l);
 // d[0..k) = sigma[0..k); info fields from fro2_A and sigma.

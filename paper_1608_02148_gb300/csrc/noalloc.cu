@@ -92,7 +92,7 @@ extern "C" int rsvdgb_pass_atx_noalloc(void* cuda_stream, const void* A, int64_t
     a.splits = (int)splits;
     a.split_stride = per_split;
     launch_simt_gemm(s, true, false, false, a);
-    launch_reduce_splits(s, scratch, (int)splits, per_split, n, l, ldz, Z, nullptr, ldz);
+    launch_reduce_splits(s, scratch, (int)splits, per_split, n, l, ldz, Z, ldz);
     if (cudaGetLastError() != cudaSuccess) return RSVDGB_ERR_CUDA;
     return RSVDGB_OK;
 }

@@ -99,7 +99,7 @@ struct Work {
     float *Pth, *Ptl, *Yth, *Ytl;  // TF32 hi/lo parts of the panels (tensor-core engine)
     float *Qth, *Qtl, *Th, *Tl;    // hi/lo of the first CholeskyQR2 basis and of a small factor
     void *Ptb, *Ytb;               // BF16 panels (mixed precision)
-    float* G;  // l x l Gram (FP64 sums of FP32 partials, stored FP32)
+    float* G;  // l x l Gram (sum of per-CTA FP32 partials)
     float *T1, *T2, *T, *R1, *R2, *RB, *M, *sigma, *Ut, *Jt, *jwork;
     int *status, *breakdowns, *sweeps;
     double* fro2;
@@ -258,7 +258,7 @@ void tall_gemm(cudaStream_t s, int sm, bool AT, bool BT, bool CT, const void* A,
     prof_mark(prof, true, 0);
     launch_simt_gemm(s, AT, BT, CT, a);
     prof_mark(prof, false, pass_bytes);
-    launch_reduce_splits(s, part, splits, rows * ldc, rows, cols, ldc, C, nullptr, ldc);
+    launch_reduce_splits(s, part, splits, rows * ldc, rows, cols, ldc, C, ldc);
 }
 
 double a_bytes(const Geom& g) { return (double)g.m * (double)g.n * (g.a_bf16 ? 2.0 : 4.0); }
@@ -296,20 +296,28 @@ void pass_over_A(rsvdgb_handle* h, const Geom& g, Work& w, bool A_side, const fl
                        out_h, out_l, ldO, w.part, stored_atx ? 0 : 1, &splits, w.status, fro2);
     prof_mark(h, false, a_bytes(g));
     if (splits > 0) {
-        launch_reduce_splits(s, w.part, (int)splits, (int64_t)g.L * ldO, g.l, rows, ldO, out, nullptr, ldO);
+        launch_reduce_splits(s, w.part, (int)splits, (int64_t)g.L * ldO, g.l, rows, ldO, out, ldO);
         if (out_h) launch_split_tf32(s, out, ldO, rows, g.l, g.L, out_h, out_l);
     }
 }
 
-// G (l x l, FP64) = X^T X for a column-major rows x l matrix given as X and its
-// TF32 hi/lo parts, on the tensor cores (3xTF32, K split over the rows).
+// G (l x l) = X^T X for a column-major rows x l matrix X (leading dimension
+// ld) on the tensor cores (3xTF32).  Up to l_pad = 128 the Gram kernel reads
+// X once; wider sketches use the pass kernel on X^T with the TF32 hi/lo
+// parts of X (Xh, Xl) as its panel.
+bool tc_gram_direct(const Geom& g, const float* Xt, int64_t ld) { return tc_gram_supported(Xt, nullptr, ld, g.L); }
+
 void tc_gram(rsvdgb_handle* h, const Geom& g, Work& w, const float* Xt, const float* Xh, const float* Xl, int64_t ld,
              int64_t rows)
 {
+    if (tc_gram_direct(g, Xt, ld)) {
+        launch_tc_gram(h->stream, h->sm_count, Xt, nullptr, rows, ld, g.l, g.L, w.part, w.G, w.status);
+        return;
+    }
     int64_t splits = 0;
     launch_tc_gemm(h->stream, h->sm_count, false, Xt, g.L, rows, ld, Xh, Xl, ld, g.L, nullptr, nullptr, nullptr, g.L,
                    w.part, 0, &splits, w.status, nullptr);
-    launch_reduce_splits(h->stream, w.part, (int)splits, (int64_t)g.L * g.L, g.l, g.l, g.L, w.G, nullptr, g.l);
+    launch_reduce_splits(h->stream, w.part, (int)splits, (int64_t)g.L * g.L, g.l, g.l, g.L, w.G, g.l);
 }
 
 // Z = X T (rows x l, column-major, with TF32 hi/lo parts) for a column-major
@@ -353,11 +361,15 @@ void split_panel(cudaStream_t s, const Geom& g, Work& w)
         launch_split_tf32(s, w.Pt, g.ldn, g.n, g.l, g.L, w.Pth, w.Ptl);
 }
 
-// G (l x l, FP64) = X^T Z for column-major rows x l matrices X and Z
+// G (l x l) = X^T Z for column-major rows x l matrices X and Z
 // (Z = X gives the Gram matrix).
 void cross_gram(cudaStream_t s, int sm, const float* Xt, const float* Zt, int64_t ld, int64_t rows, int l,
-                float* part, float* G)
+                float* part, float* G, int l_pad = 0, int* status = nullptr)
 {
+    if (l_pad > 0 && tc_gram_supported(Xt, Zt, ld, l_pad)) {
+        launch_tc_gram(s, sm, Xt, Zt, rows, ld, l, l_pad, part, G, status);
+        return;
+    }
     GemmArgs a{};
     a.A = Xt;
     a.lda = ld;
@@ -373,12 +385,13 @@ void cross_gram(cudaStream_t s, int sm, const float* Xt, const float* Zt, int64_
     a.splits = splits;
     a.split_stride = (int64_t)l * l;
     launch_simt_gemm(s, false, true, false, a);
-    launch_reduce_splits(s, part, splits, (int64_t)l * l, l, l, l, G, nullptr, l);
+    launch_reduce_splits(s, part, splits, (int64_t)l * l, l, l, l, G, l);
 }
 
-void gram(cudaStream_t s, int sm, const float* Xt, int64_t ld, int64_t rows, int l, float* part, float* G)
+void gram(cudaStream_t s, int sm, const float* Xt, int64_t ld, int64_t rows, int l, float* part, float* G,
+          int l_pad = 0, int* status = nullptr)
 {
-    cross_gram(s, sm, Xt, Xt, ld, rows, l, part, G);
+    cross_gram(s, sm, Xt, Xt, ld, rows, l, part, G, l_pad, status);
 }
 
 // Zt (rows x l, column-major) = X T with X column-major (rows x l) and T an
@@ -391,13 +404,15 @@ void times_small(cudaStream_t s, int sm, const float* Xt, int64_t ld, int64_t ro
 
 // CholeskyQR2 of a column-major rows x l matrix X (in Xt): Q1 = X R1^{-1},
 // Q = Q1 R2^{-1}, the orthonormal basis written to Qt (tmp holds Q1; Xt, tmp
-// and Qt are distinct).
-void cholqr2(cudaStream_t s, int sm, Work& w, const float* Xt, int64_t ld, int64_t rows, int l, float* tmp, float* Qt)
+// and Qt are distinct).  l_pad > 0 puts the Grams on the tensor cores where
+// the shape allows it.
+void cholqr2(cudaStream_t s, int sm, Work& w, const float* Xt, int64_t ld, int64_t rows, int l, float* tmp, float* Qt,
+             int l_pad)
 {
-    gram(s, sm, Xt, ld, rows, l, w.part, w.G);
+    gram(s, sm, Xt, ld, rows, l, w.part, w.G, l_pad, w.status);
     launch_chol_inv(s, w.G, l, 0.f, w.R1, w.T1, w.status, w.breakdowns);
     times_small(s, sm, Xt, ld, rows, l, w.T1, tmp, w.part);
-    gram(s, sm, tmp, ld, rows, l, w.part, w.G);
+    gram(s, sm, tmp, ld, rows, l, w.part, w.G, l_pad, w.status);
     launch_chol_inv(s, w.G, l, 0.f, w.R2, w.T2, w.status, w.breakdowns);
     times_small(s, sm, tmp, ld, rows, l, w.T2, Qt, w.part);
 }
@@ -449,7 +464,7 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
         apply_At(h, g, w, false);
         times_small(s, sm, w.Wt, g.ldn, g.n, l, w.T, w.Zt, w.part);
         // Q = qr(A^T Q): CholeskyQR2 on the n side, result in the panel
-        cholqr2(s, sm, w, w.Zt, g.ldn, g.n, l, w.Wt, w.Pt);
+        cholqr2(s, sm, w, w.Zt, g.ldn, g.n, l, w.Wt, w.Pt, g.use_tc ? (int)g.L : 0);
         split_panel(s, g, w);
         // Y = A Q
         apply_A(h, g, w, nullptr);
@@ -462,7 +477,9 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
     // Y1 = Y T1, G = Y1^T Y1, Q = Y1 T2.  Q ends up in Yt.
     launch_chol_inv(s, w.G, l, 0.f, w.R1, w.T1, w.status, w.breakdowns);
     if (g.use_tc) {
-        tc_times_small(h, g, w, w.Yt, g.ldm, g.m, w.T1, w.Qt, w.Qth, w.Qtl);
+        // the TF32 split of Q1 is needed only when the Gram runs on the pass kernel
+        const bool direct = tc_gram_direct(g, w.Qt, g.ldm);
+        tc_times_small(h, g, w, w.Yt, g.ldm, g.m, w.T1, w.Qt, direct ? nullptr : w.Qth, direct ? nullptr : w.Qtl);
         tc_gram(h, g, w, w.Qt, w.Qth, w.Qtl, g.ldm, g.m);
     } else {
         times_small(s, sm, w.Yt, g.ldm, g.m, l, w.T1, w.Qt, w.part);
@@ -484,8 +501,8 @@ int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t 
         // formed as Q_B^T B^T from the computed Q_B, so that B^T = Q_B R_B
         // holds to FP32 rounding whatever the error of the triangular
         // factors (R2 R1 would carry the inverse's error l u kappa).
-        cholqr2(s, sm, w, w.Wt, g.ldn, g.n, l, w.Zt, w.Pt);
-        cross_gram(s, sm, w.Pt, w.Wt, g.ldn, g.n, l, w.part, w.G);
+        cholqr2(s, sm, w, w.Wt, g.ldn, g.n, l, w.Zt, w.Pt, g.use_tc ? (int)g.L : 0);
+        cross_gram(s, sm, w.Pt, w.Wt, g.ldn, g.n, l, w.part, w.G, g.use_tc ? (int)g.L : 0, w.status);
         launch_small_transpose(s, w.G, w.M, l);
         launch_jacobi_svd(s, w.M, l, w.sigma, w.Ut, w.Jt, w.jwork, w.sweeps, o.nV);
         // U = Q Ut (Eq. UQU) and V = Q_B J, truncated
@@ -837,7 +854,7 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
                             nullptr, ldM, part, transpose ? 0 : 1, &used, status, nullptr);
     }
     if (rc) return rc;
-    if (used > 0) launch_reduce_splits(s, part, (int)used, (int64_t)L * ldM, l, M, ldM, Yc, nullptr, ldM);
+    if (used > 0) launch_reduce_splits(s, part, (int)used, (int64_t)L * ldM, l, M, ldM, Yc, ldM);
     launch_colmajor_to_rowmajor(s, Yc, ldM, M, l, Y, ldy);
     RSVDGB_CUDA_TRY(cudaGetLastError());
     return RSVDGB_OK;

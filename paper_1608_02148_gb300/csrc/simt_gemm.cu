@@ -142,26 +142,39 @@ void launch_typed(cudaStream_t s, const GemmArgs& g)
     count_launches();
 }
 
-__global__ void reduce_splits_kernel(const float* __restrict__ part, int splits, int64_t split_stride, int64_t rows,
-                                     int64_t cols, int64_t ld, float* __restrict__ out32, double* __restrict__ out64,
-                                     int64_t ld_out)
+// out = sum over the splits of part (rows x cols, leading dimension ld, split
+// s at part + s * split_stride).  A CTA takes one row and 32 consecutive
+// columns; warp w sums splits w, w + 8, ... with four independent
+// accumulators (all loads of a lane in flight together), then the eight warp
+// sums are added in a fixed order, so the result does not depend on timing.
+__global__ void __launch_bounds__(256) reduce_splits_kernel(const float* __restrict__ part, int splits,
+                                                            int64_t split_stride, int64_t rows, int64_t cols,
+                                                            int64_t ld, float* __restrict__ out, int64_t ld_out)
 {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= rows * cols) return;
-    const int64_t r = e / cols, c = e % cols;
-    const float* src = part + r * ld + c;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int sidx = 0;
-    for (; sidx + 3 < splits; sidx += 4) {
-        a0 += (double)src[(sidx + 0) * split_stride];
-        a1 += (double)src[(sidx + 1) * split_stride];
-        a2 += (double)src[(sidx + 2) * split_stride];
-        a3 += (double)src[(sidx + 3) * split_stride];
+    __shared__ float red[8][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t ncb = (cols + 31) / 32;
+    const int64_t r = blockIdx.x / ncb;
+    const int64_t c = (blockIdx.x % ncb) * 32 + lane;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    if (c < cols) {
+        const float* src = part + r * ld + c;
+        int s = warp;
+        for (; s + 24 < splits; s += 32) {
+            a0 += src[(int64_t)s * split_stride];
+            a1 += src[(int64_t)(s + 8) * split_stride];
+            a2 += src[(int64_t)(s + 16) * split_stride];
+            a3 += src[(int64_t)(s + 24) * split_stride];
+        }
+        for (; s < splits; s += 8) a0 += src[(int64_t)s * split_stride];
     }
-    for (; sidx < splits; ++sidx) a0 += (double)src[sidx * split_stride];
-    const double acc = (a0 + a1) + (a2 + a3);
-    if (out32) out32[r * ld_out + c] = (float)acc;
-    if (out64) out64[r * ld_out + c] = acc;
+    red[warp][lane] = (a0 + a1) + (a2 + a3);
+    __syncthreads();
+    if (warp == 0 && c < cols) {
+        const float t = ((red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane])) +
+                        ((red[4][lane] + red[5][lane]) + (red[6][lane] + red[7][lane]));
+        out[r * ld_out + c] = t;
+    }
 }
 
 }  // namespace
@@ -182,12 +195,12 @@ void launch_simt_gemm(cudaStream_t s, bool AT, bool BT, bool CT, const GemmArgs&
 }
 
 void launch_reduce_splits(cudaStream_t s, const float* part, int splits, int64_t split_stride, int64_t rows,
-                          int64_t cols, int64_t ld, float* out32, double* out64, int64_t ld_out)
+                          int64_t cols, int64_t ld, float* out, int64_t ld_out)
 {
-    const int64_t total = rows * cols;
-    if (total == 0) return;
-    reduce_splits_kernel<<<(unsigned)ceil_div(total, 64), 64, 0, s>>>(part, splits, split_stride, rows, cols, ld,
-                                                                          out32, out64, ld_out); count_launches();
+    if (rows * cols == 0) return;
+    const int64_t blocks = rows * ((cols + 31) / 32);
+    reduce_splits_kernel<<<(unsigned)blocks, 256, 0, s>>>(part, splits, split_stride, rows, cols, ld, out, ld_out);
+    count_launches();
 }
 
 }  // namespace rsvdgb

@@ -8,10 +8,11 @@
 //  * small helpers -- l x l products, transposes, layout changes, the
 //                     finishing kernel that writes d and rsvdgb_info.
 //
-// Precision: these kernels compute in FP32 with FP64 Gram inputs.  GB300's
+// Precision: these kernels compute in FP32 on FP32 Gram inputs.  GB300's
 // FP64 pipe is far slower than its FP32 pipe, and the Gram matrices they
-// factor carry FP32-level error already, so FP64 here would not change the
-// result beyond that error; CholeskyQR2 recovers orthogonality to FP32 level.
+// factor carry FP32-level error already (FP32 accumulation over the rows),
+// so FP64 here would not change the result beyond that error; CholeskyQR2
+// recovers orthogonality to FP32 level.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -646,9 +647,15 @@ __global__ void __launch_bounds__(NT, 1)
             }
             __syncthreads();
         }
+        // ranks by descending sigma, ties by column; a NaN sigma (non-finite
+        // input) ranks as -1, so the ranks always form a permutation
         for (int c = tid; c < L; c += NT) {
+            const float kc = (sv[c] == sv[c]) ? sv[c] : -1.f;
             int r = 0;
-            for (int o = 0; o < L; ++o) r += (sv[o] > sv[c]) || (sv[o] == sv[c] && o < c);
+            for (int o = 0; o < L; ++o) {
+                const float ko = (sv[o] == sv[o]) ? sv[o] : -1.f;
+                r += (ko > kc) || (ko == kc && o < c);
+            }
             rank[c] = r;
             col_of_rank[r] = c;
         }
