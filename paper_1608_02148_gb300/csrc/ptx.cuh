@@ -60,6 +60,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     return true;
 }
 
+// Warp-wide form: lane 0 alone polls (31 lanes spinning on shared memory
+// would crowd out the warps doing work), then every lane takes the completed
+// phase once itself, which gives each the barrier's acquire ordering.  The
+// phase cannot advance again before this warp acts on it, so that check
+// succeeds at once; it is bounded all the same.  Same result on all lanes.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status)
+{
+    const int lane = threadIdx.x & 31;
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait(bar, parity, abort_flag, status) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok && lane != 0)
+        for (int i = 0; i < (1 << 20) && !mbar_test(bar, parity); ++i) {
+        }
+    return ok != 0;
+}
+
 __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int c0, int c1)
 {
     asm volatile(

@@ -159,15 +159,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int64_t c = 0; c < nk; ++c) {
             const int s = (int)(c % S);
             const uint32_t ph = (uint32_t)((c / S) & 1);
-            if (!(ok = mbar_wait(&full_bar[s], ph, &abort_flag, p.status))) break;
+            if (!(ok = mbar_wait_warp(&full_bar[s], ph, &abort_flag, p.status))) break;
             if (t < l_pad) {
 #pragma unroll
                 for (int mtx = 0; mtx < (CROSS ? 2 : 1); ++mtx) {
-                    // row t: 8 chunks of 16 bytes; the split keeps the layout
+                    // row t: 8 chunks of 16 bytes; the split keeps the layout.
+                    // Chunk j is visited as j ^ (t & 7) so that the 32 rows of a
+                    // warp spread over all banks (rows are 128 bytes apart).
                     float4* hi = (float4*)(smem + (size_t)s * kStage + mtx * 2 * kTile + t * 128);
                     float4* lo = (float4*)((uint8_t*)hi + kTile);
 #pragma unroll
-                    for (int ch = 0; ch < 8; ++ch) {
+                    for (int j = 0; j < 8; ++j) {
+                        const int ch = j ^ (t & 7);
                         const float4 v = hi[ch];
                         float4 h, r;
                         h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int r = q * 32 + lane;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         float* out = p.part + (int64_t)blockIdx.x * l_pad * l_pad;
-        if (ok && (ok = mbar_wait(&acc_bar, 0, &abort_flag, p.status))) {
+        if (ok && (ok = mbar_wait_warp(&acc_bar, 0, &abort_flag, p.status))) {
             tmem_fence_after();
             for (int j0 = 0; j0 < l_pad; j0 += 16) {
                 uint32_t v[16];

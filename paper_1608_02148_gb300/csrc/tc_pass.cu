@@ -278,8 +278,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t ph = (uint32_t)((it / SA) & 1);
                 const int ts = (int)(it % kTmemStages);
                 const uint32_t tph = (uint32_t)((it / kTmemStages) & 1);
-                if (!(ok = mbar_wait(&afull_bar[s], ph, &abort_flag, p.status))) break;
-                if (!(ok = mbar_wait(&tfree_bar[ts], tph ^ 1, &abort_flag, p.status))) break;
+                if (!(ok = mbar_wait_warp(&afull_bar[s], ph, &abort_flag, p.status))) break;
+                if (!(ok = mbar_wait_warp(&tfree_bar[ts], tph ^ 1, &abort_flag, p.status))) break;
                 tmem_fence_after();
                 const uint8_t* st = a_ring + (size_t)s * a_stage_bytes;
                 uint32_t hi[G][kBK / 2], lo[G][kBK / 2];
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!ok) break;
             // ---- epilogue of this tile set: 16-column chunks alternate between the two warps of a quarter
-            if (!(ok = mbar_wait(&accf_bar, (uint32_t)set & 1, &abort_flag, p.status))) break;
+            if (!(ok = mbar_wait_warp(&accf_bar, (uint32_t)set & 1, &abort_flag, p.status))) break;
             tmem_fence_after();
             for (int g = 0; g < gv; ++g) {
                 const int64_t idx = (t0 + g) * kTileRows + r;  // row (AX) or column (AtX) of A
