@@ -36,9 +36,18 @@ METRIC = "rank-k rSVD wall time and % HBM roofline, mixed/learned-q vs FP32 at e
 WORKLOADS = {
     "spiked200k": dict(desc="rsvd 200000x2000 fp32, sigma_i=1/i + N(0,1e-3^2) noise, k=100 p=10 q=2",
                        m=200000, n=2000, k=100, p=10, q=2, noise=1e-3),
+    "spiked50k": dict(desc="rsvd 50000x2000 fp32, sigma_i=1/i + N(0,1e-3^2) noise, k=100 p=10 q=2 (profiling size)",
+                      m=50000, n=2000, k=100, p=10, q=2, noise=1e-3),
     "planted2k": dict(desc="rsvd 2000x1000 fp32, sigma_i=exp(-i/20), k=20 p=10 q=2",
                       m=2000, n=1000, k=20, p=10, q=2, noise=0.0),
 }
+
+# DRAM bytes (read + write) per byte of A of the FP32 tensor-core pass kernel,
+# from one ncu capture on the 50000 x 2000 workload (profiles/tc_kernels_spiked50k.md):
+# A-side pass 410.2 + 49.0 MB, A^T-side pass 445.2 + 3.1 MB per 400 MB of A.  The
+# traffic scales with the rows processed, so the full-size launch carries the
+# same ratio.  Set to None when the pass kernel changes.
+TC_PASS_TRAFFIC_PER_A_BYTE = ((410.2 + 49.0) + (445.2 + 3.1)) / (2 * 400.0)
 
 # FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 SIMT_FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -333,8 +342,13 @@ def main():
                     "hbm_view": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm, "frac": achieved_gbs / hbm,
                                  "peak_source": peak_kind}}
     else:
+        traffic = None
+        if TC_PASS_TRAFFIC_PER_A_BYTE is not None and args.prec == "fp32":
+            traffic = TC_PASS_TRAFFIC_PER_A_BYTE * a_bytes
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved_gbs / hbm, "traffic": None, "peak_source": peak_kind,
+                    "frac": achieved_gbs / hbm, "traffic": traffic, "peak_source": peak_kind,
+                    "traffic_source": "ncu dram bytes on the 50000x2000 workload, scaled by rows"
+                    if traffic is not None else None,
                     "kernel": "tc_pass_kernel (pass over A, tcgen05 3xTF32)",
                     "tensor_view": {"achieved_tflops_algorithmic": achieved_tflops,
                                     "tf32_flops_issued_per_algorithmic": 3.0 * (((l + 15) // 16) * 16) / l}}

@@ -71,13 +71,16 @@ def small_planted(seed: int = 0x160802148 + 1000) -> np.ndarray:
 
 def _orthonormal_torch(G):
     """Orthonormalise the columns of a tall torch matrix with device matmuls
-    and a host (numpy, float64) factorisation of the small Gram matrix, twice.
+    (FP64 Gram) and a host (numpy, float64) factorisation of the small Gram
+    matrix, twice.
     Only library products are used; torch's device linear-algebra module is
     not needed."""
     import torch
 
     for _ in range(2):
-        gram = (G.T @ G).double().cpu().numpy()
+        Gd = G.double()
+        gram = (Gd.T @ Gd).cpu().numpy()  # FP64 Gram: a square Gaussian has kappa ~ n
+        del Gd
         R = np.linalg.cholesky(gram).T
         Rinv = np.linalg.inv(R)
         G = G @ torch.as_tensor(Rinv, dtype=G.dtype, device=G.device)
