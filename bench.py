@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=40000, help="row sample for the oracle baseline")
     ap.add_argument("--batched", type=int, default=4096, help="matrices in the batched workload (0 = skip)")
+    ap.add_argument("--controller-eval", type=int, default=16,
+                    help="held-out 20000x5000 matrices for the learned-(q, p) evaluation (0 = skip)")
     return ap.parse_args()
 
 
@@ -380,6 +382,47 @@ def main():
     except Exception as exc:  # a variant the build does not serve
         variants = {other: {"unavailable": str(exc)}}
 
+    # ---------------- learned (q, p) on the same A: the packaged controller ----------------
+    ctl_path = os.path.join(ROOT, "paper_1608_02148_gb300", "controller_default.bin")
+    if os.path.exists(ctl_path):
+        try:
+            rs.rsvdgb_controller_load(h, ctl_path)
+            o3 = rs.make_opts(p=wl["p"], q=wl["q"], seed=rank, prec=args.prec, engine=args.engine,
+                              q_mode="learned")
+            for _ in range(2):
+                rs.rsvdgb_rsvd(h, A, k, opts=o3, out=bufs, sync_info=False)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            nv = max(3, args.steps // 2)
+            for _ in range(nv):
+                rs.rsvdgb_rsvd(h, A, k, opts=o3, out=bufs, sync_info=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            info3 = rs._info_from(bufs[3])
+            err_main = float(np.sqrt(max(info.err2_k, 0.0)))
+            err3 = float(np.sqrt(max(info3.err2_k, 0.0)))
+            variants["learned_" + args.prec] = {
+                "ms": e0.elapsed_time(e1) / nv, "err_k_fro": err3, "q_used": info3.q_used,
+                "p_used": info3.p_used, "passes_over_A": 2 * info3.q_used + 2,
+                "err_ratio_vs_" + args.prec: err3 / err_main if err_main > 0 else None}
+        except Exception as exc:
+            variants["learned_" + args.prec] = {"unavailable": str(exc)}
+
+    # ---------------- learned (q, p) against fixed p = 10, q = 2 on held-out planted matrices ----------------
+    controller = None
+    if args.controller_eval > 0 and rank == 0 and os.path.exists(ctl_path):
+        try:
+            from paper_1608_02148_gb300 import controller_train as ct
+            rs.rsvdgb_controller_load(h, ctl_path)
+            t0 = time.perf_counter()
+            controller = ct.evaluate(h, args.controller_eval, seed=0x160802148 + 5000 + 7777)
+            controller["target"] = "||A - U S V^T||_F <= 1.05 x optimum + 1e-4 ||A||_F"
+            controller["seconds"] = time.perf_counter() - t0
+        except Exception as exc:
+            controller = {"unavailable": str(exc)}
+
     # ---------------- batched workload: 4096 ragged matrices, one graph launch ----------------
     batched = None
     if args.batched > 0 and rank == 0:
@@ -432,6 +475,7 @@ def main():
                 "pass_kernels": {"launches": pass_n, "avg_ms": pass_avg_ms, "share_of_step":
                                  pass_ms / max(elapsed, 1e-9) if world == 1 else None},
                 "variants": variants,
+                "controller": controller,
                 "batched": batched,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                 "info": info.as_dict()}

@@ -70,6 +70,15 @@ enum { RSVDGB_ROW_MAJOR = 0, RSVDGB_COL_MAJOR = 1 };
  * where they apply; SIMT forces the FP32 FMA kernels. */
 enum { RSVDGB_ENGINE_AUTO = 0, RSVDGB_ENGINE_SIMT = 1, RSVDGB_ENGINE_TC = 2 };
 
+/* How q and p are chosen.  FIXED: opts.q and opts.p.  LEARNED: the handle's
+ * controller (rsvdgb_controller_load / rsvdgb_controller_set) predicts them
+ * from the first sketch, which is taken with the widest oversampling p_max
+ * (Omega is nested in l, so its first k + p columns are the sketch for the
+ * chosen p); with no controller loaded the call falls back to FIXED.  The
+ * learned mode synchronises the handle's stream once, after the first pass,
+ * to read the decision. */
+enum { RSVDGB_Q_FIXED = 0, RSVDGB_Q_LEARNED = 1 };
+
 typedef struct rsvdgb_opts {
     int32_t p;       /* oversampling, l = k + p (Sec. 2.2.1); default 10         */
     int32_t q;       /* subspace iterations (Sec. 2.2.2); default 2              */
@@ -78,7 +87,11 @@ typedef struct rsvdgb_opts {
     uint64_t seed;   /* Philox key of Omega; default 0                           */
     int32_t layout;  /* RSVDGB_ROW_MAJOR / COL_MAJOR; default ROW_MAJOR          */
     int32_t engine;  /* RSVDGB_ENGINE_*; default AUTO                             */
-    int32_t reserved[6];
+    int32_t q_mode;  /* RSVDGB_Q_FIXED / RSVDGB_Q_LEARNED; default FIXED          */
+    int32_t p_max;   /* learned mode: largest oversampling (>= 2); default 24     */
+    int32_t q_max;   /* learned mode: largest q; default 6                        */
+    int32_t reserved[3]; /* zero; reserved[0] = 1 runs rsvdgb_rsvd_batched
+                            eagerly instead of replaying its CUDA graph       */
 } rsvdgb_opts;
 
 /* Diagnostics written by the device at the end of a call (device memory). */
@@ -246,6 +259,69 @@ int rsvdgb_pass_atx(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64
  */
 int rsvdgb_pass_atx_noalloc(void* cuda_stream, const void* A, int64_t m, int64_t n, int64_t lda, int dtype,
                             const float* X, int64_t ldx, int l, float* Z, int64_t ldz);
+
+/* ------------------------------------------------------------------------
+ * Learned (q, p) controller.  The paper leaves q and p to the user
+ * (Sec. 3.4 recommends p = 10, q = 1 or 2, more iterations for slowly
+ * decaying spectra; no counterpart exists for choosing them per matrix).
+ * A small MLP (16 -> 64 -> 64 -> 2, ReLU, FP32) maps 16 statistics of the
+ * first sketch (the diagonal of the CholeskyQR factor R of Y = A Omega
+ * relative to R_11 at indices around k -- R_jj^2 estimates the rank-(j-1)
+ * range-finder error -- the sketch energy against ||A||_F^2, shape) to
+ * (q, log2 p).
+ * Parameters: RSVDGB_MLP_PARAMS floats, laid out as mu[16], sd[16] (input
+ * standardisation), W1[64][16], b1[64], W2[64][64], b2[64], W3[2][64], b3[2].
+ * File format (little-endian): 8 bytes "RSVDMLP1", int32 RSVDGB_MLP_PARAMS,
+ * then the parameters as float32.
+ * ---------------------------------------------------------------------- */
+#define RSVDGB_MLP_PARAMS 5410
+#define RSVDGB_MLP_FEATURES 16
+
+typedef struct rsvdgb_train_opts {
+    int32_t epochs;  /* passes over the data set; default 300                  */
+    int32_t batch;   /* minibatch size; default 256                            */
+    float lr;        /* Adam step size; default 2e-3                           */
+    float tau;       /* pinball-loss quantile in (0, 1); default 0.99          */
+    uint64_t seed;   /* initialisation and shuffling; default 0                */
+    int32_t reserved[4];
+} rsvdgb_train_opts;
+
+/* Defaults of rsvdgb_train_opts. */
+void rsvdgb_default_train_opts(rsvdgb_train_opts* o);
+
+/* Load a parameter file (format above) into the handle; the learned mode of
+ * rsvdgb_rsvd then uses it.  RSVDGB_ERR_INVALID_ARG for a missing or
+ * malformed file.  Synchronises the handle's stream. */
+int rsvdgb_controller_load(rsvdgb_handle* h, const char* path);
+
+/* Same from host memory (RSVDGB_MLP_PARAMS floats). */
+int rsvdgb_controller_set(rsvdgb_handle* h, const float* params_host);
+
+/* Train on a data set file and write the parameter file.  The data set is
+ * 8 bytes "RSVDDS01", int32 n, int32 RSVDGB_MLP_FEATURES, then n x 16 float32
+ * features (as rsvdgb_controller_features writes them) and n x 2 float32
+ * targets (q, log2 p).  Training runs on the handle's GPU (minibatch pinball
+ * loss, hand-written forward/backward kernels, Adam); the trained parameters
+ * are also loaded into the handle.  final_loss (host, may be NULL) receives
+ * the mean loss over the data set.  Synchronises. */
+int rsvdgb_controller_train(rsvdgb_handle* h, const char* dataset_path, const rsvdgb_train_opts* opts,
+                            const char* out_path, float* final_loss);
+
+/* The 16 controller features of A (device output feats[16]): pass 1 with the
+ * sketch width k + opts->p_max (clamped to min(m, n)), the CholeskyQR factor
+ * of the sketch and ||A||_F^2, as the learned mode computes them.  Arguments
+ * as rsvdgb_rsvd; asynchronous. */
+int rsvdgb_controller_features(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k,
+                               const rsvdgb_opts* opts, float* feats);
+
+/* Network evaluation and gradient on device arrays (P: RSVDGB_MLP_PARAMS
+ * floats; X: n x 16; Y: n x 2; out: n x 2).  rsvdgb_mlp_grad writes the
+ * gradient of the mean pinball loss (quantile tau) with respect to the
+ * trainable parameters (RSVDGB_MLP_PARAMS - 32 floats, W1 first) and the mean
+ * loss (device float).  Asynchronous. */
+int rsvdgb_mlp_forward(rsvdgb_handle* h, const float* P, const float* X, int n, float* out);
+int rsvdgb_mlp_grad(rsvdgb_handle* h, const float* P, const float* X, const float* Y, int n, float tau, float* grad,
+                    float* loss);
 
 /*
  * Instrumentation (not part of the paper's method).

@@ -12,6 +12,7 @@ passages each function follows.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from pathlib import Path
@@ -78,6 +79,12 @@ def _load():
     lib.oracle_num_threads.argtypes = []
     lib.oracle_num_threads.restype = I
     lib.oracle_set_num_threads.argtypes = [I]
+    lib.oracle_mlp_params.argtypes = []
+    lib.oracle_mlp_params.restype = I
+    lib.oracle_mlp_forward.argtypes = [P, P, I64, P]
+    lib.oracle_mlp_forward.restype = None
+    lib.oracle_mlp_loss_grad.argtypes = [P, P, P, I64, ctypes.c_double, P]
+    lib.oracle_mlp_loss_grad.restype = ctypes.c_double
     lib.oracle_set_num_threads.restype = None
     _lib = lib
     return lib
@@ -237,3 +244,68 @@ def canonical_signs(U: np.ndarray, V: np.ndarray):
             U[:, c] = -U[:, c]
             V[:, c] = -V[:, c]
     return U, V
+
+
+# ---------------------------------------------------------------- controller network (FP64)
+def mlp_params() -> int:
+    return _load().oracle_mlp_params()
+
+
+def mlp_forward(P, X):
+    """Network outputs (n x 2) for float64 parameters P and inputs X (n x 16)."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    out = np.zeros((X.shape[0], 2))
+    _load().oracle_mlp_forward(_ptr(P), _ptr(X), X.shape[0], _ptr(out))
+    return out
+
+
+def mlp_loss_grad(P, X, Y, tau=0.9, with_grad=True):
+    """Mean pinball loss and its gradient w.r.t. the trainable parameters."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    g = np.zeros(mlp_params() - 32) if with_grad else None
+    loss = _load().oracle_mlp_loss_grad(_ptr(P), _ptr(X), _ptr(Y), X.shape[0], float(tau),
+                                       _ptr(g) if with_grad else None)
+    return loss, g
+
+
+def controller_features(A: np.ndarray, k: int, p_max: int = 40, seed: int = 0, sdist: str = "normal"):
+    """The 16 controller features of a row-major A with m >= n, as the library
+    defines them: the sketch Y = A Omega with l = min(k + p_max, n) columns
+    (the test matrix of Sec. 2.3), the diagonal r_j = |R_jj| of its QR factor
+    (Householder, FP64; unique up to signs) and ||A||_F^2; then
+      [log10 m, log10 n, log10 k, k / n,
+       log10(r_j / r_1) for j = ceil(k/4), ceil(k/2), ceil(3k/4), k, k + 1,
+                            k + max(p_max // 4, 1), k + max(p_max // 2, 1), l
+                        (indices clamped to [1, l]),
+       sum_{j<=k} r_j^2 / sum_j r_j^2,
+       log10(||Y||_F^2 / (l ||A||_F^2)),
+       log10(r_k / r_l),
+       p_max / k]."""
+    m, n = A.shape
+    if m < n:
+        raise ValueError("m >= n expected")
+    l = min(k + p_max, n)
+    Om = omega(n, l, seed, sdist).astype(np.float64)
+    Y = gemm_ax(A, Om)
+    _, R = householder_qr(Y)
+    r = np.maximum(np.abs(np.diag(R)), 1e-30)
+    fa = fro2(A)
+
+    def lr(j):
+        j = min(max(j, 1), l)
+        return math.log10(r[j - 1] / r[0])
+
+    e_all = float(np.sum(r ** 2))
+    e_k = float(np.sum(r[:k] ** 2))
+    tr = float(np.sum(Y * Y))
+    f = [math.log10(m), math.log10(n), math.log10(k), k / n,
+         lr((k + 3) // 4), lr((k + 1) // 2), lr((3 * k + 3) // 4), lr(k), lr(k + 1),
+         lr(k + max(p_max // 4, 1)), lr(k + max(p_max // 2, 1)), lr(l),
+         e_k / e_all if e_all > 0 else 1.0,
+         math.log10(tr / (l * fa)) if (fa > 0 and tr > 0) else 0.0,
+         math.log10(r[min(k, l) - 1] / r[l - 1]),
+         p_max / k]
+    return np.array(f)

@@ -599,3 +599,109 @@ void oracle_set_num_threads(int n)
     (void)n;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned (q, p) controller: the network and its loss, for the gradient    */
+/* check of the GPU training kernels.                                       */
+/*                                                                          */
+/* The paper leaves q and p to the user (Sec. 3.4); this network is not     */
+/* from the paper.  Its definition is the library's parameter format:       */
+/* x_hat = (x - mu) / sd, h1 = relu(W1 x_hat + b1), h2 = relu(W2 h1 + b2),  */
+/* o = W3 h2 + b3 with 16 inputs, 64 + 64 hidden units and 2 outputs;       */
+/* parameters mu[16], sd[16], W1[64][16], b1[64], W2[64][64], b2[64],       */
+/* W3[2][64], b3[2] (row-major).  relu'(0) = 0.  Loss of a sample: the      */
+/* pinball loss summed over the outputs, rho_tau(u) = u (tau - [u < 0]),    */
+/* u = y - o; the loss of a set is the mean over its samples.  The gradient */
+/* is plain reverse-mode differentiation of that expression, in FP64.       */
+/* Pinned by central finite differences and by the closed form of a network */
+/* whose output is its bias.                                                */
+/* ------------------------------------------------------------------------ */
+enum { MLP_I = 16, MLP_H = 64, MLP_O = 2 };
+enum {
+    MLP_MU = 0,
+    MLP_SD = MLP_I,
+    MLP_W1 = 2 * MLP_I,
+    MLP_B1 = MLP_W1 + MLP_H * MLP_I,
+    MLP_W2 = MLP_B1 + MLP_H,
+    MLP_B2 = MLP_W2 + MLP_H * MLP_H,
+    MLP_W3 = MLP_B2 + MLP_H,
+    MLP_B3 = MLP_W3 + MLP_O * MLP_H,
+    MLP_NP = MLP_B3 + MLP_O
+};
+
+int oracle_mlp_params(void) { return MLP_NP; }
+
+static void mlp_layers(const double* P, const double* x, double* xh, double* h1, double* h2, double* o)
+{
+    for (int t = 0; t < MLP_I; ++t) xh[t] = (x[t] - P[MLP_MU + t]) / P[MLP_SD + t];
+    for (int j = 0; j < MLP_H; ++j) {
+        double a = P[MLP_B1 + j];
+        for (int t = 0; t < MLP_I; ++t) a += P[MLP_W1 + j * MLP_I + t] * xh[t];
+        h1[j] = a > 0.0 ? a : 0.0;
+    }
+    for (int j = 0; j < MLP_H; ++j) {
+        double a = P[MLP_B2 + j];
+        for (int t = 0; t < MLP_H; ++t) a += P[MLP_W2 + j * MLP_H + t] * h1[t];
+        h2[j] = a > 0.0 ? a : 0.0;
+    }
+    for (int c = 0; c < MLP_O; ++c) {
+        double a = P[MLP_B3 + c];
+        for (int t = 0; t < MLP_H; ++t) a += P[MLP_W3 + c * MLP_H + t] * h2[t];
+        o[c] = a;
+    }
+}
+
+/* out[i][c] = network output for sample i (X: n x 16, row-major). */
+void oracle_mlp_forward(const double* P, const double* X, int64_t n, double* out)
+{
+    double xh[MLP_I], h1[MLP_H], h2[MLP_H];
+    for (int64_t i = 0; i < n; ++i) mlp_layers(P, X + i * MLP_I, xh, h1, h2, out + i * MLP_O);
+}
+
+/* Mean pinball loss over n samples; grad (MLP_NP - 32 values, W1 first:
+ * the trainable parameters) receives its gradient when non-null. */
+double oracle_mlp_loss_grad(const double* P, const double* X, const double* Y, int64_t n, double tau, double* grad)
+{
+    const int ntrain = MLP_NP - MLP_W1;
+    if (grad)
+        for (int e = 0; e < ntrain; ++e) grad[e] = 0.0;
+    double loss = 0.0;
+    double xh[MLP_I], h1[MLP_H], h2[MLP_H], o[MLP_O], d2[MLP_H], d1[MLP_H];
+    for (int64_t i = 0; i < n; ++i) {
+        mlp_layers(P, X + i * MLP_I, xh, h1, h2, o);
+        double dout[MLP_O];
+        for (int c = 0; c < MLP_O; ++c) {
+            const double u = Y[i * MLP_O + c] - o[c];
+            const double w = (u < 0.0) ? tau - 1.0 : tau;
+            loss += u * w;
+            dout[c] = -w / (double)n;
+        }
+        if (!grad) continue;
+        /* output layer */
+        for (int c = 0; c < MLP_O; ++c) {
+            grad[MLP_B3 - MLP_W1 + c] += dout[c];
+            for (int t = 0; t < MLP_H; ++t) grad[MLP_W3 - MLP_W1 + c * MLP_H + t] += dout[c] * h2[t];
+        }
+        /* second hidden layer */
+        for (int j = 0; j < MLP_H; ++j) {
+            double a = 0.0;
+            for (int c = 0; c < MLP_O; ++c) a += dout[c] * P[MLP_W3 + c * MLP_H + j];
+            d2[j] = h2[j] > 0.0 ? a : 0.0;
+        }
+        for (int j = 0; j < MLP_H; ++j) {
+            grad[MLP_B2 - MLP_W1 + j] += d2[j];
+            for (int t = 0; t < MLP_H; ++t) grad[MLP_W2 - MLP_W1 + j * MLP_H + t] += d2[j] * h1[t];
+        }
+        /* first hidden layer */
+        for (int t = 0; t < MLP_H; ++t) {
+            double a = 0.0;
+            for (int j = 0; j < MLP_H; ++j) a += d2[j] * P[MLP_W2 + j * MLP_H + t];
+            d1[t] = h1[t] > 0.0 ? a : 0.0;
+        }
+        for (int j = 0; j < MLP_H; ++j) {
+            grad[MLP_B1 - MLP_W1 + j] += d1[j];
+            for (int t = 0; t < MLP_I; ++t) grad[j * MLP_I + t] += d1[j] * xh[t];
+        }
+    }
+    return loss / (double)n;
+}

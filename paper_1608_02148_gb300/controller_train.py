@@ -1,0 +1,206 @@
+"""Training data, training and evaluation of the learned (q, p) controller.
+
+The controller picks the number of subspace iterations q and the oversampling
+p of Algorithm rSVD per matrix (the paper leaves them to the user, Sec. 3.4).
+This script
+
+1. draws planted matrices A = H_U diag(sigma) H_V (exact, known spectrum; m
+   uniform in [2000, 20000], n in [1000, 5000], k log-uniform in
+   [10, 200], spectra exponential / power-law / step), so the rank-k optimum
+   ||A - A_k||_F = sqrt(sum_{i>k} sigma_i^2) is known in closed form;
+2. labels each one with the cheapest (q, p) on a grid (cost (2q + 2)(k + p),
+   proportional to the work of the passes) whose rSVD meets
+   ||A - U S V^T||_F <= 1.03 x optimum + 1e-4 ||A||_F, running this library's
+   rSVD (the evaluation asks for 1.05 x: the labels keep a margin for the
+   randomness of Omega; the second term is the resolution of the FP32 path:
+   on spectra decaying by more than ~10^4 across the sketch, FP32 CholeskyQR
+   leaves an error near 1e-4 ||A||_F whatever q and p);
+3. computes the 16 features of each matrix with rsvdgb_controller_features,
+   writes the data set and trains the network on the GPU
+   (rsvdgb_controller_train: hand-written forward / backward kernels, Adam,
+   pinball loss with tau = 0.99);
+4. evaluates on held-out 20000 x 5000 matrices: success rate at the target,
+   passes over A and wall time of the learned mode against fixed p = 10,
+   q = 2.
+
+Usage (one GPU):  python -m paper_1608_02148_gb300.controller_train --train 2500 --eval 64 \\
+                      --out paper_1608_02148_gb300/controller_default.bin
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import struct
+import sys
+import time
+
+import numpy as np
+
+if __package__ in (None, ""):
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from paper_1608_02148_gb300 import inputs, rsvdgb  # noqa: E402
+else:
+    from . import inputs, rsvdgb
+
+P_GRID = (2, 4, 6, 10, 16, 24)
+Q_GRID = (0, 1, 2, 3, 4, 5, 6)
+TARGET_RATIO = 1.05      # accuracy target of the evaluation
+LABEL_RATIO = 1.03       # labels ask for a margin inside it (one Omega per label)
+FP32_FLOOR = 1e-4        # resolution of the FP32 path on extremely graded spectra
+P_MAX = 24
+Q_MAX = 6
+
+
+def residual(A, d, U, V):
+    import torch
+    R = A - (U * d[None, :]) @ V.T
+    return float(torch.linalg.vector_norm(R.double()))
+
+
+def draw(rng, m_range, n_range):
+    # shapes uniform in [m_lo, m_hi] x [n_lo, n_hi] (large shapes, where the
+    # held-out 20000 x 5000 set lies, are not under-represented)
+    m = int(round(rng.uniform(m_range[0], m_range[1])))
+    n = int(round(rng.uniform(n_range[0], n_range[1])))
+    k_hi = min(200, min(m, n) - P_MAX - 1)
+    k = int(round(math.exp(rng.uniform(math.log(10), math.log(k_hi)))))
+    sigma, kind = inputs.controller_spectrum(rng, k, min(m, n))
+    return m, n, k, sigma, kind
+
+
+def target_of(sigma, k, fro, ratio=TARGET_RATIO):
+    opt = math.sqrt(float(np.sum(np.asarray(sigma[k:], dtype=np.float64) ** 2)))
+    return ratio * opt + FP32_FLOOR * fro, opt
+
+
+def run(h, A, k, p, q, seed, mode="fixed"):
+    opts = rsvdgb.make_opts(p=p, q=q, seed=seed, q_mode=mode, p_max=P_MAX, q_max=Q_MAX)
+    d, U, V, info = rsvdgb.rsvdgb_rsvd(h, A, k, opts=opts)
+    return d, U, V, info
+
+
+def label(h, A, k, target, seed):
+    """Cheapest (q, p) of the grid meeting the target; (Q_MAX, P_MAX) if none."""
+    cands = sorted(((2 * q + 2) * (k + p), q, p) for q in Q_GRID for p in P_GRID)
+    runs = 0
+    for _, q, p in cands:
+        d, U, V, info = run(h, A, k, p, q, seed)
+        runs += 1
+        if info.status == 0 and residual(A, d, U, V) <= target:
+            return q, p, runs
+    return Q_MAX, P_MAX, runs
+
+
+def features(h, A, k, seed):
+    opts = rsvdgb.make_opts(seed=seed, p_max=P_MAX, q_max=Q_MAX)
+    return rsvdgb.rsvdgb_controller_features(h, A, k, opts=opts).cpu().numpy().astype(np.float32)
+
+
+def make_dataset(h, count, seed, m_range=(2000, 20000), n_range=(1000, 5000), log=print):
+    import torch
+    rng = np.random.default_rng(seed)
+    X = np.zeros((count, rsvdgb.MLP_FEATURES), np.float32)
+    Y = np.zeros((count, 2), np.float32)
+    runs = 0
+    t0 = time.time()
+    for i in range(count):
+        m, n, k, sigma, kind = draw(rng, m_range, n_range)
+        A = inputs.planted_reflector(m, n, sigma, seed=seed * 100003 + i, device="cuda")
+        fro = math.sqrt(float(np.sum(sigma ** 2)))
+        target, _ = target_of(sigma, k, fro, LABEL_RATIO)
+        X[i] = features(h, A, k, seed + i)
+        q, p, r = label(h, A, k, target, seed + i)
+        runs += r
+        Y[i] = (q, math.log2(p))
+        del A
+        if (i + 1) % 50 == 0:
+            torch.cuda.empty_cache()
+            log(f"  {i + 1}/{count} matrices, {runs} rSVD runs, {time.time() - t0:.0f} s")
+    return X, Y, runs
+
+
+def write_dataset(path, X, Y):
+    with open(path, "wb") as f:
+        f.write(b"RSVDDS01")
+        f.write(struct.pack("<ii", X.shape[0], X.shape[1]))
+        f.write(np.ascontiguousarray(X, dtype="<f4").tobytes())
+        f.write(np.ascontiguousarray(Y, dtype="<f4").tobytes())
+
+
+def evaluate(h, count, seed, m=20000, n=5000):
+    """Learned mode (controller loaded in h) against fixed p = 10, q = 2."""
+    import torch
+    rng = np.random.default_rng(seed)
+    res = {"learned": {"ok": 0, "passes": 0, "ms": 0.0, "p": 0}, "fixed": {"ok": 0, "passes": 0, "ms": 0.0, "p": 0}}
+    st = torch.cuda.current_stream()
+    for i in range(count):
+        _, _, k, sigma, kind = draw(rng, (m, m), (n, n))
+        A = inputs.planted_reflector(m, n, sigma, seed=seed * 100003 + i, device="cuda")
+        fro = math.sqrt(float(np.sum(sigma ** 2)))
+        target, _ = target_of(sigma, k, fro)
+        for name, mode in (("learned", "learned"), ("fixed", "fixed")):
+            run(h, A, k, 10, 2, seed + i, mode)  # warm
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            d, U, V, info = run(h, A, k, 10, 2, seed + i, mode)
+            e1.record(st)
+            torch.cuda.synchronize()
+            r = res[name]
+            r["ms"] += e0.elapsed_time(e1)
+            r["passes"] += 2 * info.q_used + 2
+            r["p"] += info.p_used
+            r["ok"] += int(info.status == 0 and residual(A, d, U, V) <= target)
+        del A
+    for r in res.values():
+        r["success_rate"] = r.pop("ok") / count
+        r["mean_passes"] = r.pop("passes") / count
+        r["mean_ms"] = r.pop("ms") / count
+        r["mean_p"] = r.pop("p") / count
+    res["matrices"] = count
+    res["shape"] = [m, n]
+    return res
+
+
+def main(argv=None):
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=2500, help="training matrices")
+    ap.add_argument("--eval", type=int, default=64, help="held-out 20000 x 5000 matrices")
+    ap.add_argument("--seed", type=int, default=0x160802148 + 5000)
+    ap.add_argument("--epochs", type=int, default=500)
+    ap.add_argument("--tau", type=float, default=0.99)
+    ap.add_argument("--dataset", default=None, help="data set file (written, or read with --reuse)")
+    ap.add_argument("--reuse", action="store_true", help="train on an existing data set file")
+    ap.add_argument("--out", required=True, help="parameter file to write")
+    ap.add_argument("--report", default=None, help="JSON report")
+    args = ap.parse_args(argv)
+    h = rsvdgb.Handle(0)
+    ds = args.dataset or (os.path.splitext(args.out)[0] + ".dataset")
+    report = {}
+    if not args.reuse:
+        X, Y, runs = make_dataset(h, args.train, args.seed)
+        write_dataset(ds, X, Y)
+        report["dataset"] = {"matrices": args.train, "rsvd_runs": runs,
+                             "label_q_mean": float(Y[:, 0].mean()), "label_p_mean": float(np.mean(2 ** Y[:, 1]))}
+    o = rsvdgb.rsvdgb_default_train_opts()
+    o.epochs = args.epochs
+    o.tau = args.tau
+    t0 = time.time()
+    loss = rsvdgb.rsvdgb_controller_train(h, ds, args.out, o)
+    report["train"] = {"final_loss": loss, "epochs": args.epochs, "seconds": time.time() - t0}
+    if args.eval > 0:
+        report["eval"] = evaluate(h, args.eval, args.seed + 7777)
+    print(json.dumps(report, indent=1))
+    if args.report:
+        with open(args.report, "w") as f:
+            json.dump(report, f, indent=1)
+    h.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

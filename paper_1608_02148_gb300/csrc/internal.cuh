@@ -21,6 +21,33 @@ namespace rsvdgb {
         if (err_ != cudaSuccess) return RSVDGB_ERR_CUDA;        \
     } while (0)
 
+// ---------------------------------------------------------------------------
+// Learned (q, p) controller (controller.cu)
+// ---------------------------------------------------------------------------
+constexpr int kMlpIn = 16, kMlpHidden = 64, kMlpOut = 2;
+// mu[16], sd[16], W1[64][16], b1[64], W2[64][64], b2[64], W3[2][64], b3[2]
+constexpr int kMlpParams = 2 * kMlpIn + kMlpHidden * kMlpIn + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden +
+                           kMlpOut * kMlpHidden + kMlpOut;
+// 16 features of the first sketch from its CholeskyQR factor R (lmax x lmax,
+// row-major) and ||A||_F^2.
+void launch_controller_features(cudaStream_t s, const float* R, int lmax, const double* fro2, int64_t m, int64_t n,
+                                int k, int p_max, float* feats);
+// out[i][0..1] = MLP(X[i]) for n samples (device pointers, P = kMlpParams floats).
+void launch_mlp_forward(cudaStream_t s, const float* P, const float* X, int n, float* out);
+// (q, p) from the network output: q in [0, q_max], p in [p_min, p_max], k + p <= mn.
+void launch_controller_decide(cudaStream_t s, const float* out2, int q_max, int p_min, int p_max, int k, int64_t mn,
+                              int* qp);
+// Gradient of the mean pinball loss over nb samples (rows idx[0..nb) of X, Y,
+// or the first nb rows when idx is null) with respect to the trainable
+// parameters (kMlpParams - 32 floats, W1 first); loss (may be null) gets the
+// mean loss.  scratch holds mlp_grad_scratch_floats(nb) floats.
+size_t mlp_grad_scratch_floats(int nb);
+int launch_mlp_grad(cudaStream_t s, const float* P, const float* X, const float* Y, const int* idx, int nb, float tau,
+                    float* scratch, float* grad, float* loss);
+// Train from host data (n samples); writes kMlpParams floats to P_host_out.
+int mlp_train(cudaStream_t s, const float* X_host, const float* Y_host, int n, int epochs, int batch, float lr,
+              float tau, uint64_t seed, float* P_host_out, float* final_loss);
+
 // Process-wide count of kernel launches issued by the library.
 void count_launches(int n = 1);
 int64_t launches_so_far();

@@ -19,12 +19,17 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
 
 #include "internal.cuh"
+
+static_assert(RSVDGB_MLP_PARAMS == rsvdgb::kMlpParams, "controller parameter count");
+static_assert(RSVDGB_MLP_FEATURES == rsvdgb::kMlpIn, "controller feature count");
 
 using namespace rsvdgb;
 
@@ -54,6 +59,9 @@ struct rsvdgb_handle {
     size_t host_stage_bytes = 0;
     PassProfile prof;
     BatchedPlan* batched = nullptr;  // plan of the last batch layout
+    float* ctl_params = nullptr;     // learned (q, p) controller (device, kMlpParams floats)
+    float* ctl_scratch = nullptr;    // features, network output, decision (device)
+    int* ctl_host = nullptr;         // pinned host copy of the decision (q, p)
 };
 
 namespace {
@@ -136,7 +144,7 @@ size_t partial_floats(const Geom& g, int sm_count)
     return (size_t)need;
 }
 
-void carve_work(Carve& c, const Geom& g, int sm_count, Work& w)
+void carve_work(Carve& c, const Geom& g, int sm_count, Work& w, int L_lo = 0)
 {
     const int64_t L = g.L;
     w.Pt = c.take<float>(L * g.ldn);
@@ -160,7 +168,16 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w)
     }
     w.Wt = c.take<float>(L * g.ldn);
     w.Zt = c.take<float>(L * g.ldn);
-    w.part = c.take<float>(partial_floats(g, sm_count));
+    // split-K partials: the learned mode runs the sketch at g.L and the rest at
+    // any narrower width down to L_lo, so take the largest need over them
+    size_t part = partial_floats(g, sm_count);
+    for (int Lx = std::max(16, L_lo); L_lo > 0 && Lx < g.L; Lx += 16) {
+        Geom gx = g;
+        gx.L = Lx;
+        gx.l = std::min(gx.l, Lx);
+        part = std::max(part, partial_floats(gx, sm_count));
+    }
+    w.part = c.take<float>(part);
     w.G = c.take<float>(L * L);
     w.T1 = c.take<float>(L * L);
     w.T2 = c.take<float>(L * L);
@@ -433,29 +450,81 @@ struct Outputs {
 };
 
 // Algorithm rqb (+ rSVD when d != nullptr) on the logical matrix.
-int run_fp32(rsvdgb_handle* h, const Geom& g, int k, int q, int sdist, uint64_t seed, const Outputs& o)
+// Learned choice of (q, p): the sketch is taken at the widest width, the
+// controller's decision is read back (one stream synchronisation) and the
+// run continues with the first k + p columns of that sketch.
+struct Learned {
+    int k;
+    int p_max, q_max;
+    float* feats_out;  // features only (rsvdgb_controller_features): stop after them
+};
+
+// Steps 2-3 at the geometry g: Omega, Y = A Omega with ||A||_F^2, Gram of Y.
+void sketch(rsvdgb_handle* h, const Geom& g, Work& w, int sdist, uint64_t seed)
+{
+    const cudaStream_t s = h->stream;
+    launch_omega(s, g.n, g.ldn, g.l, g.L, seed, sdist, w.Pt, g.ldn);
+    split_panel(s, g, w);
+    apply_A(h, g, w, w.fro2);
+    if (g.use_tc)
+        tc_gram(h, g, w, w.Yt, w.Yth, w.Ytl, g.ldm, g.m);
+    else
+        gram(s, h->sm_count, w.Yt, g.ldm, g.m, g.l, w.part, w.G);
+}
+
+// Controller features of the sketch in w (its Gram in w.G), from the
+// CholeskyQR factor R of Y (Y = Q R) and ||A||_F^2.
+void sketch_features(rsvdgb_handle* h, const Geom& g, Work& w, int k, int p_max, float* feats)
+{
+    const cudaStream_t s = h->stream;
+    launch_chol_inv(s, w.G, g.l, 0.f, w.R1, w.T, w.status, w.breakdowns);
+    launch_controller_features(s, w.R1, g.l, w.fro2, g.m, g.n, k, p_max, feats);
+}
+
+int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, const Outputs& o,
+             const Learned* lc = nullptr)
 {
     const cudaStream_t s = h->stream;
     const int sm = h->sm_count;
     Carve probe(nullptr);
     Work w{};
-    carve_work(probe, g, sm, w);
+    const int L_lo = lc ? (int)round_up(std::min<int64_t>((int64_t)k + 2, g.n), 16) : 0;
+    carve_work(probe, g, sm, w, L_lo);
     int rc = ensure_workspace(h, probe.off + 1024);
     if (rc) return rc;
     Carve c(h->ws);
-    carve_work(c, g, sm, w);
-    const int l = g.l;
+    carve_work(c, g, sm, w, L_lo);
 
     launch_clear_scalars(s, w.status, w.breakdowns, w.fro2);
-    // step 2: Omega (n x l) into the panel
-    launch_omega(s, g.n, g.ldn, l, g.L, seed, sdist, w.Pt, g.ldn);
-    split_panel(s, g, w);
-    // step 3: Y = A Omega, with ||A||_F^2 accumulated on the way
-    apply_A(h, g, w, w.fro2);
-    if (g.use_tc)
-        tc_gram(h, g, w, w.Yt, w.Yth, w.Ytl, g.ldm, g.m);
-    else
-        gram(s, sm, w.Yt, g.ldm, g.m, l, w.part, w.G);
+    // steps 2-3: Omega (n x l) into the panel, Y = A Omega with ||A||_F^2, Gram
+    sketch(h, g, w, sdist, seed);
+    if (lc) {
+        float* feats = lc->feats_out ? lc->feats_out : h->ctl_scratch;
+        sketch_features(h, g, w, k, lc->p_max, feats);
+        if (lc->feats_out) {
+            RSVDGB_CUDA_TRY(cudaGetLastError());
+            return RSVDGB_OK;
+        }
+        // a shifted retry of the sketch's Cholesky (a sketch wider than the rank
+        // of A) is not a breakdown of the factorisation that is reported
+        RSVDGB_CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(int), s));
+        RSVDGB_CUDA_TRY(cudaMemsetAsync(w.breakdowns, 0, sizeof(int), s));
+        float* out2 = h->ctl_scratch + 16;
+        int* qp = (int*)(h->ctl_scratch + 32);
+        launch_mlp_forward(s, h->ctl_params, feats, 1, out2);
+        launch_controller_decide(s, out2, lc->q_max, 2, lc->p_max, k, g.n, qp);
+        RSVDGB_CUDA_TRY(cudaMemcpyAsync(h->ctl_host, qp, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        RSVDGB_CUDA_TRY(cudaStreamSynchronize(s));
+        q = h->ctl_host[0];
+        // continue with the first k + p columns of the sketch (Omega nested in l)
+        g.l = (int)std::min<int64_t>((int64_t)k + h->ctl_host[1], g.n);
+        g.L = (int)round_up(g.l, 16);
+        if (g.use_tc)
+            tc_gram(h, g, w, w.Yt, w.Yth, w.Ytl, g.ldm, g.m);
+        else
+            gram(s, sm, w.Yt, g.ldm, g.m, g.l, w.part, w.G);
+    }
+    const int l = g.l;
     // step 4: subspace iterations
     for (int it = 0; it < q; ++it) {
         // Q = qr(Y): only the span is carried forward, so one Cholesky step
@@ -603,6 +672,20 @@ void rsvdgb_default_opts(rsvdgb_opts* o)
     o->seed = 0;
     o->layout = RSVDGB_ROW_MAJOR;
     o->engine = RSVDGB_ENGINE_AUTO;
+    o->q_mode = RSVDGB_Q_FIXED;
+    o->p_max = 24;
+    o->q_max = 6;
+}
+
+void rsvdgb_default_train_opts(rsvdgb_train_opts* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->epochs = 300;
+    o->batch = 256;
+    o->lr = 2e-3f;
+    o->tau = 0.99f;
+    o->seed = 0;
 }
 
 const char* rsvdgb_status_string(int status)
@@ -650,6 +733,9 @@ int rsvdgb_destroy(rsvdgb_handle* h)
     if (h->host_stage) cudaFree(h->host_stage);
     for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
     destroy_plan(h->batched);
+    if (h->ctl_params) cudaFree(h->ctl_params);
+    if (h->ctl_scratch) cudaFree(h->ctl_scratch);
+    if (h->ctl_host) cudaFreeHost(h->ctl_host);
     delete h;
     return RSVDGB_OK;
 }
@@ -672,8 +758,12 @@ int rsvdgb_rsvd(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t l
     else
         rsvdgb_default_opts(&o);
     if (o.q < 0 || o.sdist < 0 || o.sdist > 2) return RSVDGB_ERR_INVALID_ARG;
+    if (o.q_mode != RSVDGB_Q_FIXED && o.q_mode != RSVDGB_Q_LEARNED) return RSVDGB_ERR_INVALID_ARG;
+    if (o.q_mode == RSVDGB_Q_LEARNED && (o.p_max < 2 || o.q_max < 0)) return RSVDGB_ERR_INVALID_ARG;
+    // learned mode with a loaded controller: sketch at the widest width first
+    const bool learned = o.q_mode == RSVDGB_Q_LEARNED && h->ctl_params != nullptr;
     Geom g{};
-    rc = make_geom(A, m, n, lda, dtype, o.layout, k, o.p, o.engine, o.prec, g);
+    rc = make_geom(A, m, n, lda, dtype, o.layout, k, learned ? o.p_max : o.p, o.engine, o.prec, g);
     if (rc) return rc;
     if (nu < 0) nu = k;
     if (nv < 0) nv = k;
@@ -689,6 +779,10 @@ int rsvdgb_rsvd(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t l
     } else {
         out.U = V; out.ldU = ldv; out.nU = nv;
         out.V = U; out.ldV = ldu; out.nV = nu;
+    }
+    if (learned) {
+        const Learned lc{k, o.p_max, o.q_max, nullptr};
+        return run_fp32(h, g, k, o.q, o.sdist, o.seed, out, &lc);
     }
     return run_fp32(h, g, k, o.q, o.sdist, o.seed, out);
 }
@@ -895,6 +989,132 @@ int rsvdgb_rsvd_batched(rsvdgb_handle* h, int batch, const rsvdgb_matrix_desc* d
         if (!r.d || (r.U && r.ldu < k) || (r.V && r.ldv < k)) return RSVDGB_ERR_INVALID_ARG;
     }
     return batched_rsvd(&h->batched, h->device, h->sm_count, h->stream, batch, descs, k, o, outs, infos);
+}
+
+static int controller_alloc(rsvdgb_handle* h)
+{
+    if (!h->ctl_params) RSVDGB_CUDA_TRY(cudaMalloc(&h->ctl_params, sizeof(float) * kMlpParams));
+    if (!h->ctl_scratch) RSVDGB_CUDA_TRY(cudaMalloc(&h->ctl_scratch, sizeof(float) * 64));
+    if (!h->ctl_host) RSVDGB_CUDA_TRY(cudaMallocHost(&h->ctl_host, sizeof(int) * 2));
+    return RSVDGB_OK;
+}
+
+int rsvdgb_controller_set(rsvdgb_handle* h, const float* params_host)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!params_host) return RSVDGB_ERR_INVALID_ARG;
+    for (int i = 0; i < kMlpParams; ++i)
+        if (!std::isfinite(params_host[i])) return RSVDGB_ERR_INVALID_ARG;
+    for (int i = 0; i < kMlpIn; ++i)
+        if (!(params_host[kMlpIn + i] > 0.f)) return RSVDGB_ERR_INVALID_ARG;  // sd > 0
+    rc = controller_alloc(h);
+    if (rc) return rc;
+    RSVDGB_CUDA_TRY(cudaMemcpyAsync(h->ctl_params, params_host, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice,
+                                    h->stream));
+    RSVDGB_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return RSVDGB_OK;
+}
+
+int rsvdgb_controller_load(rsvdgb_handle* h, const char* path)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!path) return RSVDGB_ERR_INVALID_ARG;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return RSVDGB_ERR_INVALID_ARG;
+    char magic[8];
+    int32_t count = 0;
+    std::vector<float> P(kMlpParams);
+    const bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "RSVDMLP1", 8) == 0 &&
+                    std::fread(&count, 4, 1, f) == 1 && count == kMlpParams &&
+                    std::fread(P.data(), sizeof(float), kMlpParams, f) == (size_t)kMlpParams;
+    std::fclose(f);
+    if (!ok) return RSVDGB_ERR_INVALID_ARG;
+    return rsvdgb_controller_set(h, P.data());
+}
+
+int rsvdgb_controller_train(rsvdgb_handle* h, const char* dataset_path, const rsvdgb_train_opts* opts,
+                            const char* out_path, float* final_loss)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!dataset_path || !out_path) return RSVDGB_ERR_INVALID_ARG;
+    rsvdgb_train_opts o;
+    if (opts)
+        o = *opts;
+    else
+        rsvdgb_default_train_opts(&o);
+    FILE* f = std::fopen(dataset_path, "rb");
+    if (!f) return RSVDGB_ERR_INVALID_ARG;
+    char magic[8];
+    int32_t n = 0, nf = 0;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "RSVDDS01", 8) == 0 &&
+              std::fread(&n, 4, 1, f) == 1 && std::fread(&nf, 4, 1, f) == 1 && n > 0 && nf == kMlpIn;
+    std::vector<float> X, Y;
+    if (ok) {
+        X.resize((size_t)n * kMlpIn);
+        Y.resize((size_t)n * kMlpOut);
+        ok = std::fread(X.data(), sizeof(float), X.size(), f) == X.size() &&
+             std::fread(Y.data(), sizeof(float), Y.size(), f) == Y.size();
+    }
+    std::fclose(f);
+    if (!ok) return RSVDGB_ERR_INVALID_ARG;
+    for (float v : X)
+        if (!std::isfinite(v)) return RSVDGB_ERR_INVALID_ARG;
+    for (float v : Y)
+        if (!std::isfinite(v)) return RSVDGB_ERR_INVALID_ARG;
+    std::vector<float> P(kMlpParams);
+    rc = mlp_train(h->stream, X.data(), Y.data(), n, o.epochs, o.batch, o.lr, o.tau, o.seed, P.data(), final_loss);
+    if (rc) return rc;
+    FILE* g = std::fopen(out_path, "wb");
+    if (!g) return RSVDGB_ERR_INVALID_ARG;
+    const int32_t count = kMlpParams;
+    ok = std::fwrite("RSVDMLP1", 1, 8, g) == 8 && std::fwrite(&count, 4, 1, g) == 1 &&
+         std::fwrite(P.data(), sizeof(float), kMlpParams, g) == (size_t)kMlpParams;
+    ok = (std::fclose(g) == 0) && ok;
+    if (!ok) return RSVDGB_ERR_INVALID_ARG;
+    return rsvdgb_controller_set(h, P.data());
+}
+
+int rsvdgb_controller_features(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k,
+                               const rsvdgb_opts* opts, float* feats)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    rsvdgb_opts o;
+    if (opts)
+        o = *opts;
+    else
+        rsvdgb_default_opts(&o);
+    if (!feats || o.p_max < 2 || o.sdist < 0 || o.sdist > 2) return RSVDGB_ERR_INVALID_ARG;
+    Geom g{};
+    rc = make_geom(A, m, n, lda, dtype, o.layout, k, o.p_max, o.engine, o.prec, g);
+    if (rc) return rc;
+    Outputs out{};
+    const Learned lc{k, o.p_max, o.q_max, feats};
+    return run_fp32(h, g, k, 0, o.sdist, o.seed, out, &lc);
+}
+
+int rsvdgb_mlp_forward(rsvdgb_handle* h, const float* P, const float* X, int n, float* out)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!P || !X || !out || n < 1) return RSVDGB_ERR_INVALID_ARG;
+    launch_mlp_forward(h->stream, P, X, n, out);
+    RSVDGB_CUDA_TRY(cudaGetLastError());
+    return RSVDGB_OK;
+}
+
+int rsvdgb_mlp_grad(rsvdgb_handle* h, const float* P, const float* X, const float* Y, int n, float tau, float* grad,
+                    float* loss)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!P || !X || !Y || !grad || n < 1 || !(tau > 0.f && tau < 1.f)) return RSVDGB_ERR_INVALID_ARG;
+    rc = ensure_workspace(h, sizeof(float) * mlp_grad_scratch_floats(n) + 256);
+    if (rc) return rc;
+    return launch_mlp_grad(h->stream, P, X, Y, nullptr, n, tau, (float*)h->ws, grad, loss);
 }
 
 int rsvdgb_profile_passes(rsvdgb_handle* h, int enable)

@@ -157,3 +157,44 @@ def ragged_batch(count: int, m_range=(256, 4096), n_range=(64, 1024), seed: int 
             A -= 2.0 * (A @ v) @ v.T
         mats.append(A.to(torch.float32).contiguous())
     return mats, rates
+
+
+def planted_reflector(m: int, n: int, sigma, seed: int, device="cpu"):
+    """A = H_U diag(sigma) H_V (float32), sigma on the leading diagonal and H_U,
+    H_V products of two seeded Householder reflectors: exactly the planted
+    singular values, built in FP64 on the device."""
+    import torch
+
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+    mn = min(m, n)
+    sig = torch.as_tensor(np.asarray(sigma, dtype=np.float64)[:mn], device=device)
+    A = torch.zeros(m, n, dtype=torch.float64, device=device)
+    idx = torch.arange(sig.shape[0], device=device)
+    A[idx, idx] = sig
+    for _ in range(2):
+        u = torch.randn(m, 1, generator=gen, device=device, dtype=torch.float64)
+        u /= u.norm()
+        A -= 2.0 * u @ (u.T @ A)
+        v = torch.randn(n, 1, generator=gen, device=device, dtype=torch.float64)
+        v /= v.norm()
+        A -= 2.0 * (A @ v) @ v.T
+    return A.to(torch.float32).contiguous()
+
+
+def controller_spectrum(rng, k: int, count: int):
+    """A random spectrum of one of three families (descending, sigma_1 = 1):
+    exponential exp(-r (i - 1)), r log-uniform in [1e-3, 0.5]; power law
+    i^-alpha, alpha uniform in [0.25, 3]; step: 1 for i <= s, s uniform in
+    [k/2, 2k], then delta log-uniform in [1e-4, 0.3].  Returns (sigma, label)."""
+    i = np.arange(1, count + 1, dtype=np.float64)
+    kind = int(rng.integers(0, 3))
+    if kind == 0:
+        r = math.exp(rng.uniform(math.log(1e-3), math.log(0.5)))
+        return np.exp(-r * (i - 1)), f"exp r={r:.4g}"
+    if kind == 1:
+        a = rng.uniform(0.25, 3.0)
+        return i ** (-a), f"power alpha={a:.3g}"
+    s = int(rng.integers(max(1, k // 2), 2 * k + 1))
+    d = math.exp(rng.uniform(math.log(1e-4), math.log(0.3)))
+    return np.where(i <= s, 1.0, d), f"step s={s} delta={d:.3g}"

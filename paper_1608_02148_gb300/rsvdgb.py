@@ -27,7 +27,14 @@ LAYOUT = {"row": 0, "col": 1}
 EXPORTS = ["rsvdgb_create", "rsvdgb_destroy", "rsvdgb_set_stream", "rsvdgb_default_opts", "rsvdgb_status_string",
            "rsvdgb_sketch_width", "rsvdgb_rsvd", "rsvdgb_rsvd_host", "rsvdgb_rqb", "rsvdgb_omega",
            "rsvdgb_pass_ax", "rsvdgb_pass_atx", "rsvdgb_profile_passes", "rsvdgb_profile_read",
-           "rsvdgb_kernel_launches", "rsvdgb_pass_atx_noalloc", "rsvdgb_rsvd_batched"]
+           "rsvdgb_kernel_launches", "rsvdgb_pass_atx_noalloc", "rsvdgb_rsvd_batched",
+           "rsvdgb_default_train_opts", "rsvdgb_controller_load", "rsvdgb_controller_set",
+           "rsvdgb_controller_train", "rsvdgb_controller_features", "rsvdgb_mlp_forward", "rsvdgb_mlp_grad"]
+
+Q_MODE = {"fixed": 0, "learned": 1}
+MLP_PARAMS = 5410  # RSVDGB_MLP_PARAMS
+MLP_FEATURES = 16  # RSVDGB_MLP_FEATURES
+MLP_TRAINABLE = MLP_PARAMS - 2 * MLP_FEATURES
 
 # Static scratch of rsvdgb_pass_atx_noalloc (RSVDGB_NOALLOC_SCRATCH_BYTES).
 NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -36,7 +43,13 @@ NOALLOC_SCRATCH_BYTES = 16 << 20
 class RsvdgbOpts(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("q", ctypes.c_int32), ("sdist", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("layout", ctypes.c_int32), ("engine", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("q_mode", ctypes.c_int32), ("p_max", ctypes.c_int32), ("q_max", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+class RsvdgbTrainOpts(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("tau", ctypes.c_float),
+                ("seed", ctypes.c_uint64), ("reserved", ctypes.c_int32 * 4)]
 
 
 class RsvdgbInfo(ctypes.Structure):
@@ -104,6 +117,15 @@ def load(path: Path | str | None = None):
                                         ctypes.POINTER(RsvdgbResultDesc), P]
     lib.rsvdgb_kernel_launches.argtypes = []
     lib.rsvdgb_kernel_launches.restype = I64
+    lib.rsvdgb_default_train_opts.argtypes = [ctypes.POINTER(RsvdgbTrainOpts)]
+    lib.rsvdgb_default_train_opts.restype = None
+    lib.rsvdgb_controller_load.argtypes = [P, ctypes.c_char_p]
+    lib.rsvdgb_controller_set.argtypes = [P, P]
+    lib.rsvdgb_controller_train.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(RsvdgbTrainOpts), ctypes.c_char_p,
+                                            ctypes.POINTER(ctypes.c_float)]
+    lib.rsvdgb_controller_features.argtypes = [P, P, I64, I64, I64, I, I, ctypes.POINTER(RsvdgbOpts), P]
+    lib.rsvdgb_mlp_forward.argtypes = [P, P, P, I, P]
+    lib.rsvdgb_mlp_grad.argtypes = [P, P, P, P, I, ctypes.c_float, P, P]
     _lib = lib
     return lib
 
@@ -133,11 +155,17 @@ def _rowmajor_ld(t):
     return t.stride(0)
 
 
-def make_opts(p=10, q=2, sdist="normal", prec="fp32", seed=0, layout="row", engine="auto") -> RsvdgbOpts:
+def make_opts(p=10, q=2, sdist="normal", prec="fp32", seed=0, layout="row", engine="auto", q_mode="fixed",
+              p_max=None, q_max=None) -> RsvdgbOpts:
     o = RsvdgbOpts()
     load().rsvdgb_default_opts(ctypes.byref(o))
     o.p, o.q, o.sdist, o.prec = p, q, SDIST[sdist], PREC[prec]
     o.seed, o.layout, o.engine = seed, LAYOUT[layout], ENGINE[engine]
+    o.q_mode = Q_MODE[q_mode]
+    if p_max is not None:
+        o.p_max = p_max
+    if q_max is not None:
+        o.q_max = q_max
     return o
 
 
@@ -372,3 +400,63 @@ def rsvdgb_rsvd_batched(h: Handle, call: BatchedCall, opts: RsvdgbOpts | None = 
                                     call.infos.data_ptr())
     _check("rsvdgb_rsvd_batched", rc)
     return call
+
+
+# ---------------------------------------------------------------- learned (q, p) controller
+def rsvdgb_default_train_opts() -> RsvdgbTrainOpts:
+    o = RsvdgbTrainOpts()
+    load().rsvdgb_default_train_opts(ctypes.byref(o))
+    return o
+
+
+def rsvdgb_controller_load(h: Handle, path):
+    _check("rsvdgb_controller_load", load().rsvdgb_controller_load(h.ptr, str(path).encode()))
+
+
+def rsvdgb_controller_set(h: Handle, params):
+    """params: host float32 array of MLP_PARAMS values."""
+    import numpy as np
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    if a.size != MLP_PARAMS:
+        raise ValueError(f"expected {MLP_PARAMS} parameters")
+    _check("rsvdgb_controller_set", load().rsvdgb_controller_set(h.ptr, a.ctypes.data))
+
+
+def rsvdgb_controller_train(h: Handle, dataset_path, out_path, opts: RsvdgbTrainOpts | None = None) -> float:
+    o = opts if opts is not None else rsvdgb_default_train_opts()
+    loss = ctypes.c_float(0.0)
+    _check("rsvdgb_controller_train", load().rsvdgb_controller_train(h.ptr, str(dataset_path).encode(), ctypes.byref(o),
+                                                                     str(out_path).encode(), ctypes.byref(loss)))
+    return float(loss.value)
+
+
+def rsvdgb_controller_features(h: Handle, A, k, opts: RsvdgbOpts | None = None, out=None):
+    """16 features of A (device float32 tensor), as the learned mode computes them."""
+    torch = _torch()
+    o = opts if opts is not None else rsvdgb_default_opts()
+    m, n = A.shape
+    f = out if out is not None else torch.empty(MLP_FEATURES, dtype=torch.float32, device=A.device)
+    _check("rsvdgb_controller_features", load().rsvdgb_controller_features(
+        h.ptr, A.data_ptr(), m, n, _rowmajor_ld(A), _dtype_code(A), k, ctypes.byref(o), f.data_ptr()))
+    return f
+
+
+def rsvdgb_mlp_forward(h: Handle, P, X):
+    torch = _torch()
+    X = X.contiguous()
+    out = torch.empty(X.shape[0], 2, dtype=torch.float32, device=X.device)
+    _check("rsvdgb_mlp_forward", load().rsvdgb_mlp_forward(h.ptr, P.data_ptr(), X.data_ptr(), X.shape[0],
+                                                           out.data_ptr()))
+    return out
+
+
+def rsvdgb_mlp_grad(h: Handle, P, X, Y, tau=0.9):
+    """Gradient of the mean pinball loss w.r.t. the trainable parameters, and the loss."""
+    torch = _torch()
+    X = X.contiguous()
+    Y = Y.contiguous()
+    grad = torch.empty(MLP_TRAINABLE, dtype=torch.float32, device=X.device)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    _check("rsvdgb_mlp_grad", load().rsvdgb_mlp_grad(h.ptr, P.data_ptr(), X.data_ptr(), Y.data_ptr(), X.shape[0],
+                                                     ctypes.c_float(tau), grad.data_ptr(), loss.data_ptr()))
+    return grad, loss
