@@ -430,7 +430,8 @@ __device__ __forceinline__ float warp_sum(float v)
 // Otherwise the sweeps are repeated from the original M with J accumulated.
 //
 // MODE 0: columns in the global work buffer; 1: columns in shared memory;
-// 2: also a staged copy of M (rows padded to a multiple of 4).  MODE is a
+// 2: also a staged copy of M (rows padded to a multiple of 4); 3: the columns
+// of M in shared memory, J (accumulated or M^T u) in global memory.  MODE is a
 // template parameter so that shared-memory columns get shared-memory loads.
 template <int E, int NT, int MODE>
 __global__ void __launch_bounds__(NT, 1)
@@ -443,7 +444,7 @@ __global__ void __launch_bounds__(NT, 1)
     constexpr int use_smem = MODE;
     extern __shared__ __align__(16) float sm[];
     float* Mc = MODE ? sm : gwork;
-    float* Jc = MODE ? sm + (size_t)L * Lp : gwork + (size_t)L * Lp;
+    float* Jc = (MODE == 1 || MODE == 2) ? sm + (size_t)L * Lp : gwork + (size_t)L * Lp;
     __shared__ int rotated;
     __shared__ int need_j;
     __shared__ float sv[256];
@@ -844,6 +845,8 @@ int init_small_kernels()
     rc |= raise_smem_limit(jacobi_kernel<14, 512, 2>, optin);
     rc |= raise_smem_limit(jacobi_kernel<16, 512, 2>, optin);
     rc |= raise_smem_limit(jacobi_kernel<20, 512, 1>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<24, 512, 3>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<28, 512, 3>, optin);
     return rc ? RSVDGB_ERR_CUDA : RSVDGB_OK;
 }
 
@@ -867,14 +870,18 @@ void launch_jacobi_typed(cudaStream_t s, const float* M, int l, int L, float* si
 {
     const size_t Lp = 8 * E;
     const size_t cols = (size_t)2 * L * Lp * sizeof(float);
-    const size_t bytes = MODE == 2 ? cols + (size_t)l * ((L + 3) & ~3) * sizeof(float) : (MODE == 1 ? cols : 0);
+    const size_t bytes = MODE == 2   ? cols + (size_t)l * ((L + 3) & ~3) * sizeof(float)
+                         : MODE == 1 ? cols
+                         : MODE == 3 ? cols / 2
+                                     : 0;
     jacobi_kernel<E, NT, MODE><<<1, NT, bytes, s>>>(M, l, L, sigma, Ut, Jt, work, sweeps, kv);
 }
 
 // Columns of L = l rounded up to even rows; E elements per lane of the eight
 // lanes of a pair, so the padded column stride 8 E covers L.  Up to L = 128
 // the columns and a staged M fit in shared memory (MODE 2), up to 160 the
-// columns alone (MODE 1); wider sketches keep the columns in global memory.
+// columns alone (MODE 1); wider sketches keep M's columns in shared memory and
+// J in global memory (MODE 3).
 void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, float* Ut, float* Jt, float* work,
                        int* sweeps, int kv)
 {
@@ -889,8 +896,8 @@ void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, floa
     else if (e <= 14) launch_jacobi_typed<14, 512, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
     else if (e <= 16) launch_jacobi_typed<16, 512, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
     else if (e <= 20) launch_jacobi_typed<20, 512, 1>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
-    else if (e <= 24) launch_jacobi_typed<24, 512, 0>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
-    else launch_jacobi_typed<28, 512, 0>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 24) launch_jacobi_typed<24, 512, 3>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else launch_jacobi_typed<28, 512, 3>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
     count_launches();
 }
 
