@@ -129,11 +129,14 @@ bool tc_pass_supported(int64_t m, int64_t n, int64_t lda, int l_pad, const void*
 // out_rowmajor (direct output only) out is written row-major:
 // out[idx * ld_out + j] for j < out_cols.  With bf16_panel the products run in
 // BF16 (A rounded to nearest BF16, P given as one BF16 panel in Phi with
-// leading dimension ldp elements; Plo unused), one MMA per K step.
+// leading dimension ldp elements; Plo unused), one MMA per K step.  With
+// a_bf16, A (passed through the float pointer) holds BF16 values: exact in
+// TF32, so the FP32-accurate product needs two MMAs (a p_hi + a p_lo).
 int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int64_t m, int64_t n, int64_t lda,
                    const float* Phi, const float* Plo, int64_t ldp, int l_pad, float* out, float* out_hi,
                    float* out_lo, int64_t ld_out, float* partial, int64_t want_splits, int64_t* splits_out,
-                   int* status, double* fro2, int out_rowmajor = 0, int out_cols = 0, int bf16_panel = 0);
+                   int* status, double* fro2, int out_rowmajor = 0, int out_cols = 0, int bf16_panel = 0,
+                   int a_bf16 = 0);
 int64_t tc_pass_max_splits(int64_t m, int64_t n, int l_pad, int sm_count);
 int64_t tc_split_count(int64_t k_total, int64_t units, int sm_count);
 // l x l row-major T -> column-major L x L TF32 hi/lo panel (zero padded),

@@ -307,10 +307,10 @@ void pass_over_A(rsvdgb_handle* h, const Geom& g, Work& w, bool A_side, const fl
     if (Pbf)
         launch_tc_gemm(s, h->sm_count, stored_atx, (const float*)g.A, g.sm(), g.sn(), g.lda, (const float*)Pbf,
                        nullptr, ldP, g.L, out, out_h, out_l, ldO, w.part, stored_atx ? 0 : 1, &splits, w.status, fro2,
-                       0, 0, 1);
+                       0, 0, 1, g.a_bf16);
     else
         launch_tc_gemm(s, h->sm_count, stored_atx, (const float*)g.A, g.sm(), g.sn(), g.lda, Ph, Pl, ldP, g.L, out,
-                       out_h, out_l, ldO, w.part, stored_atx ? 0 : 1, &splits, w.status, fro2);
+                       out_h, out_l, ldO, w.part, stored_atx ? 0 : 1, &splits, w.status, fro2, 0, 0, 0, g.a_bf16);
     prof_mark(h, false, a_bytes(g));
     if (splits > 0) {
         launch_reduce_splits(s, w.part, (int)splits, (int64_t)g.L * ldO, g.l, rows, ldO, out, ldO);
@@ -941,11 +941,13 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
     if (bf) {
         launch_to_bf16(s, Xc, ldK, K, l, L, Xh);
         rc = launch_tc_gemm(s, h->sm_count, transpose, (const float*)A, m, n, lda, Xh, nullptr, ldK, L, Yc, nullptr,
-                            nullptr, ldM, part, transpose ? 0 : 1, &used, status, nullptr, 0, 0, 1);
+                            nullptr, ldM, part, transpose ? 0 : 1, &used, status, nullptr, 0, 0, 1,
+                            dtype == RSVDGB_BF16);
     } else {
         launch_split_tf32(s, Xc, ldK, K, l, L, Xh, Xl);
         rc = launch_tc_gemm(s, h->sm_count, transpose, (const float*)A, m, n, lda, Xh, Xl, ldK, L, Yc, nullptr,
-                            nullptr, ldM, part, transpose ? 0 : 1, &used, status, nullptr);
+                            nullptr, ldM, part, transpose ? 0 : 1, &used, status, nullptr, 0, 0, 0,
+                            dtype == RSVDGB_BF16);
     }
     if (rc) return rc;
     if (used > 0) launch_reduce_splits(s, part, (int)used, (int64_t)L * ldM, l, M, ldM, Yc, ldM);

@@ -70,7 +70,7 @@ struct TcParams {
 };
 
 // ----------------------------------------------------------------- the kernel
-template <bool TRANS, int G, bool SQ, bool BF>
+template <bool TRANS, int G, bool SQ, bool BF, bool ABF>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_pass_kernel(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapPhi,
                    const __grid_constant__ CUtensorMap tmapPlo, TcParams p)
@@ -90,12 +90,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int lane = threadIdx.x & 31;
     const int SA = p.a_stages, SP = p.p_stages;
     const int l_pad = p.l_pad;
-    const uint32_t a_tile_bytes = kTileRows * kBK * 4;         // 16 KB
+    const uint32_t a_tile_bytes = kTileRows * kBK * (ABF ? 2 : 4);  // 16 KB (8 KB for BF16 A)
     // panel tile: l_pad rows x kBK elements (TF32 hi + lo: 128 B rows each; BF16: one 64 B row)
     const uint32_t p_tile_bytes = (uint32_t)l_pad * kBK * (BF ? 2 : 4);
     const uint32_t a_stage_bytes = G * a_tile_bytes;
     const uint32_t p_stage_bytes = (BF ? 1 : 2) * p_tile_bytes;
-    constexpr uint32_t kAcols = BF ? kBK / 2 : 2 * kBK;  // TMEM columns of one converted A tile
+    // TMEM columns of one converted A tile: BF16 pairs; TF32 hi + lo; or hi
+    // alone for BF16 A, which TF32 holds exactly (a_lo = 0)
+    constexpr uint32_t kAcols = BF ? kBK / 2 : (ABF ? kBK : 2 * kBK);
     uint8_t* a_ring = smem;
     uint8_t* p_ring = smem + (size_t)SA * a_stage_bytes;
 
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
                             mma_tf32_tmemA(d, ahi + kk * 8, bhi, idesc, acc);
                             mma_tf32_tmemA(d, ahi + kk * 8, blo, idesc, 1u);
-                            mma_tf32_tmemA(d, alo + kk * 8, bhi, idesc, 1u);
+                            if (!ABF) mma_tf32_tmemA(d, alo + kk * 8, bhi, idesc, 1u);
                         }
                     }
                     mma_commit(&pempty_bar[s]);
@@ -287,6 +289,48 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int g = 0; g < G; ++g) {
                     if (g >= gv) continue;
                     const float* tile = (const float*)(st + g * a_tile_bytes);
+                    if (ABF) {
+                        // BF16 A: this warp's 16 K values as FP32 (exact: BF16 is a
+                        // prefix of FP32 and of TF32)
+                        float a16[KH];
+                        const uint16_t* tb = (const uint16_t*)tile;
+                        if (!TRANS) {
+                            // row r of a 128 x 32 tile, 64-byte rows, 64-byte swizzle:
+                            // 16-byte chunk c of row r sits at chunk (c ^ ((r >> 1) & 3));
+                            // this warp takes chunks 2hk, 2hk+1
+#pragma unroll
+                            for (int cc = 0; cc < 2; ++cc) {
+                                const int ch = 2 * hk + cc;
+                                const uint4 v = *(const uint4*)((const uint8_t*)tile + r * 64 +
+                                                                ((ch ^ ((r >> 1) & 3)) << 4));
+                                const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    a16[cc * 8 + 2 * e] = __uint_as_float(w4[e] << 16);
+                                    a16[cc * 8 + 2 * e + 1] = __uint_as_float(w4[e] & 0xFFFF0000u);
+                                }
+                            }
+                        } else {
+                            // column r of a 32 x 128 tile (rows of 256 bytes, no swizzle)
+#pragma unroll
+                            for (int kk = 0; kk < KH; ++kk)
+                                a16[kk] = __uint_as_float((uint32_t)tb[(KH * hk + kk) * kTileRows + r] << 16);
+                        }
+                        if (BF) {
+#pragma unroll
+                            for (int e = 0; e < KH / 2; ++e) {
+                                if (SQ) sq = fmaf(a16[2 * e], a16[2 * e], fmaf(a16[2 * e + 1], a16[2 * e + 1], sq));
+                                hi[g][e] = pack_bf16(a16[2 * e], a16[2 * e + 1]);  // exact
+                            }
+                        } else {
+#pragma unroll
+                            for (int kk = 0; kk < KH; ++kk) {
+                                if (SQ) sq = fmaf(a16[kk], a16[kk], sq);
+                                hi[g][kk] = __float_as_uint(a16[kk]);
+                            }
+                        }
+                        continue;
+                    }
                     if (BF) {
                         // BF16 (round to nearest) of this warp's 16 K values, packed in pairs
                         float a16[KH];
@@ -357,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     const uint32_t col = tmem + a_col0 + (uint32_t)(ts * G + g) * kAcols + (uint32_t)(KH * hk);
                     tmem_st16(col + lane_off, hi[g]);
-                    tmem_st16(col + kBK + lane_off, lo[g]);
+                    if (!ABF) tmem_st16(col + kBK + lane_off, lo[g]);
                 }
                 tmem_wait_st();
                 tmem_fence_before();
@@ -418,11 +462,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ----------------------------------------------------------------- host side
-template <bool TRANS, int G, bool BF>
+template <bool TRANS, int G, bool BF, bool ABF>
 int launch_typed(cudaStream_t s, const CUtensorMap& mA, const CUtensorMap& mhi, const CUtensorMap& mlo,
                  TcParams p, dim3 grid, size_t smem)
 {
-    auto kern = p.fro2 ? tc_pass_kernel<TRANS, G, true, BF> : tc_pass_kernel<TRANS, G, false, BF>;
+    auto kern = p.fro2 ? tc_pass_kernel<TRANS, G, true, BF, ABF> : tc_pass_kernel<TRANS, G, false, BF, ABF>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return RSVDGB_ERR_CUDA;
     kern<<<grid, kThreads, smem, s>>>(mA, mhi, mlo, p);
@@ -430,10 +474,10 @@ int launch_typed(cudaStream_t s, const CUtensorMap& mA, const CUtensorMap& mhi, 
     return cudaGetLastError() == cudaSuccess ? RSVDGB_OK : RSVDGB_ERR_CUDA;
 }
 
-int groups_for(int l_pad, bool bf)
+int groups_for(int l_pad, bool bf, bool abf = false)
 {
     // TMEM: G accumulators of l_pad columns + 2 stages x G converted A tiles <= 512
-    const int acols = bf ? kBK / 2 : 2 * kBK;
+    const int acols = bf ? kBK / 2 : (abf ? kBK : 2 * kBK);
     int g = 3;
     while (g > 1 && ((g * l_pad + 31) / 32 * 32 + kTmemStages * g * acols) > 512) --g;
     return g;
@@ -443,9 +487,8 @@ int groups_for(int l_pad, bool bf)
 
 bool tc_pass_supported(int64_t m, int64_t n, int64_t lda, int l_pad, const void* A, int a_bf16)
 {
-    if (a_bf16) return false;
     if (l_pad < 16 || l_pad > 256 || (l_pad % 16)) return false;
-    if ((lda * 4) % 16 || ((uintptr_t)A % 16)) return false;
+    if ((lda * (a_bf16 ? 2 : 4)) % 16 || ((uintptr_t)A % 16)) return false;
     if (m > 0x7fffffff || n > 0x7fffffff) return false;
     return get_encoder() != nullptr;
 }
@@ -453,11 +496,12 @@ bool tc_pass_supported(int64_t m, int64_t n, int64_t lda, int l_pad, const void*
 int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int64_t m, int64_t n, int64_t lda,
                    const float* Phi, const float* Plo, int64_t ldp, int l_pad, float* out, float* out_hi,
                    float* out_lo, int64_t ld_out, float* partial, int64_t want_splits, int64_t* splits_out,
-                   int* status, double* fro2, int out_rowmajor, int out_cols, int bf16_panel)
+                   int* status, double* fro2, int out_rowmajor, int out_cols, int bf16_panel, int a_bf16)
 {
     const bool bf = bf16_panel != 0;
-    const int G = groups_for(l_pad, bf);
-    const size_t a_stage = (size_t)G * kTileRows * kBK * 4;
+    const bool abf = a_bf16 != 0;
+    const int G = groups_for(l_pad, bf, abf);
+    const size_t a_stage = (size_t)G * kTileRows * kBK * (abf ? 2 : 4);
     const size_t p_stage = (bf ? 2 : 8) * (size_t)l_pad * kBK;
     const size_t budget = 224 * 1024;  // dynamic shared memory, 1 KB kept for alignment
     int sp = (3 * p_stage + 2 * a_stage <= budget) ? 3 : 2;
@@ -468,7 +512,15 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
     CUtensorMap mA, mhi, mlo;
     const int64_t k_total = trans ? m : n;
     bool ok;
-    if (!trans)
+    if (abf) {
+        // BF16 A: 64-byte rows of 32 K values (A side) or 256-byte rows (A^T side)
+        if (!trans)
+            ok = encode_2d(&mA, A, n, m, lda * 2, kBK, kTileRows, CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+        else
+            ok = encode_2d(&mA, A, n, m, lda * 2, kTileRows, kBK, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    } else if (!trans)
         ok = encode_2d(&mA, A, n, m, lda * 4, kBK, kTileRows, CU_TENSOR_MAP_SWIZZLE_128B);
     else
         ok = encode_2d(&mA, A, n, m, lda * 4, kTileRows, kBK, CU_TENSOR_MAP_SWIZZLE_NONE);
@@ -518,19 +570,31 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
     else
         grid = dim3((unsigned)units, (unsigned)splits);
     if (splits_out) *splits_out = direct ? 0 : splits;
-    switch ((bf ? 16 : 0) + (trans ? 8 : 0) + G) {
-        case 1: return launch_typed<false, 1, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 2: return launch_typed<false, 2, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 3: return launch_typed<false, 3, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 9: return launch_typed<true, 1, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 10: return launch_typed<true, 2, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 11: return launch_typed<true, 3, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 17: return launch_typed<false, 1, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 18: return launch_typed<false, 2, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 19: return launch_typed<false, 3, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 25: return launch_typed<true, 1, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 26: return launch_typed<true, 2, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 27: return launch_typed<true, 3, true>(s, mA, mhi, mlo, p, grid, smem);
+    switch ((abf ? 32 : 0) + (bf ? 16 : 0) + (trans ? 8 : 0) + G) {
+        case 1: return launch_typed<false, 1, false, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 2: return launch_typed<false, 2, false, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 3: return launch_typed<false, 3, false, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 9: return launch_typed<true, 1, false, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 10: return launch_typed<true, 2, false, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 11: return launch_typed<true, 3, false, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 17: return launch_typed<false, 1, true, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 18: return launch_typed<false, 2, true, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 19: return launch_typed<false, 3, true, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 25: return launch_typed<true, 1, true, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 26: return launch_typed<true, 2, true, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 27: return launch_typed<true, 3, true, false>(s, mA, mhi, mlo, p, grid, smem);
+        case 33: return launch_typed<false, 1, false, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 34: return launch_typed<false, 2, false, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 35: return launch_typed<false, 3, false, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 41: return launch_typed<true, 1, false, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 42: return launch_typed<true, 2, false, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 43: return launch_typed<true, 3, false, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 49: return launch_typed<false, 1, true, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 50: return launch_typed<false, 2, true, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 51: return launch_typed<false, 3, true, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 57: return launch_typed<true, 1, true, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 58: return launch_typed<true, 2, true, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 59: return launch_typed<true, 3, true, true>(s, mA, mhi, mlo, p, grid, smem);
         default: return RSVDGB_ERR_UNSUPPORTED;
     }
 }
@@ -539,7 +603,7 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
 int64_t tc_pass_max_splits(int64_t m, int64_t n, int l_pad, int sm_count)
 {
     // automatic split count of an A^T X launch on an m x n matrix
-    const int G = std::max(groups_for(l_pad, false), groups_for(l_pad, true));
+    const int G = std::max(std::max(groups_for(l_pad, false), groups_for(l_pad, true)), groups_for(l_pad, false, true));
     const int64_t units = ceil_div(ceil_div(n, kTileRows), G);
     int64_t splits = std::max<int64_t>(1, (int64_t)sm_count / units);
     splits = std::min<int64_t>(splits, std::max<int64_t>(1, m / (4 * kBK)));

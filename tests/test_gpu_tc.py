@@ -136,3 +136,57 @@ def test_bf16_sketch_rsvd_equal_error(rs, handle, m, n, k, p, q):
     assert err <= 1.01 * err_o, (err, err_o)
     # the device's own estimate of the rank-k error agrees with the explicit residual
     assert abs(np.sqrt(max(info.err2_k, 0.0)) - err) <= 1e-3 * np.sqrt(oracle.fro2(A)) + 1e-3 * err
+
+
+@pytest.mark.parametrize("m,n,l", [(300, 200, 30), (1030, 520, 220), (4096, 256, 100), (777, 1000, 112), (64, 640, 8)])
+@pytest.mark.parametrize("prec", ["fp32", "bf16_sketch"])
+def test_tc_passes_bf16_stored_a(rs, handle, m, n, l, prec):
+    """A stored in BF16 (Sec. 3.6 allows any numeric matrix; the C3 workload
+    stores A in BF16).  BF16 values are exact in TF32, so the FP32-accurate
+    product needs a p_hi + a p_lo only and meets the same bound,
+    (2^-19 + 2 K u32)(|A||X|); in mixed precision the BF16 panel bound holds."""
+    import torch
+    rng = np.random.default_rng(5 * m + n + l)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    Ab = inputs.bf16_bits(A)
+    Aval = inputs.bf16_to_f32(Ab).astype(np.float64)
+    A_dev = to_dev(Ab.view(np.int16)).view(torch.bfloat16)
+    X = rng.standard_normal((n, l)).astype(np.float32)
+    W = rng.standard_normal((m, l)).astype(np.float32)
+    Y = rs.rsvdgb_pass_ax(handle, A_dev, to_dev(X), engine="tc", prec=prec).cpu().numpy().astype(np.float64)
+    Z = rs.rsvdgb_pass_atx(handle, A_dev, to_dev(W), engine="tc", prec=prec).cpu().numpy().astype(np.float64)
+    Yo = oracle.gemm_ax(Ab, X.astype(np.float64))
+    Zo = oracle.gemm_atx(Ab, W.astype(np.float64))
+    c = 2.0 ** -19 if prec == "fp32" else 2.0 ** -8
+    by = (c + 2 * n * 2.0 ** -24) * (np.abs(Aval) @ np.abs(X))
+    bz = (c + 2 * m * 2.0 ** -24) * (np.abs(Aval).T @ np.abs(W))
+    assert np.all(np.abs(Y - Yo) <= by), float(np.max(np.abs(Y - Yo) / by))
+    assert np.all(np.abs(Z - Zo) <= bz), float(np.max(np.abs(Z - Zo) / bz))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16_sketch"])
+def test_tc_rsvd_bf16_stored_a(rs, handle, prec):
+    """rSVD of a BF16-stored A on the tensor cores against the oracle run on
+    the same BF16 values: FP32 tolerances for the FP32 path, equal error
+    (<= 1.01 x the oracle's) for the mixed one."""
+    import torch
+    A = inputs.planted(3000, 512, inputs.exp_spectrum(512, 0.04), seed=31)
+    Ab = inputs.bf16_bits(A)
+    A_dev = to_dev(Ab.view(np.int16)).view(torch.bfloat16)
+    k = 40
+    d_o, U_o, V_o, Q_o, B_o = oracle.rsvd(Ab, k, p=10, q=2, seed=8, return_qb=True)
+    d, U, V, info = rs.rsvdgb_rsvd(handle, A_dev, k, opts=rs.make_opts(p=10, q=2, seed=8, prec=prec))
+    torch.cuda.synchronize()
+    assert info.status == 0 and info.engine == 2
+    if prec == "fp32":
+        assert sigma_err(d.cpu().numpy(), d_o) <= 1e-5
+        sB = np.linalg.svd(B_o, compute_uv=False)
+        tol = subspace_tol(sB, k, sB[0])
+        assert sin_theta(U.cpu().numpy(), U_o) <= tol
+        assert sin_theta(V.cpu().numpy(), V_o) <= tol
+    else:
+        Aval = inputs.bf16_to_f32(Ab).astype(np.float64)
+        err_o = np.sqrt(oracle.residual_fro2(Aval, U_o, d_o, V_o))
+        err = np.sqrt(oracle.residual_fro2(Aval, U.cpu().numpy().astype(np.float64),
+                                           d.cpu().numpy().astype(np.float64), V.cpu().numpy().astype(np.float64)))
+        assert err <= 1.01 * err_o, (err, err_o)
