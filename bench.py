@@ -38,6 +38,9 @@ WORKLOADS = {
                        m=200000, n=2000, k=100, p=10, q=2, noise=1e-3),
     "spiked50k": dict(desc="rsvd 50000x2000 fp32, sigma_i=1/i + N(0,1e-3^2) noise, k=100 p=10 q=2 (profiling size)",
                       m=50000, n=2000, k=100, p=10, q=2, noise=1e-3),
+    "c3bf16": dict(desc="rsvd 100000x50000 bf16, sigma=1 (i<=200), 1e-2 beyond, + N(0,1e-4^2) noise, "
+                        "k=200 p=20 q=3", m=100000, n=50000, k=200, p=20, q=3, noise=1e-4, step=200,
+                   dtype="bf16", cpu_rows=1000),
     "planted2k": dict(desc="rsvd 2000x1000 fp32, sigma_i=exp(-i/20), k=20 p=10 q=2",
                       m=2000, n=1000, k=20, p=10, q=2, noise=0.0),
 }
@@ -166,6 +169,17 @@ def make_matrix(wl, seed, device):
     import numpy as np
     from paper_1608_02148_gb300 import inputs
     m, n = wl["m"], wl["n"]
+    if wl.get("step"):
+        # step spectrum on structured orthogonal factors, noise, stored BF16
+        import torch
+        sigma = np.where(np.arange(1, n + 1) <= wl["step"], 1.0, 1e-2)
+        A = inputs.planted_reflector(m, n, sigma, seed, device=device)
+        gen = torch.Generator(device=device)
+        gen.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+        for r0 in range(0, m, 8192):  # noise in row blocks
+            blk = A[r0:r0 + 8192]
+            blk.add_(torch.randn(blk.shape, generator=gen, device=device, dtype=torch.float32), alpha=wl["noise"])
+        return A.to(torch.bfloat16) if wl.get("dtype") == "bf16" else A
     if wl["noise"] > 0:
         sigma = 1.0 / np.arange(1, n + 1, dtype=np.float64)
         return inputs.spiked_noise(m, n, sigma, wl["noise"], seed, device=device)
@@ -328,7 +342,7 @@ def main():
     value = elapsed / (args.steps * world)
 
     passes = 2 * wl["q"] + 2
-    a_bytes = m * n * 4
+    a_bytes = m * n * (2 if A.dtype == torch.bfloat16 else 4)
     hbm = peaks["hbm_gbs"]
     roof_ms = passes * a_bytes / (hbm * 1e9) * 1e3
     pass_avg_ms = pass_ms / max(pass_n, 1)
@@ -345,7 +359,7 @@ def main():
                                  "peak_source": peak_kind}}
     else:
         traffic = None
-        if TC_PASS_TRAFFIC_PER_A_BYTE is not None and args.prec == "fp32":
+        if TC_PASS_TRAFFIC_PER_A_BYTE is not None and args.prec == "fp32" and A.dtype == torch.float32:
             traffic = TC_PASS_TRAFFIC_PER_A_BYTE * a_bytes
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                     "frac": achieved_gbs / hbm, "traffic": traffic, "peak_source": peak_kind,
@@ -353,7 +367,8 @@ def main():
                     if traffic is not None else None,
                     "kernel": "tc_pass_kernel (pass over A, tcgen05 3xTF32)",
                     "tensor_view": {"achieved_tflops_algorithmic": achieved_tflops,
-                                    "tf32_flops_issued_per_algorithmic": 3.0 * (((l + 15) // 16) * 16) / l}}
+                                    "tf32_flops_issued_per_algorithmic":
+                                        (2.0 if A.dtype == torch.bfloat16 else 3.0) * (((l + 15) // 16) * 16) / l}}
 
     # ---------------- the other precision at equal error (same A, same Omega) ----------------
     variants = {}
@@ -454,8 +469,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        rows = min(args.cpu_rows, m)
-        A_rows = A[:rows].cpu().numpy()
+        rows = min(wl.get("cpu_rows", args.cpu_rows), m)
+        if A.dtype == torch.bfloat16:  # the oracle reads BF16 bit patterns
+            A_rows = A[:rows].view(torch.int16).cpu().numpy().view(np.uint16)
+        else:
+            A_rows = A[:rows].cpu().numpy()
         t = cpu_oracle_time(A_rows, wl, 0)
         cpu = {"value": t * (m / rows) * 1e3, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
                "sample": f"oracle rsvd on rows 0..{rows - 1} of the same A ({rows}x{n}), time x{m / rows:g}"}
@@ -463,7 +481,8 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "vs_baseline": None, "dtype": "bf16-stored A, f32 arithmetic" if A.dtype == torch.bfloat16 else "f32",
+                "data": "synthetic",
                 "config": {"workload": wl["desc"], "m": m, "n": n, "k": k, "p": wl["p"], "q": wl["q"], "l": l,
                            "prec": args.prec, "engine": engine, "engine_requested": args.engine,
                            "passes_over_A": passes,
