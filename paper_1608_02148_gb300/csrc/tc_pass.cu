@@ -63,6 +63,7 @@ struct TcParams {
     float* out_lo;         // AX: TF32 lo part of Y (may be null)
     int64_t ld_out;
     int out_rowmajor;      // direct output stored row-major: out[idx * ld_out + j], j < out_cols
+    int out_vec4;          // row-major output 16-byte aligned (float4 stores)
     int out_cols;
     int64_t split_stride;  // AtX: floats between partials
     int* status;
@@ -109,8 +110,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         k_begin = (int64_t)blockIdx.y * p.k_per_split;
         k_end = min(p.k_total, k_begin + p.k_per_split);
     } else {
-        tile_begin = (int64_t)blockIdx.x * G;
-        tile_end = min(p.num_tiles, tile_begin + G);
+        // sets of G lane tiles; a grid narrower than the sets makes the CTAs
+        // persistent over a range of them
+        const int64_t units = (p.num_tiles + G - 1) / G;
+        tile_begin = units * blockIdx.x / gridDim.x * G;
+        tile_end = min(p.num_tiles, units * (blockIdx.x + 1) / gridDim.x * G);
         k_begin = (int64_t)blockIdx.y * p.k_per_split;
         k_end = min(p.k_total, k_begin + p.k_per_split);
     }
@@ -422,9 +426,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tmem_wait_ld();
                     if (idx < lim) {
                         if (p.out_rowmajor) {
+                            // a row of the output per thread: 16-byte stores when aligned
+                            float* orow = out + idx * p.ld_out + j0;
+                            if (p.out_vec4 && j0 + 16 <= p.out_cols) {
 #pragma unroll
-                            for (int e = 0; e < 16; ++e)
-                                if (j0 + e < p.out_cols) out[idx * p.ld_out + j0 + e] = __uint_as_float(v[e]);
+                                for (int e = 0; e < 4; ++e)
+                                    *(float4*)(orow + 4 * e) =
+                                        make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
+                                                    __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 16; ++e)
+                                    if (j0 + e < p.out_cols) orow[e] = __uint_as_float(v[e]);
+                            }
                         } else {
 #pragma unroll
                             for (int e = 0; e < 16; ++e) {
@@ -562,11 +576,14 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
     p.split_stride = direct ? 0 : (int64_t)l_pad * ld_out;
     p.out_rowmajor = direct ? out_rowmajor : 0;
     p.out_cols = out_cols > 0 ? out_cols : l_pad;
+    p.out_vec4 = (p.out_rowmajor && ((uintptr_t)p.out % 16) == 0 && (ld_out % 4) == 0) ? 1 : 0;
     if (out_rowmajor && !direct) return RSVDGB_ERR_INVALID_ARG;
     dim3 grid;
     if (!trans)
         grid = dim3((unsigned)std::min<int64_t>(std::max<int64_t>(sm_count / splits, 1), p.num_tiles),
                     (unsigned)splits);
+    else if (direct)
+        grid = dim3((unsigned)std::min<int64_t>(units, sm_count), 1);  // persistent over the sets
     else
         grid = dim3((unsigned)units, (unsigned)splits);
     if (splits_out) *splits_out = direct ? 0 : splits;
