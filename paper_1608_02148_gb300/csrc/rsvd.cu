@@ -532,8 +532,11 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
         launch_chol_inv(s, w.G, l, 0.f, w.R1, w.T, w.status, w.breakdowns);
         apply_At(h, g, w, false);
         times_small(s, sm, w.Wt, g.ldn, g.n, l, w.T, w.Zt, w.part);
-        // Q = qr(A^T Q): CholeskyQR2 on the n side, result in the panel
-        cholqr2(s, sm, w, w.Zt, g.ldn, g.n, l, w.Wt, w.Pt, g.use_tc ? (int)g.L : 0);
+        // Q = qr(A^T Q) on the n side: here too only the span is carried
+        // forward, so one CholeskyQR step, Q_n = Z R^{-1}, into the panel
+        gram(s, sm, w.Zt, g.ldn, g.n, l, w.part, w.G, g.use_tc ? (int)g.L : 0, w.status);
+        launch_chol_inv(s, w.G, l, 0.f, w.R1, w.T1, w.status, w.breakdowns);
+        times_small(s, sm, w.Zt, g.ldn, g.n, l, w.T1, w.Pt, w.part);
         split_panel(s, g, w);
         // Y = A Q
         apply_A(h, g, w, nullptr);

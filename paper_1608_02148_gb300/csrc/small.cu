@@ -696,13 +696,21 @@ __global__ void finalize_info_kernel(const float* __restrict__ sigma, int l, int
     const int tid = threadIdx.x;
     if (d && sigma)
         for (int i = tid; i < k; i += blockDim.x) d[i] = sigma[i];
-    if (tid == 0 && info) {
-        double sb = 0.0, sk = 0.0;
-        for (int i = 0; sigma && i < l; ++i) {
-            const double s = (double)sigma[i];
-            sb += s * s;
-            if (i < k) sk += s * s;
-        }
+    if (tid >= 32 || !info) return;
+    // sum of squares over the l (and the first k) singular values: one warp,
+    // lane-strided loads in flight together, FP64 shuffle reduction
+    double sb = 0.0, sk = 0.0;
+    for (int i = tid; sigma && i < l; i += 32) {
+        const double s = (double)sigma[i];
+        sb += s * s;
+        if (i < k) sk += s * s;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        sk += __shfl_xor_sync(0xffffffffu, sk, o);
+    }
+    if (tid == 0) {
         const double fa = fro2A ? *fro2A : 0.0;
         int st = status ? *status : 0;
         if (!isfinite(fa)) st = RSVDGB_ERR_NONFINITE;
