@@ -189,7 +189,9 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w, int L_lo = 0)
     w.sigma = c.take<float>(256);
     w.Ut = c.take<float>(L * L);
     w.Jt = c.take<float>(L * L);
-    w.jwork = c.take<float>(2 * (L + 2) * (L + 2));
+    // Jacobi columns when they do not fit in shared memory: 2 x l x Lp with the
+    // padded column stride Lp <= l rounded up to 32
+    w.jwork = c.take<float>(2 * (L + 32) * (L + 32));
     w.status = c.take<int>(1);
     w.breakdowns = c.take<int>(1);
     w.sweeps = c.take<int>(1);

@@ -128,6 +128,7 @@ def test_rsvd_small_planted_2000x1000(rs, handle):
 @pytest.mark.parametrize("m,n,k,p,q", [
     (1000, 300, 10, 5, 0), (777, 333, 20, 4, 1), (300, 1000, 12, 6, 2),  # wide matrix
     (513, 257, 100, 10, 1), (256, 250, 1, 0, 1), (400, 230, 200, 20, 1),  # l = 220
+    (600, 300, 170, 10, 1), (500, 260, 190, 10, 1),  # l = 180, 200: wide Jacobi and Cholesky
     (128, 64, 60, 10, 2),  # l clamps to min(m, n)
 ])
 def test_rsvd_ragged_shapes(rs, handle, m, n, k, p, q):
