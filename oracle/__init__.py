@@ -190,6 +190,47 @@ def rsvd(A: np.ndarray, k: int, p: int = 10, q: int = 2, sdist: str = "normal", 
     return d, U, V
 
 
+def values(A: np.ndarray) -> np.ndarray:
+    """The stored values of A promoted exactly to float64 (uint16 = BF16 bits)."""
+    if A.dtype == np.uint16:
+        return (A.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    return np.asarray(A, dtype=np.float64)
+
+
+def rpca(A: np.ndarray, k: int, center: bool = True, scale: bool = True, p: int = 10, q: int = 2,
+         sdist: str = "normal", seed: int = 0):
+    """Algorithm rpca (Sec. 4.2): principal components of the m x n data
+    matrix A (rows = observations, columns = variables).
+
+    Preprocessing of the rpca() interface (Sec. 4.4), written out in FP64:
+      centre   mu_j = (1/m) sum_i a_ij                     (center=True, else 0)
+      scale    s_j  = sqrt( sum_i (a_ij - mu_j)^2 / (m - 1) )  (scale=True, else 1)
+               -- with the centring this is the sample standard deviation, so
+               X^T X / (m - 1) is the correlation matrix; without it the root
+               mean square with the same m - 1 denominator.  A column with
+               s_j = 0 is left as the zero column (its multiplier is 0).
+      X = (A - 1 mu^T) diag(1 / s)
+    then step 1 [U, Sigma, W] = rsvd(X, k, p, q) (this module's rsvd, the same
+    test matrix), step 2 Lambda = Sigma^2 / (m - 1), step 3 Z = U Sigma.
+    Returns a dict: rotation W (n x k), eigvals Lambda (k), sdev sqrt(Lambda),
+    x Z (m x k), center mu (n), scale s (n)."""
+    Av = values(A)
+    m, n = Av.shape
+    mu = Av.mean(axis=0) if center else np.zeros(n)
+    Xc = Av - mu[None, :]
+    if scale:
+        s = np.sqrt(np.sum(Xc * Xc, axis=0) / (m - 1))
+        mult = np.where(s > 0, 1.0 / np.where(s > 0, s, 1.0), 0.0)
+    else:
+        s = np.ones(n)
+        mult = np.ones(n)
+    X = np.ascontiguousarray(Xc * mult[None, :])
+    d, U, W = rsvd(X, k, p=p, q=q, sdist=sdist, seed=seed)
+    lam = d * d / (m - 1)
+    return {"rotation": W, "eigvals": lam, "sdev": np.sqrt(lam), "x": U * d[None, :],
+            "center": mu, "scale": s, "sigma": d, "X": X}
+
+
 def power_direct(A: np.ndarray, l: int, q: int, sdist: str = "normal", seed: int = 0) -> np.ndarray:
     """Algorithm poweriter_direct: Y = (A A^T)^q A Omega (m >= n)."""
     ptr, code, m, n, lda = _amat(A)

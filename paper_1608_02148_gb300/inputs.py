@@ -198,3 +198,37 @@ def controller_spectrum(rng, k: int, count: int):
     s = int(rng.integers(max(1, k // 2), 2 * k + 1))
     d = math.exp(rng.uniform(math.log(1e-4), math.log(0.3)))
     return np.where(i <= s, 1.0, d), f"step s={s} delta={d:.3g}"
+
+
+def pca_data(m: int, n: int, rank: int, seed: int, decay: float = 0.85, noise_std: float = 0.05,
+             mean_ratio: float = 5.0, scale_range=(0.1, 10.0), device="cpu", zero_var_cols=0):
+    """Observations x variables data with heterogeneous units, as the PCA
+    examples treat them (rows = observations, columns = variables):
+
+        A = (F L^T + E) diag(c) + 1 mu^T
+
+    F (m x rank) i.i.d. N(0, 1) latent factors; L (n x rank) i.i.d. N(0, 1)
+    loadings with column j scaled by decay^j (a decaying spectrum of the
+    correlation matrix); E i.i.d. N(0, noise_std^2); c log-uniform in
+    scale_range (units); mu_j = mean_ratio * c_j * N(0, 1) (column offsets
+    several spreads away from zero).  The last ``zero_var_cols`` columns are
+    constant (zero variance).  float32 storage, built with torch on any device."""
+    import torch
+
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+    F = torch.randn(m, rank, generator=gen, device=dev, dtype=torch.float32)
+    L = torch.randn(n, rank, generator=gen, device=dev, dtype=torch.float32)
+    L *= decay ** torch.arange(rank, device=dev, dtype=torch.float32)[None, :]
+    A = torch.randn(m, n, generator=gen, device=dev, dtype=torch.float32)
+    A.mul_(noise_std)
+    A.addmm_(F, L.T)
+    del F, L
+    lo, hi = math.log(scale_range[0]), math.log(scale_range[1])
+    c = torch.exp(lo + (hi - lo) * torch.rand(n, generator=gen, device=dev, dtype=torch.float32))
+    mu = mean_ratio * c * torch.randn(n, generator=gen, device=dev, dtype=torch.float32)
+    A.mul_(c[None, :]).add_(mu[None, :])
+    if zero_var_cols > 0:
+        A[:, n - zero_var_cols:] = mu[None, n - zero_var_cols:]
+    return A.contiguous()
