@@ -163,6 +163,47 @@ int rsvdgb_rsvd_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int6
                      int nv, const rsvdgb_opts* opts, float* d, float* U, int64_t ldu, float* V, int64_t ldv,
                      rsvdgb_info* info);
 
+/*
+ * rpca(A, k, center, scale, retx, p, q) of Sec. 4.4 -- Algorithm rpca
+ * (Sec. 4.2): the k dominant principal components of the data matrix A
+ * (m observations in rows x n variables in columns).
+ *   A, m, n, lda, dtype, opts   as in rsvdgb_rsvd (device, read only; opts
+ *          NULL = defaults; opts->layout = COL_MAJOR: A stored n x m).
+ *   k      1 <= k < min(m, n).
+ *   center nonzero: subtract the column means mu_j.
+ *   scale  nonzero: divide column j by s_j = sqrt(sum_i (a_ij - mu_j)^2 / (m - 1))
+ *          (the standard deviation with `center`; without it the root mean
+ *          square with the same m - 1 denominator).  A constant column
+ *          (s_j = 0) is analysed as the zero column.
+ *   rotation  device float, n x k row-major (ldr >= k): the eigenvectors W
+ *          (NULL: not returned).
+ *   eigvals   device float[k], required: Lambda = sigma^2 / (m - 1), descending.
+ *   sdev      device float[k] or NULL: sqrt(Lambda).
+ *   x      device float, m x k row-major (ldx >= k): the principal
+ *          components Z = U Sigma = X W (NULL: not returned, retx = FALSE).
+ *   center_out, scale_out  device float[n] or NULL: mu (0 without `center`)
+ *          and s (1 without `scale`).
+ *   info   device rsvdgb_info or NULL; fro2_A is ||X||_F^2 of the centred,
+ *          scaled matrix X.
+ * The centring and scaling are applied implicitly: A is never copied or
+ * modified; each product with X is a product with A plus a rank-one
+ * correction, and the statistics cost one extra pass over A.  Eigenvectors
+ * are defined up to sign.  Returns as rsvdgb_rsvd (RSVDGB_ERR_INVALID_ARG
+ * also for eigvals NULL or a leading dimension < k).
+ */
+int rsvdgb_rpca(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k, int center,
+                int scale, const rsvdgb_opts* opts, float* rotation, int64_t ldr, float* eigvals, float* sdev,
+                float* x, int64_t ldx, float* center_out, float* scale_out, rsvdgb_info* info);
+
+/*
+ * Same as rsvdgb_rpca with HOST pointers for A and every output (staged
+ * through a device buffer owned by the handle; the call synchronises).
+ * Returns the device status (info->status) if the launches succeeded.
+ */
+int rsvdgb_rpca_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k,
+                     int center, int scale, const rsvdgb_opts* opts, float* rotation, int64_t ldr, float* eigvals,
+                     float* sdev, float* x, int64_t ldx, float* center_out, float* scale_out, rsvdgb_info* info);
+
 /* One matrix of a batch: device pointer to A (m x n row-major, lda >= n). */
 typedef struct rsvdgb_matrix_desc {
     const void* A;

@@ -132,11 +132,14 @@ bool tc_pass_supported(int64_t m, int64_t n, int64_t lda, int l_pad, const void*
 // leading dimension ldp elements; Plo unused), one MMA per K step.  With
 // a_bf16, A (passed through the float pointer) holds BF16 values: exact in
 // TF32, so the FP32-accurate product needs two MMAs (a p_hi + a p_lo).
+// chunk_stages > 0 bounds each tensor-memory accumulation chain to that many
+// 32-wide K stages; the chunks are summed in the output in FP32 (the tensor
+// core's accumulation truncates, which biases long sums toward zero).
 int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int64_t m, int64_t n, int64_t lda,
                    const float* Phi, const float* Plo, int64_t ldp, int l_pad, float* out, float* out_hi,
                    float* out_lo, int64_t ld_out, float* partial, int64_t want_splits, int64_t* splits_out,
                    int* status, double* fro2, int out_rowmajor = 0, int out_cols = 0, int bf16_panel = 0,
-                   int a_bf16 = 0);
+                   int a_bf16 = 0, int chunk_stages = 0);
 int64_t tc_pass_max_splits(int64_t m, int64_t n, int l_pad, int sm_count);
 int64_t tc_split_count(int64_t k_total, int64_t units, int sm_count);
 // l x l row-major T -> column-major L x L TF32 hi/lo panel (zero padded),
@@ -188,6 +191,34 @@ void launch_colmajor_to_rowmajor(cudaStream_t s, const float* in, int64_t ld, in
                                  int64_t ldo);
 void launch_rowmajor_to_colmajor(cudaStream_t s, const float* in, int64_t ldi, int64_t rows, int cols, int cols_pad,
                                  float* out, int64_t ld);
+
+// Randomized PCA (pca.cu): implicit centring / scaling of the data matrix.
+// Per-variable statistics in one pass over the stored matrix S (rows_s x
+// cols_s, lda): the variables are the columns of S (vars_are_cols) or its
+// rows.  Writes mu (centre or 0), cmul (1 / scale, 0 for a constant
+// variable, or 1), the optional user copies, and ||X||_F^2 of the analysed
+// matrix to *fro2.  part holds stats_chunks(...) x nvar double2.
+int64_t stats_chunks(bool vars_are_cols, int64_t rows_s, int64_t cols_s, int sm_count);
+void launch_var_stats(cudaStream_t s, int sm_count, const void* S, int64_t lda, int64_t rows_s, int64_t cols_s,
+                      int a_bf16, bool vars_are_cols, int center, int scale, double2* part, float* mu, float* cmul,
+                      float* center_out, float* scale_out, double* fro2_part, double* fro2);
+// part[c * l + j] (c < *chunks_out <= kAffineMaxChunks): partial sums of
+// sum_i X_ij w_i over row chunks (w null: 1); X column-major rows x l (ld).
+constexpr int kAffineMaxChunks = 64;
+void launch_affine_dot(cudaStream_t s, int sm_count, const float* X, int64_t ld, int64_t rows, int l, const float* w,
+                       double* part, int* chunks_out);
+// out_ij = r_i (out_ij - u_i h_j), h_j = sum of the chunk partials of
+// column j (part null: no shift; u, r null: 1); optional TF32 split.
+void launch_affine_post(cudaStream_t s, float* out, int64_t ld, int64_t rows, int l, const float* r, const float* u,
+                        const double* part, int chunks, float* hi, float* lo);
+// out_ij = r_i in_ij (column-major; in == out allowed), optional TF32 split;
+// zero over the padding (rows up to ld, columns up to l_pad).
+void launch_scale_rows(cudaStream_t s, const float* in, int64_t ld, int64_t rows, int l, int l_pad, const float* r,
+                       float* out, float* hi, float* lo);
+// T[i * l + c] *= sigma[c] for c < ncols (l x l row-major).
+void launch_scale_cols_small(cudaStream_t s, float* T, int l, int ncols, const float* sigma);
+// eig = sigma^2 / (m_obs - 1), sdev = sigma / sqrt(m_obs - 1) (first k).
+void launch_pca_values(cudaStream_t s, const float* sigma, int k, int64_t m_obs, float* eig, float* sdev);
 
 // Batched rSVD (batched.cu): plan cache owned by the handle.
 struct BatchedPlan;

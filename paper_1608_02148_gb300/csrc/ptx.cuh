@@ -162,6 +162,15 @@ __device__ __forceinline__ void mma_tf32_tmemA(uint32_t d_tmem, uint32_t a_tmem,
         : "memory");
 }
 
+// Reduction of four consecutive floats in global memory (round to nearest);
+// 16-byte aligned address; no value is returned.
+__device__ __forceinline__ void red_add_v4(float* ptr, float4 v)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(ptr), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))

@@ -67,6 +67,10 @@ struct rsvdgb_handle {
 namespace {
 
 constexpr int kMaxL = 224;  // widest sketch the one-CTA l x l kernels hold in shared memory
+// Tensor-core accumulation chains of the products whose scale matters (the
+// projection B = Q^T A, Grams on the pass kernel, the C-ABI products) are cut
+// every kExactChunk K stages of 32 (the accumulator truncates; see tc_pass.cu).
+constexpr int kExactChunk = 16;
 
 // Bump allocator over the handle's workspace (256-byte aligned pieces).
 struct Carve {
@@ -83,6 +87,18 @@ struct Carve {
     }
 };
 
+// Implicit centring / scaling of the logical matrix (randomized PCA): the
+// analysed matrix is X = (A - 1 mu^T) diag(c) when the variables are the
+// logical columns, X = diag(c) (A - mu 1^T) when they are the logical rows
+// (the data matrix had fewer observations than variables).  mu null: no
+// centring; c null: no scaling.  part: partial sums of the correction vector.
+struct Affine {
+    bool rows;
+    const float* mu;
+    const float* c;
+    double* part;
+};
+
 // Problem geometry after the m >= n normalisation.  The logical matrix is
 // either the stored row-major matrix S or its transpose.
 struct Geom {
@@ -97,6 +113,8 @@ struct Geom {
     bool use_tc;   // passes over A on the tensor cores
     bool bf16;     // sketch and power passes in BF16 (mixed precision)
     int64_t ldm, ldn;
+    const Affine* aff = nullptr;  // randomized PCA: products with X instead of A
+    int64_t pca_nvar = 0;         // randomized PCA: number of variables (0: plain rSVD)
     // stored matrix dimensions (rows x cols of the row-major S)
     int64_t sm() const { return trans ? n : m; }
     int64_t sn() const { return trans ? m : n; }
@@ -111,6 +129,11 @@ struct Work {
     float *T1, *T2, *T, *R1, *R2, *RB, *M, *sigma, *Ut, *Jt, *jwork;
     int *status, *breakdowns, *sweeps;
     double* fro2;
+    // randomized PCA: centre and multiplier per variable, statistics and
+    // correction partial sums
+    float *mu, *cmul;
+    double2* spart;
+    double *hpart, *fpart;
 };
 
 int splits_for(int64_t tiles, int64_t K, int sm_count)
@@ -196,6 +219,18 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w, int L_lo = 0)
     w.breakdowns = c.take<int>(1);
     w.sweeps = c.take<int>(1);
     w.fro2 = c.take<double>(1);
+    w.mu = w.cmul = nullptr;
+    w.spart = nullptr;
+    w.hpart = w.fpart = nullptr;
+    if (g.pca_nvar > 0) {
+        const bool vars_are_cols = (g.swap_uv == g.trans);
+        const int64_t chunks = stats_chunks(vars_are_cols, g.sm(), g.sn(), sm_count);
+        w.mu = c.take<float>(g.pca_nvar);
+        w.cmul = c.take<float>(g.pca_nvar);
+        w.spart = c.take<double2>(chunks * g.pca_nvar);
+        w.hpart = c.take<double>((size_t)kAffineMaxChunks * L);
+        w.fpart = c.take<double>(ceil_div(g.pca_nvar, 256));
+    }
 }
 
 int ensure_workspace(rsvdgb_handle* h, size_t bytes)
@@ -287,7 +322,8 @@ double a_bytes(const Geom& g) { return (double)g.m * (double)g.n * (g.a_bf16 ? 2
 // parts (tensor-core engine).  out is column-major (rows x l, ldO); when
 // out_h/out_l are given (tensor-core engine) they receive its TF32 split.
 void pass_over_A(rsvdgb_handle* h, const Geom& g, Work& w, bool A_side, const float* P, const float* Ph,
-                 const float* Pl, float* out, float* out_h, float* out_l, double* fro2, const void* Pbf = nullptr)
+                 const float* Pl, float* out, float* out_h, float* out_l, double* fro2, const void* Pbf = nullptr,
+                 int chunk = 0)
 {
     const cudaStream_t s = h->stream;
     const int64_t rows = A_side ? g.m : g.n;
@@ -309,10 +345,11 @@ void pass_over_A(rsvdgb_handle* h, const Geom& g, Work& w, bool A_side, const fl
     if (Pbf)
         launch_tc_gemm(s, h->sm_count, stored_atx, (const float*)g.A, g.sm(), g.sn(), g.lda, (const float*)Pbf,
                        nullptr, ldP, g.L, out, out_h, out_l, ldO, w.part, stored_atx ? 0 : 1, &splits, w.status, fro2,
-                       0, 0, 1, g.a_bf16);
+                       0, 0, 1, g.a_bf16, chunk);
     else
         launch_tc_gemm(s, h->sm_count, stored_atx, (const float*)g.A, g.sm(), g.sn(), g.lda, Ph, Pl, ldP, g.L, out,
-                       out_h, out_l, ldO, w.part, stored_atx ? 0 : 1, &splits, w.status, fro2, 0, 0, 0, g.a_bf16);
+                       out_h, out_l, ldO, w.part, stored_atx ? 0 : 1, &splits, w.status, fro2, 0, 0, 0, g.a_bf16,
+                       chunk);
     prof_mark(h, false, a_bytes(g));
     if (splits > 0) {
         launch_reduce_splits(s, w.part, (int)splits, (int64_t)g.L * ldO, g.l, rows, ldO, out, ldO);
@@ -335,7 +372,7 @@ void tc_gram(rsvdgb_handle* h, const Geom& g, Work& w, const float* Xt, const fl
     }
     int64_t splits = 0;
     launch_tc_gemm(h->stream, h->sm_count, false, Xt, g.L, rows, ld, Xh, Xl, ld, g.L, nullptr, nullptr, nullptr, g.L,
-                   w.part, 0, &splits, w.status, nullptr);
+                   w.part, 0, &splits, w.status, nullptr, 0, 0, 0, 0, kExactChunk);
     launch_reduce_splits(h->stream, w.part, (int)splits, (int64_t)g.L * g.L, g.l, g.l, g.L, w.G, g.l);
 }
 
@@ -352,28 +389,70 @@ void tc_times_small(rsvdgb_handle* h, const Geom& g, Work& w, const float* Xt, i
 
 // Y = A_logical X with X = Pt (n x l) -> Yt (m x l) [+ TF32 split of Y].
 // In mixed precision the product runs in BF16 on the BF16 copy of the panel.
+// With an affine map (randomized PCA) the result is Y = X_pca Pt: the panel
+// was already scaled by split_panel when the variables are the columns;
+// here the correction Y = r (A P - u h^T) follows the pass, with
+// h = P^T mu (columns: u = 1, r = 1) or h = P^T 1 (rows: u = mu, r = c).
 void apply_A(rsvdgb_handle* h, const Geom& g, Work& w, double* fro2)
 {
-    pass_over_A(h, g, w, true, w.Pt, w.Pth, w.Ptl, w.Yt, w.Yth, w.Ytl, fro2, g.bf16 ? w.Ptb : nullptr);
+    const Affine* af = g.aff;
+    int chunks = 0;
+    if (af && af->mu)
+        launch_affine_dot(h->stream, h->sm_count, w.Pt, g.ldn, g.n, g.l, af->rows ? nullptr : af->mu, af->part,
+                          &chunks);
+    pass_over_A(h, g, w, true, w.Pt, w.Pth, w.Ptl, w.Yt, w.Yth, w.Ytl, af ? nullptr : fro2,
+                g.bf16 ? w.Ptb : nullptr);
+    if (af && (af->mu || (af->rows && af->c)))
+        launch_affine_post(h->stream, w.Yt, g.ldm, g.m, g.l, af->rows ? af->c : nullptr,
+                           af->rows ? af->mu : nullptr, af->mu ? af->part : nullptr, chunks,
+                           g.use_tc ? w.Yth : nullptr, g.use_tc ? w.Ytl : nullptr);
 }
 
 // W = A_logical^T Y with Y = Yt (m x l) -> Wt (n x l).  `accurate` keeps the
 // FP32-accurate 3xTF32 product (the projection B = Q^T A); otherwise mixed
-// precision runs it in BF16.
+// precision runs it in BF16.  With an affine map: W = X_pca^T Y, i.e.
+// W = c (A^T Y - mu h^T) with h = Y^T 1 (variables = columns), or
+// W = A^T (c Y) - 1 h^T with h = (c Y)^T mu (rows; c Y staged in Qt).
 void apply_At(rsvdgb_handle* h, const Geom& g, Work& w, bool accurate)
 {
-    if (g.bf16 && !accurate) {
-        launch_to_bf16(h->stream, w.Yt, g.ldm, g.m, g.l, g.L, w.Ytb);
-        pass_over_A(h, g, w, false, w.Yt, nullptr, nullptr, w.Wt, nullptr, nullptr, nullptr, w.Ytb);
-        return;
+    const Affine* af = g.aff;
+    const cudaStream_t s = h->stream;
+    const bool mixed = g.bf16 && !accurate;
+    const float *Y = w.Yt, *Yh = w.Yth, *Yl = w.Ytl;
+    if (af && af->rows && af->c) {
+        const bool want_split = g.use_tc && !mixed;
+        launch_scale_rows(s, w.Yt, g.ldm, g.m, g.l, g.L, af->c, w.Qt, want_split ? w.Qth : nullptr,
+                          want_split ? w.Qtl : nullptr);
+        Y = w.Qt;
+        Yh = w.Qth;
+        Yl = w.Qtl;
     }
-    pass_over_A(h, g, w, false, w.Yt, w.Yth, w.Ytl, w.Wt, nullptr, nullptr, nullptr);
+    int chunks = 0;
+    if (af && af->mu)
+        launch_affine_dot(s, h->sm_count, Y, g.ldm, g.m, g.l, af->rows ? af->mu : nullptr, af->part, &chunks);
+    if (mixed) {
+        launch_to_bf16(s, Y, g.ldm, g.m, g.l, g.L, w.Ytb);
+        pass_over_A(h, g, w, false, Y, nullptr, nullptr, w.Wt, nullptr, nullptr, nullptr, w.Ytb);
+    } else {
+        // the projection B = Q^T A (accurate) keeps its scale: short accumulation chains
+    pass_over_A(h, g, w, false, Y, Yh, Yl, w.Wt, nullptr, nullptr, nullptr, nullptr, accurate ? kExactChunk : 0);
+    }
+    if (af && (af->mu || (!af->rows && af->c)))
+        launch_affine_post(s, w.Wt, g.ldn, g.n, g.l, af->rows ? nullptr : af->c, af->rows ? nullptr : af->mu,
+                           af->mu ? af->part : nullptr, chunks, nullptr, nullptr);
 }
 
 // After the panel Pt changed: its TF32 split (or BF16 copy) for the
-// tensor-core engine.
+// tensor-core engine.  With an affine map whose variables are the logical
+// columns, the panel is first scaled by the multipliers (P <- diag(c) P).
 void split_panel(cudaStream_t s, const Geom& g, Work& w)
 {
+    if (g.aff && !g.aff->rows && g.aff->c) {
+        const bool tf = g.use_tc && !g.bf16;
+        launch_scale_rows(s, w.Pt, g.ldn, g.n, g.l, g.L, g.aff->c, w.Pt, tf ? w.Pth : nullptr, tf ? w.Ptl : nullptr);
+        if (g.bf16) launch_to_bf16(s, w.Pt, g.ldn, g.n, g.l, g.L, w.Ptb);
+        return;
+    }
     if (g.bf16)
         launch_to_bf16(s, w.Pt, g.ldn, g.n, g.l, g.L, w.Ptb);
     else if (g.use_tc)
@@ -449,6 +528,17 @@ struct Outputs {
     float* Brow;  // optional row-major B (l x n) for rqb
     int64_t ldb;
     rsvdgb_info* info;
+    int sigma_cols;  // 1: columns of the logical U scaled by sigma; 2: of V (PCA scores)
+};
+
+// Randomized PCA on top of the rSVD (Algorithm rpca): centring / scaling
+// flags, the user's optional copies of the centre and scale, the eigenvalue
+// and standard-deviation outputs, and the number of observations.
+struct PcaSpec {
+    int center, scale;
+    float *center_out, *scale_out;
+    float *eig, *sdev;
+    int64_t m_obs;
 };
 
 // Algorithm rqb (+ rSVD when d != nullptr) on the logical matrix.
@@ -484,7 +574,7 @@ void sketch_features(rsvdgb_handle* h, const Geom& g, Work& w, int k, int p_max,
 }
 
 int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, const Outputs& o,
-             const Learned* lc = nullptr)
+             const Learned* lc = nullptr, const PcaSpec* pca = nullptr)
 {
     const cudaStream_t s = h->stream;
     const int sm = h->sm_count;
@@ -498,6 +588,19 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
     carve_work(c, g, sm, w, L_lo);
 
     launch_clear_scalars(s, w.status, w.breakdowns, w.fro2);
+    Affine aff{};
+    if (pca) {
+        // randomized PCA: per-variable centre and scale in one pass over A;
+        // every later product with A becomes a product with the centred,
+        // scaled X (||X||_F^2 comes from the statistics)
+        launch_var_stats(s, sm, g.A, g.lda, g.sm(), g.sn(), g.a_bf16, g.swap_uv == g.trans, pca->center,
+                         pca->scale, w.spart, w.mu, w.cmul, pca->center_out, pca->scale_out, w.fpart, w.fro2);
+        aff.rows = g.swap_uv;
+        aff.mu = pca->center ? w.mu : nullptr;
+        aff.c = pca->scale ? w.cmul : nullptr;
+        aff.part = w.hpart;
+        g.aff = &aff;
+    }
     // steps 2-3: Omega (n x l) into the panel, Y = A Omega with ||A||_F^2, Gram
     sketch(h, g, w, sdist, seed);
     if (lc) {
@@ -579,6 +682,10 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
         cross_gram(s, sm, w.Pt, w.Wt, g.ldn, g.n, l, w.part, w.G, g.use_tc ? (int)g.L : 0, w.status);
         launch_small_transpose(s, w.G, w.M, l);
         launch_jacobi_svd(s, w.M, l, w.sigma, w.Ut, w.Jt, w.jwork, w.sweeps, o.nV);
+        // principal component scores Z = U Sigma (Algorithm rpca step 3):
+        // scale the small factor before the back-projection
+        if (o.sigma_cols == 1) launch_scale_cols_small(s, w.Ut, l, o.nU, w.sigma);
+        if (o.sigma_cols == 2) launch_scale_cols_small(s, w.Jt, l, o.nV, w.sigma);
         // U = Q Ut (Eq. UQU) and V = Q_B J, truncated
         if (o.nU > 0) {
             if (g.use_tc) {
@@ -600,6 +707,8 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
     }
     launch_finalize_info(s, o.d ? w.sigma : nullptr, o.d ? l : 0, k, o.d, w.fro2, w.status, w.breakdowns, q,
                          l - k, g.use_tc ? RSVDGB_ENGINE_TC : RSVDGB_ENGINE_SIMT, o.d ? w.sweeps : nullptr, o.info);
+    // Lambda = Sigma^2 / (m - 1) over the singular values just copied to d
+    if (pca) launch_pca_values(s, w.sigma, k, pca->m_obs, pca->eig, pca->sdev);
     RSVDGB_CUDA_TRY(cudaGetLastError());
     return RSVDGB_OK;
 }
@@ -817,6 +926,30 @@ int rsvdgb_rqb(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t ld
     return run_fp32(h, g, k, o.q, o.sdist, o.seed, out);
 }
 
+}  // extern "C"
+
+namespace {
+// Device staging buffer of the *_host entry points (grows on demand).
+int ensure_host_stage(rsvdgb_handle* h, size_t bytes)
+{
+    if (bytes <= h->host_stage_bytes) return RSVDGB_OK;
+    if (h->host_stage) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->host_stage);
+        h->host_stage = nullptr;
+        h->host_stage_bytes = 0;
+    }
+    if (cudaMalloc(&h->host_stage, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return RSVDGB_ERR_NOMEM;
+    }
+    h->host_stage_bytes = bytes;
+    return RSVDGB_OK;
+}
+}  // namespace
+
+extern "C" {
+
 int rsvdgb_rsvd_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k, int nu,
                      int nv, const rsvdgb_opts* opts, float* d, float* U, int64_t ldu, float* V, int64_t ldv,
                      rsvdgb_info* info)
@@ -849,19 +982,8 @@ int rsvdgb_rsvd_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int6
     const size_t oU = take((size_t)m * std::max(nu, 1) * sizeof(float));
     const size_t oV = take((size_t)n * std::max(nv, 1) * sizeof(float));
     const size_t oI = take(sizeof(rsvdgb_info));
-    if (off > h->host_stage_bytes) {
-        if (h->host_stage) {
-            cudaStreamSynchronize(h->stream);
-            cudaFree(h->host_stage);
-            h->host_stage = nullptr;
-            h->host_stage_bytes = 0;
-        }
-        if (cudaMalloc(&h->host_stage, off) != cudaSuccess) {
-            cudaGetLastError();
-            return RSVDGB_ERR_NOMEM;
-        }
-        h->host_stage_bytes = off;
-    }
+    rc = ensure_host_stage(h, off);
+    if (rc) return rc;
     char* base = (char*)h->host_stage;
     RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(base + oA, cols_s * esz, A, lda * esz, cols_s * esz, rows_s,
                                       cudaMemcpyHostToDevice, h->stream));
@@ -879,6 +1001,111 @@ int rsvdgb_rsvd_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int6
     rsvdgb_info hinfo;
     RSVDGB_CUDA_TRY(cudaMemcpyAsync(&hinfo, base + oI, sizeof(hinfo), cudaMemcpyDeviceToHost, h->stream));
     RSVDGB_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (info) *info = hinfo;
+    return hinfo.status;
+}
+
+int rsvdgb_rpca(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k, int center,
+                int scale, const rsvdgb_opts* opts, float* rotation, int64_t ldr, float* eigvals, float* sdev,
+                float* x, int64_t ldx, float* center_out, float* scale_out, rsvdgb_info* info)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    rsvdgb_opts o;
+    if (opts)
+        o = *opts;
+    else
+        rsvdgb_default_opts(&o);
+    if (o.q < 0 || o.sdist < 0 || o.sdist > 2) return RSVDGB_ERR_INVALID_ARG;
+    if (o.q_mode != RSVDGB_Q_FIXED && o.q_mode != RSVDGB_Q_LEARNED) return RSVDGB_ERR_INVALID_ARG;
+    if (o.q_mode == RSVDGB_Q_LEARNED && (o.p_max < 2 || o.q_max < 0)) return RSVDGB_ERR_INVALID_ARG;
+    const bool learned = o.q_mode == RSVDGB_Q_LEARNED && h->ctl_params != nullptr;
+    Geom g{};
+    rc = make_geom(A, m, n, lda, dtype, o.layout, k, learned ? o.p_max : o.p, o.engine, o.prec, g);
+    if (rc) return rc;
+    if (!eigvals) return RSVDGB_ERR_INVALID_ARG;
+    if (rotation && ldr < k) return RSVDGB_ERR_INVALID_ARG;
+    if (x && ldx < k) return RSVDGB_ERR_INVALID_ARG;
+    g.pca_nvar = n;
+    const int nx = x ? k : 0, nr = rotation ? k : 0;
+    Outputs out{};
+    out.d = eigvals;
+    out.info = info;
+    if (!g.swap_uv) {
+        out.U = x; out.ldU = ldx; out.nU = nx;
+        out.V = rotation; out.ldV = ldr; out.nV = nr;
+        out.sigma_cols = x ? 1 : 0;
+    } else {
+        out.U = rotation; out.ldU = ldr; out.nU = nr;
+        out.V = x; out.ldV = ldx; out.nV = nx;
+        out.sigma_cols = x ? 2 : 0;
+    }
+    PcaSpec pc{center ? 1 : 0, scale ? 1 : 0, center_out, scale_out, eigvals, sdev, m};
+    if (learned) {
+        const Learned lc{k, o.p_max, o.q_max, nullptr};
+        return run_fp32(h, g, k, o.q, o.sdist, o.seed, out, &lc, &pc);
+    }
+    return run_fp32(h, g, k, o.q, o.sdist, o.seed, out, nullptr, &pc);
+}
+
+int rsvdgb_rpca_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k,
+                     int center, int scale, const rsvdgb_opts* opts, float* rotation, int64_t ldr, float* eigvals,
+                     float* sdev, float* x, int64_t ldx, float* center_out, float* scale_out, rsvdgb_info* info)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!A || !eigvals || m < 1 || n < 1 || k < 1) return RSVDGB_ERR_INVALID_ARG;
+    if ((rotation && ldr < k) || (x && ldx < k)) return RSVDGB_ERR_INVALID_ARG;
+    rsvdgb_opts o;
+    if (opts)
+        o = *opts;
+    else
+        rsvdgb_default_opts(&o);
+    const size_t esz = dtype == RSVDGB_BF16 ? 2 : 4;
+    const int64_t rows_s = o.layout == RSVDGB_ROW_MAJOR ? m : n;
+    const int64_t cols_s = o.layout == RSVDGB_ROW_MAJOR ? n : m;
+    if (lda < cols_s) return RSVDGB_ERR_INVALID_ARG;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (size_t)round_up((int64_t)off, 256);
+        size_t at = off;
+        off += bytes;
+        return at;
+    };
+    const size_t oA = take((size_t)rows_s * cols_s * esz);
+    const size_t oE = take((size_t)k * sizeof(float));
+    const size_t oS = take((size_t)k * sizeof(float));
+    const size_t oR = take((size_t)n * k * sizeof(float));
+    const size_t oX = take((size_t)m * k * sizeof(float));
+    const size_t oC = take((size_t)n * sizeof(float));
+    const size_t oSc = take((size_t)n * sizeof(float));
+    const size_t oI = take(sizeof(rsvdgb_info));
+    rc = ensure_host_stage(h, off);
+    if (rc) return rc;
+    char* base = (char*)h->host_stage;
+    auto dev = [&](size_t o_) { return (float*)(base + o_); };
+    RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(base + oA, cols_s * esz, A, lda * esz, cols_s * esz, rows_s,
+                                      cudaMemcpyHostToDevice, h->stream));
+    rc = rsvdgb_rpca(h, base + oA, m, n, cols_s, dtype, k, center, scale, &o, rotation ? dev(oR) : nullptr, k,
+                     dev(oE), sdev ? dev(oS) : nullptr, x ? dev(oX) : nullptr, k,
+                     center_out ? dev(oC) : nullptr, scale_out ? dev(oSc) : nullptr, (rsvdgb_info*)(base + oI));
+    if (rc) return rc;
+    const cudaStream_t s = h->stream;
+    RSVDGB_CUDA_TRY(cudaMemcpyAsync(eigvals, dev(oE), (size_t)k * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (sdev) RSVDGB_CUDA_TRY(cudaMemcpyAsync(sdev, dev(oS), (size_t)k * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (rotation)
+        RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(rotation, ldr * sizeof(float), dev(oR), k * sizeof(float),
+                                          k * sizeof(float), n, cudaMemcpyDeviceToHost, s));
+    if (x)
+        RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(x, ldx * sizeof(float), dev(oX), k * sizeof(float), k * sizeof(float), m,
+                                          cudaMemcpyDeviceToHost, s));
+    if (center_out)
+        RSVDGB_CUDA_TRY(cudaMemcpyAsync(center_out, dev(oC), (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (scale_out)
+        RSVDGB_CUDA_TRY(cudaMemcpyAsync(scale_out, dev(oSc), (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    rsvdgb_info hinfo;
+    RSVDGB_CUDA_TRY(cudaMemcpyAsync(&hinfo, base + oI, sizeof(hinfo), cudaMemcpyDeviceToHost, s));
+    RSVDGB_CUDA_TRY(cudaStreamSynchronize(s));
     if (info) *info = hinfo;
     return hinfo.status;
 }
@@ -952,7 +1179,7 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
         launch_split_tf32(s, Xc, ldK, K, l, L, Xh, Xl);
         rc = launch_tc_gemm(s, h->sm_count, transpose, (const float*)A, m, n, lda, Xh, Xl, ldK, L, Yc, nullptr,
                             nullptr, ldM, part, transpose ? 0 : 1, &used, status, nullptr, 0, 0, 0,
-                            dtype == RSVDGB_BF16);
+                            dtype == RSVDGB_BF16, kExactChunk);
     }
     if (rc) return rc;
     if (used > 0) launch_reduce_splits(s, part, (int)used, (int64_t)L * ldM, l, M, ldM, Yc, ldM);

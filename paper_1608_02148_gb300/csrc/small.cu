@@ -425,9 +425,12 @@ __device__ __forceinline__ float warp_sum(float v)
 
 // The right singular vectors J are needed for kv columns only.  The sweeps
 // first run on M alone (half the shared-memory traffic); when the spectrum
-// allows it, J_c = M^T U_c / sigma_c for the kv leading columns (its error is
-// about u32 sigma_1 / sigma_c, accepted while sigma_kv >= 1e-3 sigma_1).
-// Otherwise the sweeps are repeated from the original M with J accumulated.
+// allows it, J_c = M^T U_c / sigma_c for the kv leading columns.  The
+// converged columns of W are orthogonal only to the stopping tolerance tol
+// (relative), and M^T u_c picks up tol sigma_a / sigma_c of every column a
+// with a larger sigma_a, so that route is taken while
+// tol sigma_1 / sigma_kv <= 2e-5.  Otherwise the sweeps are repeated from the
+// original M with J accumulated (orthogonal to rounding whatever the spectrum).
 //
 // MODE 0: columns in the global work buffer; 1: columns in shared memory;
 // 2: also a staged copy of M (rows padded to a multiple of 4); 3: the columns
@@ -664,7 +667,7 @@ __global__ void __launch_bounds__(NT, 1)
         if (tid == 0 && !accj) {
             const float s1 = sv[col_of_rank[0]];
             const float skv = kv > 0 ? sv[col_of_rank[min(kv, l) - 1]] : s1;
-            need_j = (kv > 0 && !(skv >= 1e-3f * s1)) ? 1 : 0;  // stays set after the J pass
+            need_j = (kv > 0 && !(skv * 2e-5f >= tol * s1)) ? 1 : 0;  // stays set after the J pass
         }
         __syncthreads();
         if (!need_j || accj) break;

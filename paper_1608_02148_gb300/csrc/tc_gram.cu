@@ -14,8 +14,14 @@
 // exact FP32 remainder), and the MMA warp issues x_hi z_hi + x_hi z_lo +
 // x_lo z_hi per K step of 8, accumulating in FP32 in tensor memory; each
 // product is within 2^-19 |x||z| (the same split and bound as the passes
-// over A).  Every CTA takes a range of rows and writes its l x l partial; the
-// partials are summed by the split reduction.
+// over A).  The tensor core's FP32 accumulation does not round to nearest:
+// each accumulate step drops the low bits toward zero, so a long chain of
+// accumulations shrinks a sum of positive terms (a Gram diagonal) by a
+// relative bias that grows with the chain (about 5e-5 after 500 MMAs).  So
+// every 32-row stage accumulates into a fresh tensor-memory accumulator (four
+// in rotation), and the epilogue warps add it into FP32 registers (round to
+// nearest) two stages later, while the tensor core runs the next ones.  Every CTA takes a range of rows and
+// writes its l x l partial; the partials are summed by the split reduction.
 //
 // Roles (192 threads): warp 0 issues the TMA loads, warp 1 allocates tensor
 // memory and issues the MMAs, warps 2..5 convert and run the epilogue.  All
@@ -56,7 +62,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     // stage: X tile (FP32, converted in place to x_hi), x_lo [, Z tile, z_lo]
     constexpr uint32_t kStage = (CROSS ? 4 : 2) * kTile;
     __shared__ uint64_t full_bar[kMaxStages], conv_bar[kMaxStages], empty_bar[kMaxStages];
-    __shared__ uint64_t acc_bar;
+    constexpr int kAcc = 4;  // accumulators in rotation
+    constexpr int kLag = 2;  // stage c is drained after stage c + kLag is converted
+    __shared__ uint64_t acc_bar, accf_bar[kAcc], acce_bar[kAcc];
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_flag;
 
@@ -67,7 +75,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t k_end = min(p.rows, k_begin + p.k_per_cta);
     const int64_t nk = (k_end > k_begin) ? (k_end - k_begin + kBK - 1) / kBK : 0;
     const uint32_t load_bytes = (uint32_t)l_pad * kBK * 4;  // one TMA box: l_pad rows of 128 B
-    constexpr uint32_t kTmemCols = 128;
+    constexpr uint32_t kTmemCols = 512;  // four accumulators of 128 columns
 
     // rows l_pad..127 of every tile stay zero (TMA and the converters only
     // touch rows < l_pad)
@@ -83,6 +91,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&acc_bar, 1);
+        for (int a = 0; a < kAcc; ++a) {
+            mbar_init(&accf_bar[a], 1);
+            mbar_init(&acce_bar[a], kConvWarps);
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -133,20 +145,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int64_t c = 0; c < nk; ++c) {
                 const int s = (int)(c % S);
                 const uint32_t ph = (uint32_t)((c / S) & 1);
+                const int a = (int)(c % kAcc);  // accumulator of this stage
+                // accumulator a was last used by stage c - kAcc: wait until it is drained
+                if (c >= kAcc && !(ok = mbar_wait(&acce_bar[a], (uint32_t)((c / kAcc - 1) & 1), &abort_flag,
+                                                  p.status)))
+                    break;
                 if (!(ok = mbar_wait(&conv_bar[s], ph, &abort_flag, p.status))) break;
                 tmem_fence_after();
+                const uint32_t d = tmem + (uint32_t)(a * kRows);
                 const uint32_t xhi = smem_u32(smem + (size_t)s * kStage);
                 const uint32_t xlo = xhi + kTile;
                 const uint32_t zhi = CROSS ? xhi + 2 * kTile : xhi;
                 const uint32_t zlo = CROSS ? zhi + kTile : xlo;
 #pragma unroll
                 for (int kk = 0; kk < kBK / 8; ++kk) {
-                    const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
-                    mma_tf32_ss(tmem, sw128_desc(xhi + kk * 32), sw128_desc(zhi + kk * 32), idesc, acc);
-                    mma_tf32_ss(tmem, sw128_desc(xhi + kk * 32), sw128_desc(zlo + kk * 32), idesc, 1u);
-                    mma_tf32_ss(tmem, sw128_desc(xlo + kk * 32), sw128_desc(zhi + kk * 32), idesc, 1u);
+                    const uint32_t acc = kk > 0 ? 1u : 0u;
+                    mma_tf32_ss(d, sw128_desc(xhi + kk * 32), sw128_desc(zhi + kk * 32), idesc, acc);
+                    mma_tf32_ss(d, sw128_desc(xhi + kk * 32), sw128_desc(zlo + kk * 32), idesc, 1u);
+                    mma_tf32_ss(d, sw128_desc(xlo + kk * 32), sw128_desc(zhi + kk * 32), idesc, 1u);
                 }
                 mma_commit(&empty_bar[s]);
+                mma_commit(&accf_bar[a]);
             }
             // arrives once every MMA issued above has completed (at once if none)
             mma_commit(&acc_bar);
@@ -155,6 +174,34 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // =========================== converters + epilogue (warps 2..5)
         const int t = (warp - 2) * 32 + lane;  // tile row (column of X) of this thread
+        // TMEM lane quarter warp % 4 holds accumulator rows 32 (warp % 4) ..;
+        // this thread sums row r over the stages in FP32 registers
+        const int q = warp & 3;
+        const int r = q * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        float sum[kRows];
+#pragma unroll
+        for (int j = 0; j < kRows; ++j) sum[j] = 0.f;
+        // add the accumulator of stage c into sum and hand it back to the MMA warp
+        auto drain = [&](int64_t c) -> bool {
+            const int a = (int)(c % kAcc);
+            if (!mbar_wait_warp(&accf_bar[a], (uint32_t)((c / kAcc) & 1), &abort_flag, p.status)) return false;
+            tmem_fence_after();
+#pragma unroll
+            for (int j0 = 0; j0 < kRows; j0 += 16) {
+                if (j0 < l_pad) {
+                    uint32_t v[16];
+                    tmem_ld16(tmem + (uint32_t)(a * kRows + j0) + lane_off, v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) sum[j0 + e] += __uint_as_float(v[e]);
+                }
+            }
+            tmem_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce_bar[a]);
+            return true;
+        };
         bool ok = true;
         for (int64_t c = 0; c < nk; ++c) {
             const int s = (int)(c % S);
@@ -189,22 +236,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(&conv_bar[s]);
+            // the accumulator of stage c - kLag (the tensor core has the
+            // stages after it queued meanwhile)
+            if (c >= kLag && !(ok = drain(c - kLag))) break;
         }
-        // ---- epilogue: TMEM lane quarter warp % 4 holds rows 32 (warp % 4) ..
-        const int q = warp & 3;
-        const int r = q * 32 + lane;
-        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        for (int64_t c = (nk > kLag ? nk - kLag : 0); ok && c < nk; ++c) ok = drain(c);
+        // ---- epilogue: row r of the partial from the FP32 sums
         float* out = p.part + (int64_t)blockIdx.x * l_pad * l_pad;
-        if (ok && (ok = mbar_wait_warp(&acc_bar, 0, &abort_flag, p.status))) {
-            tmem_fence_after();
-            for (int j0 = 0; j0 < l_pad; j0 += 16) {
-                uint32_t v[16];
-                tmem_ld16(tmem + (uint32_t)j0 + lane_off, v);
-                tmem_wait_ld();
-                if (r < l_pad)
+        if (ok && r < l_pad) {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) out[(int64_t)r * l_pad + j0 + e] = nk > 0 ? __uint_as_float(v[e]) : 0.f;
-            }
+            for (int j0 = 0; j0 < kRows; j0 += 16)
+                if (j0 < l_pad)
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) out[(int64_t)r * l_pad + j0 + e] = sum[j0 + e];
         }
         if (!ok) {
             // the MMA warp's final commit tells when its work has drained

@@ -21,7 +21,16 @@
 //     a_lo = a - a_hi (exact in FP32, |a_lo| < 2^-10 |a|); whether the tensor
 //     core rounds or truncates a_lo to TF32, and with the dropped a_lo p_lo
 //     term, each product is within 2^-19 |a||p| (p_hi, p_lo are split by
-//     round-to-nearest beforehand).
+//     round-to-nearest beforehand);
+//   * the tensor core's FP32 accumulation drops low bits toward zero at each
+//     step, so a long chain shrinks the sum by a relative bias that grows
+//     with its length (about 1.7e-8 per MMA on sums of random sign).  Where
+//     the scale of the result matters (the projection B = Q^T A, Grams, the
+//     C-ABI products) the K range is cut into chunks of chunk_stages stages:
+//     each chunk starts a fresh accumulator, the first chunk's result is
+//     stored and the later ones are added in FP32 (round to nearest) with
+//     reductions -- 16-byte ones into row-major split partials, which the
+//     launch then sums, when the product has split partials and an output.
 // Roles (352 threads): warp 0 issues the TMA loads of A, warp 10 those of the
 // panel, warp 1 allocates TMEM and issues MMAs (one elected lane), warps 2..9
 // convert A and run the epilogue (two warps per TMEM lane quarter, each taking
@@ -47,7 +56,8 @@ constexpr int kConvWarps = 8;      // converter / epilogue warps (two per TMEM l
 constexpr int kThreads = 128 + 32 * kConvWarps;  // + TMA(A), 2 x MMA, TMA(panel) warps
 constexpr int kMmaWarp1 = 3 + kConvWarps;        // second MMA issuer (odd groups)
 constexpr int kMaxAStages = 6;
-constexpr int kMaxPStages = 4;
+constexpr int kMaxPStages = 6;
+constexpr int kPanelStages = 3;    // panel ring depth wanted (fewer when shared memory is short)
 constexpr int kTmemStages = 2;     // A-operand buffers in TMEM
 
 struct TcParams {
@@ -66,6 +76,9 @@ struct TcParams {
     int out_vec4;          // row-major output 16-byte aligned (float4 stores)
     int out_cols;
     int64_t split_stride;  // AtX: floats between partials
+    int chunk_stages;      // > 0: accumulate at most this many K stages in TMEM before adding to the output
+    int part_rm;           // partials row-major (part + split * lanes * l_pad + idx * l_pad + j): chunks
+                           // after the first are added with 16-byte vector reductions
     int* status;
     double* fro2;          // if set: ||A||_F^2 is accumulated by the converters
 };
@@ -82,7 +95,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     __shared__ uint64_t afull_bar[kMaxAStages], aempty_bar[kMaxAStages];
     __shared__ uint64_t pfull_bar[kMaxPStages], pempty_bar[kMaxPStages];
-    __shared__ uint64_t conv_bar[kTmemStages], tfree_bar[kTmemStages];
+    constexpr int TS = kTmemStages;
+    __shared__ uint64_t conv_bar[TS], tfree_bar[TS];
     __shared__ uint64_t accf_bar, acce_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_flag;
@@ -120,11 +134,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     const int64_t num_sets = (tile_end - tile_begin + G - 1) / G;
     const int64_t nk = (k_end > k_begin) ? (k_end - k_begin + kBK - 1) / kBK : 0;
+    // K chunks of each set (one accumulator chain each)
+    const int64_t chunk = (p.chunk_stages > 0 && p.chunk_stages < nk) ? p.chunk_stages : (nk > 0 ? nk : 1);
+    const int64_t nch = (nk + chunk - 1) / chunk;
 
     // ---- TMEM columns: G accumulators of l_pad, then A buffers
     const uint32_t acc_cols = (uint32_t)G * l_pad;
     const uint32_t a_col0 = (acc_cols + 31) & ~31u;
-    const uint32_t need = a_col0 + kTmemStages * G * kAcols;
+    const uint32_t need = a_col0 + TS * G * kAcols;
     uint32_t tmem_cols = 32;
     while (tmem_cols < need) tmem_cols <<= 1;
 
@@ -137,7 +154,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&pfull_bar[s], 1);
             mbar_init(&pempty_bar[s], 2);  // one commit per MMA issuer
         }
-        for (int s = 0; s < kTmemStages; ++s) {
+        for (int s = 0; s < TS; ++s) {
             mbar_init(&conv_bar[s], kConvWarps);
             mbar_init(&tfree_bar[s], 2);
         }
@@ -209,18 +226,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int gpar = (warp == 1) ? 0 : 1;
         if (lane == 0) {
             const uint32_t idesc = BF ? bf16_idesc(kTileRows, l_pad) : tf32_idesc(kTileRows, l_pad);
-            int64_t it = 0;
+            int64_t it = 0, item = 0;
             bool ok = true;
             for (int64_t set = 0; set < num_sets && ok; ++set) {
                 const int64_t t0 = tile_begin + set * G;
                 const int gv = (int)min((int64_t)G, tile_end - t0);
-                if (!(ok = mbar_wait(&acce_bar, ((uint32_t)set & 1) ^ 1, &abort_flag, p.status))) break;
+              for (int64_t ch = 0; ch < nch && ok; ++ch, ++item) {
+                const int64_t c0 = ch * chunk, c1 = min(nk, c0 + chunk);
+                // the accumulators are free once the previous item's epilogue read them
+                if (!(ok = mbar_wait(&acce_bar, ((uint32_t)item & 1) ^ 1, &abort_flag, p.status))) break;
                 tmem_fence_after();
-                for (int64_t c = 0; c < nk; ++c, ++it) {
+                for (int64_t c = c0; c < c1; ++c, ++it) {
                     const int s = (int)(it % SP);
                     const uint32_t ph = (uint32_t)((it / SP) & 1);
-                    const int ts = (int)(it % kTmemStages);
-                    const uint32_t tph = (uint32_t)((it / kTmemStages) & 1);
+                    const int ts = (int)(it % TS);
+                    const uint32_t tph = (uint32_t)((it / TS) & 1);
                     if (!(ok = mbar_wait(&conv_bar[ts], tph, &abort_flag, p.status))) break;
                     if (!(ok = mbar_wait(&pfull_bar[s], ph, &abort_flag, p.status))) break;
                     tmem_fence_after();
@@ -234,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             // one BF16 product per K step of 16 (8 TMEM columns, 32 bytes of panel row)
 #pragma unroll
                             for (int kk = 0; kk < kBK / 16; ++kk) {
-                                const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+                                const uint32_t acc = (c > c0 || kk > 0) ? 1u : 0u;
                                 mma_bf16_tmemA(d, ahi + kk * 8, sw64_desc(phi + kk * 32), idesc, acc);
                             }
                             continue;
@@ -243,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int kk = 0; kk < kBK / 8; ++kk) {
                             const uint64_t bhi = sw128_desc(phi + kk * 32);
                             const uint64_t blo = sw128_desc(plo + kk * 32);
-                            const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+                            const uint32_t acc = (c > c0 || kk > 0) ? 1u : 0u;
                             mma_tf32_tmemA(d, ahi + kk * 8, bhi, idesc, acc);
                             mma_tf32_tmemA(d, ahi + kk * 8, blo, idesc, 1u);
                             if (!ABF) mma_tf32_tmemA(d, alo + kk * 8, bhi, idesc, 1u);
@@ -254,6 +274,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (!ok) break;
                 mma_commit(&accf_bar);
+              }
             }
             if (!ok) {
                 // wait (bounded) for the MMAs already issued before TMEM is freed
@@ -274,16 +295,103 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         constexpr int KH = kBK / 2;             // K columns converted by this warp
         float sq = 0.f;  // sum of squares of the A elements this thread converted
-        int64_t it = 0;
+        // Epilogue of one (tile set, K chunk) item: 16-column chunks alternate
+        // between the two warps of a quarter; the first chunk stores, later
+        // chunks add.  It runs after the first stage of the next item has been
+        // converted, so the tensor core restarts as soon as TMEM is drained.
+        auto epilogue = [&](int64_t e_item) -> bool {
+                const int64_t e_ch = e_item % nch;
+                const int64_t e_t0 = tile_begin + (e_item / nch) * G;
+                const int e_gv = (int)min((int64_t)G, tile_end - e_t0);
+                const bool e_first = (e_ch == 0), e_last = (e_ch == nch - 1);
+                if (!mbar_wait_warp(&accf_bar, (uint32_t)e_item & 1, &abort_flag, p.status)) return false;
+                tmem_fence_after();
+                for (int g = 0; g < e_gv; ++g) {
+                    const int64_t idx = (e_t0 + g) * kTileRows + r;  // row (AX) or column (AtX) of A
+                    const int64_t lim = TRANS ? p.n : p.m;
+                    float* out = p.out + (int64_t)blockIdx.y * p.split_stride;
+                    for (int j0 = 16 * hk; j0 < l_pad; j0 += 32) {
+                        uint32_t v[16];
+                        tmem_ld16(tmem + (uint32_t)(g * l_pad + j0) + lane_off, v);
+                        tmem_wait_ld();
+                        if (idx < lim) {
+                            if (p.out_rowmajor) {
+                                // a row of the output per thread: 16-byte stores when aligned
+                                float* orow = out + idx * p.ld_out + j0;
+                                if (p.out_vec4 && j0 + 16 <= p.out_cols) {
+#pragma unroll
+                                    for (int e = 0; e < 4; ++e) {
+                                        float4 y = make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
+                                                               __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
+                                        if (!e_first) {
+                                            const float4 o4 = *(const float4*)(orow + 4 * e);
+                                            y.x += o4.x;
+                                            y.y += o4.y;
+                                            y.z += o4.z;
+                                            y.w += o4.w;
+                                        }
+                                        *(float4*)(orow + 4 * e) = y;
+                                    }
+                                } else {
+#pragma unroll
+                                    for (int e = 0; e < 16; ++e)
+                                        if (j0 + e < p.out_cols)
+                                            orow[e] = e_first ? __uint_as_float(v[e]) : orow[e] + __uint_as_float(v[e]);
+                                }
+                            } else if (p.part_rm) {
+                                float* prow = out + idx * l_pad + j0;
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    const float4 y =
+                                        make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
+                                                    __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
+                                    if (e_first)
+                                        *(float4*)(prow + 4 * e) = y;
+                                    else
+                                        red_add_v4(prow + 4 * e, y);
+                                }
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 16; ++e) {
+                                    const int64_t o = (int64_t)(j0 + e) * p.ld_out + idx;
+                                    if (!e_first && !p.out_hi) {
+                                        // later chunks: a reduction (round to nearest) that
+                                        // returns nothing, so the warp does not wait on it;
+                                        // each address has one writer, in program order
+                                        atomicAdd(out + o, __uint_as_float(v[e]));
+                                        continue;
+                                    }
+                                    const float y = e_first ? __uint_as_float(v[e]) : out[o] + __uint_as_float(v[e]);
+                                    out[o] = y;
+                                    if (p.out_hi && e_last) {
+                                        const uint32_t h = tf32_rna(y);
+                                        p.out_hi[o] = __uint_as_float(h);
+                                        p.out_lo[o] = __uint_as_float(tf32_rna(y - __uint_as_float(h)));
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+                tmem_fence_before();
+                __syncwarp();
+                tmem_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce_bar);
+                return true;
+        };
+        int64_t it = 0, item = 0;
         bool ok = true;
         for (int64_t set = 0; set < num_sets && ok; ++set) {
             const int64_t t0 = tile_begin + set * G;
             const int gv = (int)min((int64_t)G, tile_end - t0);
-            for (int64_t c = 0; c < nk; ++c, ++it) {
+          for (int64_t ch = 0; ch < nch && ok; ++ch, ++item) {
+            const int64_t c0 = ch * chunk, c1 = min(nk, c0 + chunk);
+            for (int64_t c = c0; c < c1; ++c, ++it) {
                 const int s = (int)(it % SA);
                 const uint32_t ph = (uint32_t)((it / SA) & 1);
-                const int ts = (int)(it % kTmemStages);
-                const uint32_t tph = (uint32_t)((it / kTmemStages) & 1);
+                const int ts = (int)(it % TS);
+                const uint32_t tph = (uint32_t)((it / TS) & 1);
                 if (!(ok = mbar_wait_warp(&afull_bar[s], ph, &abort_flag, p.status))) break;
                 if (!(ok = mbar_wait_warp(&tfree_bar[ts], tph ^ 1, &abort_flag, p.status))) break;
                 tmem_fence_after();
@@ -411,54 +519,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&conv_bar[ts]);
+                // the previous item's epilogue, once this item's first stage is
+                // converted (the tensor core restarts as soon as TMEM is read)
+                if (c == c0 && item > 0 && !(ok = epilogue(item - 1))) break;
             }
             if (!ok) break;
-            // ---- epilogue of this tile set: 16-column chunks alternate between the two warps of a quarter
-            if (!(ok = mbar_wait_warp(&accf_bar, (uint32_t)set & 1, &abort_flag, p.status))) break;
-            tmem_fence_after();
-            for (int g = 0; g < gv; ++g) {
-                const int64_t idx = (t0 + g) * kTileRows + r;  // row (AX) or column (AtX) of A
-                const int64_t lim = TRANS ? p.n : p.m;
-                float* out = p.out + (int64_t)blockIdx.y * p.split_stride;
-                for (int j0 = 16 * hk; j0 < l_pad; j0 += 32) {
-                    uint32_t v[16];
-                    tmem_ld16(tmem + (uint32_t)(g * l_pad + j0) + lane_off, v);
-                    tmem_wait_ld();
-                    if (idx < lim) {
-                        if (p.out_rowmajor) {
-                            // a row of the output per thread: 16-byte stores when aligned
-                            float* orow = out + idx * p.ld_out + j0;
-                            if (p.out_vec4 && j0 + 16 <= p.out_cols) {
-#pragma unroll
-                                for (int e = 0; e < 4; ++e)
-                                    *(float4*)(orow + 4 * e) =
-                                        make_float4(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1]),
-                                                    __uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3]));
-                            } else {
-#pragma unroll
-                                for (int e = 0; e < 16; ++e)
-                                    if (j0 + e < p.out_cols) orow[e] = __uint_as_float(v[e]);
-                            }
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < 16; ++e) {
-                                const float y = __uint_as_float(v[e]);
-                                const int64_t o = (int64_t)(j0 + e) * p.ld_out + idx;
-                                out[o] = y;
-                                if (p.out_hi) {
-                                    const uint32_t h = tf32_rna(y);
-                                    p.out_hi[o] = __uint_as_float(h);
-                                    p.out_lo[o] = __uint_as_float(tf32_rna(y - __uint_as_float(h)));
-                                }
-                            }
-                        }
-                    }
-                }
-            }
-            tmem_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acce_bar);
+          }
         }
+        if (ok && item > 0) ok = epilogue(item - 1);
         if (SQ && p.fro2) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
@@ -472,6 +540,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         tmem_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+    }
+}
+
+// Sum of row-major split partials part[s][idx][j] (rows x l_pad each) into the
+// column-major output out[j * ld_out + idx], splits added in order (FP32).
+// Block: 32 rows, staged through shared memory for coalesced stores.
+__global__ void __launch_bounds__(256) reduce_rm_kernel(const float* __restrict__ part, int splits, int64_t rows,
+                                                        int l_pad, float* __restrict__ out, int64_t ld_out)
+{
+    extern __shared__ float tile[];  // 32 x (l_pad + 1)
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int nr = (int)min((int64_t)32, rows - r0);
+    const int64_t stride = rows * l_pad;
+    for (int e = threadIdx.x; e < nr * l_pad; e += blockDim.x) {
+        const float* src = part + r0 * l_pad + e;
+        float acc = 0.f;
+        for (int s = 0; s < splits; ++s) acc += src[(int64_t)s * stride];
+        tile[(e / l_pad) * (l_pad + 1) + e % l_pad] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * l_pad; e += blockDim.x) {
+        const int j = e / 32, rr = e % 32;
+        if (rr < nr) out[(int64_t)j * ld_out + r0 + rr] = tile[rr * (l_pad + 1) + j];
     }
 }
 
@@ -510,7 +601,8 @@ bool tc_pass_supported(int64_t m, int64_t n, int64_t lda, int l_pad, const void*
 int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int64_t m, int64_t n, int64_t lda,
                    const float* Phi, const float* Plo, int64_t ldp, int l_pad, float* out, float* out_hi,
                    float* out_lo, int64_t ld_out, float* partial, int64_t want_splits, int64_t* splits_out,
-                   int* status, double* fro2, int out_rowmajor, int out_cols, int bf16_panel, int a_bf16)
+                   int* status, double* fro2, int out_rowmajor, int out_cols, int bf16_panel, int a_bf16,
+                   int chunk_stages)
 {
     const bool bf = bf16_panel != 0;
     const bool abf = a_bf16 != 0;
@@ -518,7 +610,8 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
     const size_t a_stage = (size_t)G * kTileRows * kBK * (abf ? 2 : 4);
     const size_t p_stage = (bf ? 2 : 8) * (size_t)l_pad * kBK;
     const size_t budget = 224 * 1024;  // dynamic shared memory, 1 KB kept for alignment
-    int sp = (3 * p_stage + 2 * a_stage <= budget) ? 3 : 2;
+    int sp = kPanelStages;
+    while (sp > 2 && sp * p_stage + 2 * a_stage > budget) --sp;
     int sa = (int)std::min<size_t>(kMaxAStages, (budget - sp * p_stage) / a_stage);
     if (sa < 2) return RSVDGB_ERR_UNSUPPORTED;
     const size_t smem = sa * a_stage + sp * p_stage + 1024;
@@ -558,6 +651,9 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
     p.status = status;
     p.fro2 = fro2;
     p.ld_out = ld_out;
+    // each chunk boundary stalls the tensor core while the accumulators are
+    // read out, so chunks are at least 16 stages (512 K elements)
+    p.chunk_stages = chunk_stages > 0 ? std::max(chunk_stages, 16) : 0;
     p.num_tiles = ceil_div(trans ? n : m, kTileRows);
     // K splits: fill the GPU when the lane tiles alone do not
     const int64_t units = trans ? ceil_div(p.num_tiles, G) : p.num_tiles;
@@ -574,6 +670,11 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
     p.out_hi = direct ? out_hi : nullptr;
     p.out_lo = direct ? out_lo : nullptr;
     p.split_stride = direct ? 0 : (int64_t)l_pad * ld_out;
+    // chunked split products with an output: row-major partials, vector
+    // reductions, and the split sum done here
+    const int64_t lanes = trans ? n : m;
+    p.part_rm = (!direct && p.chunk_stages > 0 && out != nullptr && !out_rowmajor) ? 1 : 0;
+    if (p.part_rm) p.split_stride = lanes * l_pad;
     p.out_rowmajor = direct ? out_rowmajor : 0;
     p.out_cols = out_cols > 0 ? out_cols : l_pad;
     p.out_vec4 = (p.out_rowmajor && ((uintptr_t)p.out % 16) == 0 && (ld_out % 4) == 0) ? 1 : 0;
@@ -586,34 +687,41 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
         grid = dim3((unsigned)std::min<int64_t>(units, sm_count), 1);  // persistent over the sets
     else
         grid = dim3((unsigned)units, (unsigned)splits);
-    if (splits_out) *splits_out = direct ? 0 : splits;
+    if (splits_out) *splits_out = (direct || p.part_rm) ? 0 : splits;
+    int rc = RSVDGB_OK;
     switch ((abf ? 32 : 0) + (bf ? 16 : 0) + (trans ? 8 : 0) + G) {
-        case 1: return launch_typed<false, 1, false, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 2: return launch_typed<false, 2, false, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 3: return launch_typed<false, 3, false, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 9: return launch_typed<true, 1, false, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 10: return launch_typed<true, 2, false, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 11: return launch_typed<true, 3, false, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 17: return launch_typed<false, 1, true, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 18: return launch_typed<false, 2, true, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 19: return launch_typed<false, 3, true, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 25: return launch_typed<true, 1, true, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 26: return launch_typed<true, 2, true, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 27: return launch_typed<true, 3, true, false>(s, mA, mhi, mlo, p, grid, smem);
-        case 33: return launch_typed<false, 1, false, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 34: return launch_typed<false, 2, false, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 35: return launch_typed<false, 3, false, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 41: return launch_typed<true, 1, false, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 42: return launch_typed<true, 2, false, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 43: return launch_typed<true, 3, false, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 49: return launch_typed<false, 1, true, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 50: return launch_typed<false, 2, true, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 51: return launch_typed<false, 3, true, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 57: return launch_typed<true, 1, true, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 58: return launch_typed<true, 2, true, true>(s, mA, mhi, mlo, p, grid, smem);
-        case 59: return launch_typed<true, 3, true, true>(s, mA, mhi, mlo, p, grid, smem);
+        case 1: rc = launch_typed<false, 1, false, false>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 2: rc = launch_typed<false, 2, false, false>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 3: rc = launch_typed<false, 3, false, false>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 9: rc = launch_typed<true, 1, false, false>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 10: rc = launch_typed<true, 2, false, false>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 11: rc = launch_typed<true, 3, false, false>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 17: rc = launch_typed<false, 1, true, false>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 18: rc = launch_typed<false, 2, true, false>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 19: rc = launch_typed<false, 3, true, false>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 25: rc = launch_typed<true, 1, true, false>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 26: rc = launch_typed<true, 2, true, false>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 27: rc = launch_typed<true, 3, true, false>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 33: rc = launch_typed<false, 1, false, true>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 34: rc = launch_typed<false, 2, false, true>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 35: rc = launch_typed<false, 3, false, true>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 41: rc = launch_typed<true, 1, false, true>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 42: rc = launch_typed<true, 2, false, true>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 43: rc = launch_typed<true, 3, false, true>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 49: rc = launch_typed<false, 1, true, true>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 50: rc = launch_typed<false, 2, true, true>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 51: rc = launch_typed<false, 3, true, true>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 57: rc = launch_typed<true, 1, true, true>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 58: rc = launch_typed<true, 2, true, true>(s, mA, mhi, mlo, p, grid, smem); break;
+        case 59: rc = launch_typed<true, 3, true, true>(s, mA, mhi, mlo, p, grid, smem); break;
         default: return RSVDGB_ERR_UNSUPPORTED;
     }
+    if (rc != RSVDGB_OK || !p.part_rm) return rc;
+    const size_t red_smem = 32 * (size_t)(l_pad + 1) * sizeof(float);
+    reduce_rm_kernel<<<(unsigned)ceil_div(lanes, 32), 256, red_smem, s>>>(partial, (int)splits, lanes, l_pad, out,
+                                                                          ld_out);
+    count_launches();
+    return cudaGetLastError() == cudaSuccess ? RSVDGB_OK : RSVDGB_ERR_CUDA;
 }
 
 

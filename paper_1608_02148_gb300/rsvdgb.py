@@ -15,6 +15,7 @@ _PKG = Path(__file__).resolve().parent
 LIB_PATH = _PKG / "_build" / "librsvdgb.so"
 
 RSVDGB_OK = 0
+RSVDGB_ERR_INVALID_ARG = 1
 STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_NOMEM", 3: "ERR_CUDA", 4: "ERR_BREAKDOWN", 5: "ERR_NONFINITE",
           6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
 F32, BF16 = 0, 1
@@ -29,7 +30,8 @@ EXPORTS = ["rsvdgb_create", "rsvdgb_destroy", "rsvdgb_set_stream", "rsvdgb_defau
            "rsvdgb_pass_ax", "rsvdgb_pass_atx", "rsvdgb_profile_passes", "rsvdgb_profile_read",
            "rsvdgb_kernel_launches", "rsvdgb_pass_atx_noalloc", "rsvdgb_rsvd_batched",
            "rsvdgb_default_train_opts", "rsvdgb_controller_load", "rsvdgb_controller_set",
-           "rsvdgb_controller_train", "rsvdgb_controller_features", "rsvdgb_mlp_forward", "rsvdgb_mlp_grad"]
+           "rsvdgb_controller_train", "rsvdgb_controller_features", "rsvdgb_mlp_forward", "rsvdgb_mlp_grad",
+           "rsvdgb_rpca", "rsvdgb_rpca_host"]
 
 Q_MODE = {"fixed": 0, "learned": 1}
 MLP_PARAMS = 5410  # RSVDGB_MLP_PARAMS
@@ -105,6 +107,9 @@ def load(path: Path | str | None = None):
     sig = [P, P, I64, I64, I64, I, I, I, I, ctypes.POINTER(RsvdgbOpts), P, P, I64, P, I64, P]
     lib.rsvdgb_rsvd.argtypes = sig
     lib.rsvdgb_rsvd_host.argtypes = sig
+    pca_sig = [P, P, I64, I64, I64, I, I, I, I, ctypes.POINTER(RsvdgbOpts), P, I64, P, P, P, I64, P, P, P]
+    lib.rsvdgb_rpca.argtypes = pca_sig
+    lib.rsvdgb_rpca_host.argtypes = pca_sig
     lib.rsvdgb_rqb.argtypes = [P, P, I64, I64, I64, I, I, ctypes.POINTER(RsvdgbOpts), P, I64, P, I64, P]
     lib.rsvdgb_omega.argtypes = [P, I64, I, U64, I, P, I64]
     lib.rsvdgb_pass_ax.argtypes = [P, P, I64, I64, I64, I, P, I64, I, P, I64, I, I]
@@ -274,6 +279,63 @@ def rsvdgb_rsvd_host(h: Handle, A_host, k, nu=-1, nv=-1, opts: RsvdgbOpts | None
                               V.data_ptr() if nv_ > 0 else None, V.stride(0), ctypes.byref(info))
     _check("rsvdgb_rsvd_host", rc)
     return d, U[:, :nu_], V[:, :nv_], info
+
+
+def _pca_shape(A, opts):
+    if opts.layout == LAYOUT["row"]:
+        m, n = A.shape
+    else:  # column-major m x n matrix given as the row-major n x m tensor
+        n, m = A.shape
+    return m, n, _rowmajor_ld(A)
+
+
+def rsvdgb_rpca(h: Handle, A, k, center=True, scale=True, retx=True, opts: RsvdgbOpts | None = None,
+                sync_info=True):
+    """rpca(A, k, center, scale, retx, p, q) on a device tensor A
+    (observations x variables).  Returns a dict with rotation (n x k),
+    eigvals, sdev, x (m x k, or None without retx), center, scale, info."""
+    torch = _torch()
+    lib = load()
+    opts = opts or make_opts()
+    m, n, lda = _pca_shape(A, opts)
+    dev = A.device
+    f32 = dict(dtype=torch.float32, device=dev)
+    rot = torch.empty(n, k, **f32)
+    eig = torch.empty(k, **f32)
+    sdev = torch.empty(k, **f32)
+    x = torch.empty(m, k, **f32) if retx else None
+    cen = torch.empty(n, **f32)
+    sca = torch.empty(n, **f32)
+    info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=dev)
+    rc = lib.rsvdgb_rpca(h.ptr, A.data_ptr(), m, n, lda, _dtype_code(A), k, int(bool(center)), int(bool(scale)),
+                         ctypes.byref(opts), rot.data_ptr(), k, eig.data_ptr(), sdev.data_ptr(),
+                         x.data_ptr() if retx else None, k, cen.data_ptr(), sca.data_ptr(), info.data_ptr())
+    _check("rsvdgb_rpca", rc)
+    return {"rotation": rot, "eigvals": eig, "sdev": sdev, "x": x, "center": cen, "scale": sca,
+            "info": _info_from(info) if sync_info else info}
+
+
+def rsvdgb_rpca_host(h: Handle, A_host, k, center=True, scale=True, retx=True, opts: RsvdgbOpts | None = None):
+    """Host-buffer variant of rsvdgb_rpca (CPU tensors in and out; pin A_host
+    for full copy bandwidth).  Synchronous."""
+    torch = _torch()
+    lib = load()
+    opts = opts or make_opts()
+    m, n, lda = _pca_shape(A_host, opts)
+    pin = dict(dtype=torch.float32, pin_memory=A_host.is_pinned())
+    rot = torch.empty(n, k, **pin)
+    eig = torch.empty(k, **pin)
+    sdev = torch.empty(k, **pin)
+    x = torch.empty(m, k, **pin) if retx else None
+    cen = torch.empty(n, **pin)
+    sca = torch.empty(n, **pin)
+    info = RsvdgbInfo()
+    rc = lib.rsvdgb_rpca_host(h.ptr, A_host.data_ptr(), m, n, lda, _dtype_code(A_host), k, int(bool(center)),
+                              int(bool(scale)), ctypes.byref(opts), rot.data_ptr(), k, eig.data_ptr(),
+                              sdev.data_ptr(), x.data_ptr() if retx else None, k, cen.data_ptr(), sca.data_ptr(),
+                              ctypes.byref(info))
+    _check("rsvdgb_rpca_host", rc)
+    return {"rotation": rot, "eigvals": eig, "sdev": sdev, "x": x, "center": cen, "scale": sca, "info": info}
 
 
 def rsvdgb_rqb(h: Handle, A, k, opts: RsvdgbOpts | None = None):

@@ -190,3 +190,31 @@ def test_tc_rsvd_bf16_stored_a(rs, handle, prec):
         err = np.sqrt(oracle.residual_fro2(Aval, U.cpu().numpy().astype(np.float64),
                                            d.cpu().numpy().astype(np.float64), V.cpu().numpy().astype(np.float64)))
         assert err <= 1.01 * err_o, (err, err_o)
+
+
+def test_full_size_scale_of_products(rs, handle):
+    """200000 x 2000 (the benchmark's size): the tensor core's FP32
+    accumulation truncates, which would shrink long sums; the products whose
+    scale matters are accumulated in short chunks.  Against FP64 products of
+    the same stored values: the relative scale error of A^T X and of the
+    projection B = Q^T A stays below 5e-6, and Q from CholeskyQR2 (Grams of
+    200000 rows) is orthonormal to 2e-6 on its diagonal."""
+    import torch
+    m, n = 200000, 2000
+    A = inputs.spiked_noise(m, n, 1.0 / np.arange(1, n + 1), 1e-3, seed=0x160802148 + 2000, device="cuda")
+    A64 = A.double()
+
+    def scale_err(X, X64):
+        X = X.double()
+        return float((X * X64).sum() / (X64 * X64).sum() - 1.0)
+
+    Xm = torch.randn(m, 110, device="cuda")
+    Z = rs.rsvdgb_pass_atx(handle, A, Xm)
+    assert abs(scale_err(Z, A64.T @ Xm.double())) < 5e-6
+    Q, B, info = rs.rsvdgb_rqb(handle, A, 100, rs.make_opts(p=10, q=2))
+    torch.cuda.synchronize()
+    assert info.status == 0
+    Q64 = Q.double()
+    d = torch.diagonal(Q64.T @ Q64)
+    assert float(torch.max(torch.abs(d - 1))) < 2e-6
+    assert abs(scale_err(B, Q64.T @ A64)) < 5e-6
