@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=40000, help="row sample for the oracle baseline")
     ap.add_argument("--batched", type=int, default=4096, help="matrices in the batched workload (0 = skip)")
+    ap.add_argument("--rpca", type=int, default=1, help="time the randomized PCA workload (0 = skip)")
+    ap.add_argument("--variants", type=int, default=1,
+                    help="time the other precision and the learned mode on the same A (0 = skip)")
     ap.add_argument("--controller-eval", type=int, default=16,
                     help="held-out 20000x5000 matrices for the learned-(q, p) evaluation (0 = skip)")
     return ap.parse_args()
@@ -230,6 +233,65 @@ def run_batched(rs, h, dev, stream, count, steps, peaks):
             "status_nonzero_sampled": bad}
 
 
+def run_rpca(rs, h, dev, stream, steps, peaks, cpu_baseline, e2e_steps):
+    """Randomized PCA (Algorithm rpca, correlation PCA: centre + scale, scores
+    returned) of 200000 observations x 2000 variables with heterogeneous units
+    (inputs.pca_data: rank-100 factor model, loadings decaying 0.85^j, noise
+    0.05, column scales log-uniform in [0.1, 10], offsets 5 spreads);
+    k = 100, p = 10, q = 2: 1 statistics pass + 2q + 2 passes over A."""
+    import torch
+    from paper_1608_02148_gb300 import inputs
+    m, n, k, p, q = 200000, 2000, 100, 10, 2
+    A = inputs.pca_data(m, n, 100, seed=0x160802148 + 6000, device=dev)
+    opts = rs.make_opts(p=p, q=q, seed=1)
+    for _ in range(2):
+        r = rs.rsvdgb_rpca(h, A, k, opts=opts, sync_info=False)
+    torch.cuda.synchronize()
+    info = rs._info_from(r["info"])
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    nsteps = max(3, steps)
+    l0 = rs.rsvdgb_kernel_launches()
+    e0.record(stream)
+    for _ in range(nsteps):
+        rs.rsvdgb_rpca(h, A, k, opts=opts, sync_info=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / nsteps
+    launches = (rs.rsvdgb_kernel_launches() - l0) / nsteps
+    a_bytes = m * n * 4
+    passes = 2 * q + 3
+    roof_ms = passes * a_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3
+    out = {"workload": "rpca 200000x2000 fp32 (correlation PCA, scores), rank-100 factor model + noise, "
+                       "heterogeneous units and offsets, k=100 p=10 q=2",
+           "ms": ms, "passes_over_A": passes, "hbm_roofline_ms": roof_ms, "hbm_frac": roof_ms / ms,
+           "kernels_per_step": launches, "status": info.status,
+           "explained_variance_k": float(r["eigvals"].double().sum()) / n}
+    if e2e_steps > 0:
+        A_host = A.cpu().pin_memory()
+        rs.rsvdgb_rpca_host(h, A_host, k, opts=opts)
+        ts = []
+        for _ in range(e2e_steps):
+            t0 = time.perf_counter()
+            rs.rsvdgb_rpca_host(h, A_host, k, opts=opts)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        out["e2e"] = {"value": statistics.median(ts), "unit": "ms", "h2d_bytes_per_step": a_bytes,
+                      "d2h_bytes_per_step": 4 * (2 * k + n * k + m * k + 2 * n) + rs.INFO_BYTES}
+    if cpu_baseline:
+        import oracle
+        oracle.build()
+        rows = 20000
+        A_rows = A[:rows].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.rpca(A_rows, k, p=p, q=q, seed=1)
+        t = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": t * (m / rows) * 1e3, "unit": "ms", "cores": oracle.num_threads(),
+                               "kind": "oracle",
+                               "sample": f"oracle rpca on rows 0..{rows - 1} ({rows}x{n}), time x{m / rows:g}"}
+    del A
+    return out
+
+
 def cpu_oracle_time(A_host_rows, wl, seed_omega):
     """Median-free single timing of the FP64 oracle rSVD on a row block."""
     import oracle
@@ -374,6 +436,8 @@ def main():
     variants = {}
     other = "bf16_sketch" if args.prec == "fp32" else "fp32"
     try:
+        if not args.variants:
+            raise RuntimeError("skipped (--variants 0)")
         o2 = rs.make_opts(p=wl["p"], q=wl["q"], seed=rank, prec=other, engine=args.engine)
         for _ in range(2):
             rs.rsvdgb_rsvd(h, A, k, opts=o2, out=bufs, sync_info=False)
@@ -399,7 +463,7 @@ def main():
 
     # ---------------- learned (q, p) on the same A: the packaged controller ----------------
     ctl_path = os.path.join(ROOT, "paper_1608_02148_gb300", "controller_default.bin")
-    if os.path.exists(ctl_path):
+    if os.path.exists(ctl_path) and args.variants:
         try:
             rs.rsvdgb_controller_load(h, ctl_path)
             o3 = rs.make_opts(p=wl["p"], q=wl["q"], seed=rank, prec=args.prec, engine=args.engine,
@@ -445,6 +509,15 @@ def main():
             batched = run_batched(rs, h, dev, stream, args.batched, args.steps, peaks)
         except Exception as exc:
             batched = {"unavailable": str(exc)}
+
+    # ---------------- randomized PCA (Algorithm rpca) ----------------
+    rpca = None
+    if args.rpca > 0 and rank == 0 and args.workload == "spiked200k":
+        try:
+            rpca = run_rpca(rs, h, dev, stream, args.steps, peaks, world == 1 and not args.no_cpu_baseline,
+                            args.e2e_steps)
+        except Exception as exc:
+            rpca = {"unavailable": str(exc)}
 
     # ---------------- end to end through the host-buffer entry point ----------------
     e2e = None
@@ -496,6 +569,7 @@ def main():
                 "variants": variants,
                 "controller": controller,
                 "batched": batched,
+                "rpca": rpca,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                 "info": info.as_dict()}
         print(json.dumps(line), flush=True)

@@ -132,6 +132,9 @@ bool tc_pass_supported(int64_t m, int64_t n, int64_t lda, int l_pad, const void*
 // leading dimension ldp elements; Plo unused), one MMA per K step.  With
 // a_bf16, A (passed through the float pointer) holds BF16 values: exact in
 // TF32, so the FP32-accurate product needs two MMAs (a p_hi + a p_lo).
+// aff_h / aff_r (direct, unchunked, column-major outputs only) apply
+// out_ij = aff_r[i] (acc_ij - aff_u[i] aff_h[j]) in the epilogue (aff_h null:
+// no shift; aff_u, aff_r null: 1), before the TF32 split.
 // chunk_stages > 0 bounds each tensor-memory accumulation chain to that many
 // 32-wide K stages; the chunks are summed in the output in FP32 (the tensor
 // core's accumulation truncates, which biases long sums toward zero).
@@ -139,7 +142,8 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
                    const float* Phi, const float* Plo, int64_t ldp, int l_pad, float* out, float* out_hi,
                    float* out_lo, int64_t ld_out, float* partial, int64_t want_splits, int64_t* splits_out,
                    int* status, double* fro2, int out_rowmajor = 0, int out_cols = 0, int bf16_panel = 0,
-                   int a_bf16 = 0, int chunk_stages = 0);
+                   int a_bf16 = 0, int chunk_stages = 0, const float* aff_h = nullptr,
+                   const float* aff_u = nullptr, const float* aff_r = nullptr);
 int64_t tc_pass_max_splits(int64_t m, int64_t n, int l_pad, int sm_count);
 int64_t tc_split_count(int64_t k_total, int64_t units, int sm_count);
 // l x l row-major T -> column-major L x L TF32 hi/lo panel (zero padded),
@@ -207,6 +211,8 @@ void launch_var_stats(cudaStream_t s, int sm_count, const void* S, int64_t lda, 
 constexpr int kAffineMaxChunks = 64;
 void launch_affine_dot(cudaStream_t s, int sm_count, const float* X, int64_t ld, int64_t rows, int l, const float* w,
                        double* part, int* chunks_out);
+// h[j] = sum of the chunk partials of column j (j < l).
+void launch_affine_h(cudaStream_t s, const double* part, int chunks, int l, float* h);
 // out_ij = r_i (out_ij - u_i h_j), h_j = sum of the chunk partials of
 // column j (part null: no shift; u, r null: 1); optional TF32 split.
 void launch_affine_post(cudaStream_t s, float* out, int64_t ld, int64_t rows, int l, const float* r, const float* u,

@@ -174,6 +174,8 @@ __global__ void __launch_bounds__(256) rowstats_kernel(const void* __restrict__ 
 
 // Per-variable centre and multiplier from the partial sums (chunks x nvar),
 // the shifts x0 read again from S, and each block's share of ||X||_F^2.
+// Block: 32 variables (lane = variable); warp w sums the chunks c = w mod 8,
+// the eight warp sums are added in a fixed order.
 //   mean = x0 + s1 / m,  SS = sum (a - mean)^2 = s2 - s1^2 / m
 //   centre: mu = mean (or 0);  scale: s = sqrt(SS / (m - 1)) with the centring,
 //   sqrt(sum a^2 / (m - 1)) without it; c = 1 / s (0 for s = 0) or 1.
@@ -186,14 +188,28 @@ __global__ void __launch_bounds__(256) stats_finalize_kernel(const void* __restr
                                                              float* __restrict__ scale_out,
                                                              double* __restrict__ fro2_part)
 {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * 32 + lane;
+    __shared__ double r1[8][32], r2[8][32];
+    {
+        double a1 = 0.0, a2 = 0.0;
+        if (j < nvar)
+            for (int c = warp; c < chunks; c += 8) {
+                const double2 p = part[(int64_t)c * nvar + j];
+                a1 += p.x;
+                a2 += p.y;
+            }
+        r1[warp][lane] = a1;
+        r2[warp][lane] = a2;
+    }
+    __syncthreads();
+    if (warp != 0) return;
     double f2 = 0.0;
     if (j < nvar) {
         double s1 = 0.0, s2 = 0.0;
-        for (int c = 0; c < chunks; ++c) {
-            const double2 p = part[(int64_t)c * nvar + j];
-            s1 += p.x;
-            s2 += p.y;
+        for (int w = 0; w < 8; ++w) {
+            s1 += r1[w][lane];
+            s2 += r2[w][lane];
         }
         const double x0 = (double)load_elem<BF>(S, j * shift_stride);
         const double m = (double)m_obs;
@@ -215,14 +231,7 @@ __global__ void __launch_bounds__(256) stats_finalize_kernel(const void* __restr
         f2 = spread * cf * cf;
     }
     for (int o = 16; o > 0; o >>= 1) f2 += __shfl_xor_sync(0xffffffffu, f2, o);
-    __shared__ double red[8];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f2;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        fro2_part[blockIdx.x] = t;
-    }
+    if (lane == 0) fro2_part[blockIdx.x] = f2;
 }
 
 __global__ void sum_doubles_kernel(const double* __restrict__ part, int count, double* __restrict__ out)
@@ -244,18 +253,21 @@ __global__ void __launch_bounds__(256) affine_dot_kernel(const float* __restrict
     const int64_t r1 = min(rows, r0 + rows_per_chunk);
     const float* x = X + (int64_t)j * ld;
     double acc = 0.0;
-    float run = 0.f;
-    int cnt = 0;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        const float v = x[i];
-        run = w ? fmaf(v, w[i], run) : run + v;
-        if (++cnt == 8) {
-            acc += run;
-            run = 0.f;
-            cnt = 0;
-        }
+    // four independent FP32 runs of (at most) 8 terms each, then FP64
+    const int64_t step = blockDim.x;
+    int64_t i = r0 + threadIdx.x;
+    for (; i + 3 * step < r1; i += 32 * step) {
+        float run[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t ii = i + (int64_t)(4 * t + q) * step;
+                if (ii < r1) run[q] = w ? fmaf(x[ii], w[ii], run[q]) : run[q] + x[ii];
+            }
+        acc += (double)run[0] + (double)run[1] + (double)run[2] + (double)run[3];
     }
-    acc += run;
+    for (; i < r1; i += step) acc += w ? (double)(x[i] * w[i]) : (double)x[i];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     __shared__ double red[8];
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -265,6 +277,17 @@ __global__ void __launch_bounds__(256) affine_dot_kernel(const float* __restrict
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
         part[(int64_t)blockIdx.y * l + j] = t;
     }
+}
+
+// h[j] = sum over the chunk partials of column j (fixed order), for the
+// pass epilogue that applies the correction.
+__global__ void affine_h_kernel(const double* __restrict__ part, int chunks, int l, float* __restrict__ h)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= l) return;
+    double t = 0.0;
+    for (int c = 0; c < chunks; ++c) t += part[(int64_t)c * l + j];
+    h[j] = (float)t;
 }
 
 __device__ __forceinline__ void split_tf32(float x, float& h, float& r)
@@ -363,8 +386,9 @@ __global__ void pca_values_kernel(const float* __restrict__ sigma, int k, int64_
 int64_t stats_chunks(bool vars_are_cols, int64_t rows_s, int64_t cols_s, int sm_count)
 {
     if (!vars_are_cols) return 1;
+    // about eight 128-thread blocks per SM
     const int64_t cblocks = ceil_div(cols_s, 128 * 4);
-    int64_t chunks = ceil_div(2 * (int64_t)sm_count, cblocks);
+    int64_t chunks = ceil_div(8 * (int64_t)sm_count, cblocks);
     chunks = std::min<int64_t>(chunks, ceil_div(rows_s, kRun));
     return std::max<int64_t>(chunks, 1);
 }
@@ -394,7 +418,7 @@ void launch_var_stats(cudaStream_t s, int sm_count, const void* S, int64_t lda, 
         count_launches();
         const int used = (int)grid.y;
         const int64_t nvar = cols_s;
-        const unsigned fb = (unsigned)ceil_div(nvar, 256);
+        const unsigned fb = (unsigned)ceil_div(nvar, 32);
         if (a_bf16)
             stats_finalize_kernel<true><<<fb, 256, 0, s>>>(S, 1, part, used, nvar, rows_s, center, scale, mu, cmul,
                                                            center_out, scale_out, fro2_part);
@@ -420,7 +444,7 @@ void launch_var_stats(cudaStream_t s, int sm_count, const void* S, int64_t lda, 
     }
     count_launches();
     const int64_t nvar = rows_s;
-    const unsigned fb = (unsigned)ceil_div(nvar, 256);
+    const unsigned fb = (unsigned)ceil_div(nvar, 32);
     if (a_bf16)
         stats_finalize_kernel<true><<<fb, 256, 0, s>>>(S, lda, part, 1, nvar, cols_s, center, scale, mu, cmul,
                                                        center_out, scale_out, fro2_part);
@@ -434,8 +458,9 @@ void launch_var_stats(cudaStream_t s, int sm_count, const void* S, int64_t lda, 
 
 int affine_chunks(int64_t rows, int l, int sm_count)
 {
-    int64_t c = ceil_div(2 * (int64_t)sm_count, std::max(l, 1));
-    c = std::min<int64_t>(c, ceil_div(rows, 2048));
+    // about eight 256-thread blocks per SM
+    int64_t c = ceil_div(8 * (int64_t)sm_count, std::max(l, 1));
+    c = std::min<int64_t>(c, ceil_div(rows, 1024));
     return (int)std::max<int64_t>(std::min<int64_t>(c, kAffineMaxChunks), 1);
 }
 
@@ -447,6 +472,12 @@ void launch_affine_dot(cudaStream_t s, int sm_count, const float* X, int64_t ld,
     affine_dot_kernel<<<dim3((unsigned)l, (unsigned)chunks), 256, 0, s>>>(X, ld, rows, l, w, rpc, part);
     count_launches();
     *chunks_out = chunks;
+}
+
+void launch_affine_h(cudaStream_t s, const double* part, int chunks, int l, float* h)
+{
+    affine_h_kernel<<<(unsigned)ceil_div(l, 128), 128, 0, s>>>(part, chunks, l, h);
+    count_launches();
 }
 
 void launch_affine_post(cudaStream_t s, float* out, int64_t ld, int64_t rows, int l, const float* r, const float* u,

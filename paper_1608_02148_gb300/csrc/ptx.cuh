@@ -220,6 +220,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
         : "memory");
 }
 
+// Ties 16 registers filled by tcgen05.ld to a point after tcgen05.wait::ld, so
+// that no use of them is scheduled before the wait.
+__device__ __forceinline__ void tmem_regs_ready(uint32_t (&v)[16])
+{
+#pragma unroll
+    for (int i = 0; i < 16; ++i) asm volatile("" : "+r"(v[i]));
+}
+
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 

@@ -134,6 +134,7 @@ struct Work {
     float *mu, *cmul;
     double2* spart;
     double *hpart, *fpart;
+    float* hvec;  // correction vector h of the current pass
 };
 
 int splits_for(int64_t tiles, int64_t K, int sm_count)
@@ -222,6 +223,7 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w, int L_lo = 0)
     w.mu = w.cmul = nullptr;
     w.spart = nullptr;
     w.hpart = w.fpart = nullptr;
+    w.hvec = nullptr;
     if (g.pca_nvar > 0) {
         const bool vars_are_cols = (g.swap_uv == g.trans);
         const int64_t chunks = stats_chunks(vars_are_cols, g.sm(), g.sn(), sm_count);
@@ -229,7 +231,8 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w, int L_lo = 0)
         w.cmul = c.take<float>(g.pca_nvar);
         w.spart = c.take<double2>(chunks * g.pca_nvar);
         w.hpart = c.take<double>((size_t)kAffineMaxChunks * L);
-        w.fpart = c.take<double>(ceil_div(g.pca_nvar, 256));
+        w.fpart = c.take<double>(ceil_div(g.pca_nvar, 32));
+        w.hvec = c.take<float>(L);
     }
 }
 
@@ -323,7 +326,8 @@ double a_bytes(const Geom& g) { return (double)g.m * (double)g.n * (g.a_bf16 ? 2
 // out_h/out_l are given (tensor-core engine) they receive its TF32 split.
 void pass_over_A(rsvdgb_handle* h, const Geom& g, Work& w, bool A_side, const float* P, const float* Ph,
                  const float* Pl, float* out, float* out_h, float* out_l, double* fro2, const void* Pbf = nullptr,
-                 int chunk = 0)
+                 int chunk = 0, const float* aff_h = nullptr, const float* aff_u = nullptr,
+                 const float* aff_r = nullptr)
 {
     const cudaStream_t s = h->stream;
     const int64_t rows = A_side ? g.m : g.n;
@@ -345,11 +349,11 @@ void pass_over_A(rsvdgb_handle* h, const Geom& g, Work& w, bool A_side, const fl
     if (Pbf)
         launch_tc_gemm(s, h->sm_count, stored_atx, (const float*)g.A, g.sm(), g.sn(), g.lda, (const float*)Pbf,
                        nullptr, ldP, g.L, out, out_h, out_l, ldO, w.part, stored_atx ? 0 : 1, &splits, w.status, fro2,
-                       0, 0, 1, g.a_bf16, chunk);
+                       0, 0, 1, g.a_bf16, chunk, aff_h, aff_u, aff_r);
     else
         launch_tc_gemm(s, h->sm_count, stored_atx, (const float*)g.A, g.sm(), g.sn(), g.lda, Ph, Pl, ldP, g.L, out,
                        out_h, out_l, ldO, w.part, stored_atx ? 0 : 1, &splits, w.status, fro2, 0, 0, 0, g.a_bf16,
-                       chunk);
+                       chunk, aff_h, aff_u, aff_r);
     prof_mark(h, false, a_bytes(g));
     if (splits > 0) {
         launch_reduce_splits(s, w.part, (int)splits, (int64_t)g.L * ldO, g.l, rows, ldO, out, ldO);
@@ -396,13 +400,26 @@ void tc_times_small(rsvdgb_handle* h, const Geom& g, Work& w, const float* Xt, i
 void apply_A(rsvdgb_handle* h, const Geom& g, Work& w, double* fro2)
 {
     const Affine* af = g.aff;
+    const bool corr = af && (af->mu || (af->rows && af->c));
     int chunks = 0;
     if (af && af->mu)
         launch_affine_dot(h->stream, h->sm_count, w.Pt, g.ldn, g.n, g.l, af->rows ? nullptr : af->mu, af->part,
                           &chunks);
+    // the tensor-core A-side pass on row-major A writes Y directly: the
+    // correction runs in its epilogue; otherwise in a separate kernel
+    const bool fused = corr && g.use_tc && !g.trans;
+    const float *fh = nullptr, *fu = nullptr, *fr = nullptr;
+    if (fused) {
+        if (af->mu) {
+            launch_affine_h(h->stream, af->part, chunks, g.l, w.hvec);
+            fh = w.hvec;
+            fu = af->rows ? af->mu : nullptr;
+        }
+        fr = af->rows ? af->c : nullptr;
+    }
     pass_over_A(h, g, w, true, w.Pt, w.Pth, w.Ptl, w.Yt, w.Yth, w.Ytl, af ? nullptr : fro2,
-                g.bf16 ? w.Ptb : nullptr);
-    if (af && (af->mu || (af->rows && af->c)))
+                g.bf16 ? w.Ptb : nullptr, 0, fh, fu, fr);
+    if (corr && !fused)
         launch_affine_post(h->stream, w.Yt, g.ldm, g.m, g.l, af->rows ? af->c : nullptr,
                            af->rows ? af->mu : nullptr, af->mu ? af->part : nullptr, chunks,
                            g.use_tc ? w.Yth : nullptr, g.use_tc ? w.Ytl : nullptr);

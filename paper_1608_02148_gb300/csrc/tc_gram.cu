@@ -18,9 +18,9 @@
 // each accumulate step drops the low bits toward zero, so a long chain of
 // accumulations shrinks a sum of positive terms (a Gram diagonal) by a
 // relative bias that grows with the chain (about 5e-5 after 500 MMAs).  So
-// every 32-row stage accumulates into a fresh tensor-memory accumulator (four
-// in rotation), and the epilogue warps add it into FP32 registers (round to
-// nearest) two stages later, while the tensor core runs the next ones.  Every CTA takes a range of rows and
+// every two 32-row stages accumulate into a fresh tensor-memory accumulator
+// (four in rotation), and the epilogue warps add it into FP32 registers
+// (round to nearest) one such chunk later, while the tensor core runs on.  Every CTA takes a range of rows and
 // writes its l x l partial; the partials are summed by the split reduction.
 //
 // Roles (192 threads): warp 0 issues the TMA loads, warp 1 allocates tensor
@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr uint32_t kStage = (CROSS ? 4 : 2) * kTile;
     __shared__ uint64_t full_bar[kMaxStages], conv_bar[kMaxStages], empty_bar[kMaxStages];
     constexpr int kAcc = 4;  // accumulators in rotation
-    constexpr int kLag = 2;  // stage c is drained after stage c + kLag is converted
+    constexpr int kSpa = 2;  // stages per accumulator chunk (24 MMAs)
+    constexpr int kLag = 1;  // chunk ch is drained once chunk ch + kLag is converted
     __shared__ uint64_t acc_bar, accf_bar[kAcc], acce_bar[kAcc];
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_flag;
@@ -145,10 +146,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int64_t c = 0; c < nk; ++c) {
                 const int s = (int)(c % S);
                 const uint32_t ph = (uint32_t)((c / S) & 1);
-                const int a = (int)(c % kAcc);  // accumulator of this stage
-                // accumulator a was last used by stage c - kAcc: wait until it is drained
-                if (c >= kAcc && !(ok = mbar_wait(&acce_bar[a], (uint32_t)((c / kAcc - 1) & 1), &abort_flag,
-                                                  p.status)))
+                const int64_t ch = c / kSpa;
+                const int a = (int)(ch % kAcc);  // accumulator of this chunk
+                // accumulator a was last used by chunk ch - kAcc: wait until it is drained
+                if (c % kSpa == 0 && ch >= kAcc &&
+                    !(ok = mbar_wait(&acce_bar[a], (uint32_t)((ch / kAcc - 1) & 1), &abort_flag, p.status)))
                     break;
                 if (!(ok = mbar_wait(&conv_bar[s], ph, &abort_flag, p.status))) break;
                 tmem_fence_after();
@@ -159,13 +161,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t zlo = CROSS ? zhi + kTile : xlo;
 #pragma unroll
                 for (int kk = 0; kk < kBK / 8; ++kk) {
-                    const uint32_t acc = kk > 0 ? 1u : 0u;
+                    const uint32_t acc = (c % kSpa > 0 || kk > 0) ? 1u : 0u;
                     mma_tf32_ss(d, sw128_desc(xhi + kk * 32), sw128_desc(zhi + kk * 32), idesc, acc);
                     mma_tf32_ss(d, sw128_desc(xhi + kk * 32), sw128_desc(zlo + kk * 32), idesc, 1u);
                     mma_tf32_ss(d, sw128_desc(xlo + kk * 32), sw128_desc(zhi + kk * 32), idesc, 1u);
                 }
                 mma_commit(&empty_bar[s]);
-                mma_commit(&accf_bar[a]);
+                if (c % kSpa == kSpa - 1 || c == nk - 1) mma_commit(&accf_bar[a]);
             }
             // arrives once every MMA issued above has completed (at once if none)
             mma_commit(&acc_bar);
@@ -182,20 +184,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         float sum[kRows];
 #pragma unroll
         for (int j = 0; j < kRows; ++j) sum[j] = 0.f;
-        // add the accumulator of stage c into sum and hand it back to the MMA warp
-        auto drain = [&](int64_t c) -> bool {
-            const int a = (int)(c % kAcc);
-            if (!mbar_wait_warp(&accf_bar[a], (uint32_t)((c / kAcc) & 1), &abort_flag, p.status)) return false;
+        // add the accumulator of chunk ch into sum and hand it back to the MMA warp
+        auto drain = [&](int64_t ch) -> bool {
+            const int a = (int)(ch % kAcc);
+            if (!mbar_wait_warp(&accf_bar[a], (uint32_t)((ch / kAcc) & 1), &abort_flag, p.status)) return false;
             tmem_fence_after();
+            // two batches of four 16-column loads, one wait each
 #pragma unroll
-            for (int j0 = 0; j0 < kRows; j0 += 16) {
-                if (j0 < l_pad) {
-                    uint32_t v[16];
-                    tmem_ld16(tmem + (uint32_t)(a * kRows + j0) + lane_off, v);
-                    tmem_wait_ld();
+            for (int b0 = 0; b0 < kRows; b0 += 64) {
+                uint32_t v[4][16];
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) sum[j0 + e] += __uint_as_float(v[e]);
-                }
+                for (int t = 0; t < 4; ++t)
+                    if (b0 + 16 * t < l_pad) tmem_ld16(tmem + (uint32_t)(a * kRows + b0 + 16 * t) + lane_off, v[t]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (b0 + 16 * t < l_pad) {
+                        tmem_regs_ready(v[t]);
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) sum[b0 + 16 * t + e] += __uint_as_float(v[t][e]);
+                    }
             }
             tmem_fence_before();
             __syncwarp();
@@ -236,11 +244,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(&conv_bar[s]);
-            // the accumulator of stage c - kLag (the tensor core has the
-            // stages after it queued meanwhile)
-            if (c >= kLag && !(ok = drain(c - kLag))) break;
+            // at the end of chunk ch: drain chunk ch - kLag (the tensor core has
+            // the chunks after it queued meanwhile)
+            if ((c % kSpa == kSpa - 1 || c == nk - 1) && c / kSpa >= kLag && !(ok = drain(c / kSpa - kLag))) break;
         }
-        for (int64_t c = (nk > kLag ? nk - kLag : 0); ok && c < nk; ++c) ok = drain(c);
+        const int64_t nch = (nk + kSpa - 1) / kSpa;
+        for (int64_t ch = (nch > kLag ? nch - kLag : 0); ok && ch < nch; ++ch) ok = drain(ch);
         // ---- epilogue: row r of the partial from the FP32 sums
         float* out = p.part + (int64_t)blockIdx.x * l_pad * l_pad;
         if (ok && r < l_pad) {

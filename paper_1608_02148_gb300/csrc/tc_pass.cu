@@ -77,6 +77,9 @@ struct TcParams {
     int out_cols;
     int64_t split_stride;  // AtX: floats between partials
     int chunk_stages;      // > 0: accumulate at most this many K stages in TMEM before adding to the output
+    const float* aff_h;    // direct column-major output only: out = r_i (acc - u_i h_j)
+    const float* aff_u;    //   (h null: no shift; u, r null: 1)
+    const float* aff_r;
     int part_rm;           // partials row-major (part + split * lanes * l_pad + idx * l_pad + j): chunks
                            // after the first are added with 16-byte vector reductions
     int* status;
@@ -309,6 +312,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int g = 0; g < e_gv; ++g) {
                     const int64_t idx = (e_t0 + g) * kTileRows + r;  // row (AX) or column (AtX) of A
                     const int64_t lim = TRANS ? p.n : p.m;
+                    // rank-one correction and row scale of an affine map (centred /
+                    // scaled data): y = r_i (acc - u_i h_j)
+                    const float au = (p.aff_u && idx < lim) ? p.aff_u[idx] : 1.f;
+                    const float ar = (p.aff_r && idx < lim) ? p.aff_r[idx] : 1.f;
                     float* out = p.out + (int64_t)blockIdx.y * p.split_stride;
                     for (int j0 = 16 * hk; j0 < l_pad; j0 += 32) {
                         uint32_t v[16];
@@ -361,7 +368,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                                         atomicAdd(out + o, __uint_as_float(v[e]));
                                         continue;
                                     }
-                                    const float y = e_first ? __uint_as_float(v[e]) : out[o] + __uint_as_float(v[e]);
+                                    float y = e_first ? __uint_as_float(v[e]) : out[o] + __uint_as_float(v[e]);
+                                    if (p.aff_h) y = fmaf(-au, p.aff_h[j0 + e], y);
+                                    if (p.aff_r) y *= ar;
                                     out[o] = y;
                                     if (p.out_hi && e_last) {
                                         const uint32_t h = tf32_rna(y);
@@ -545,13 +554,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // Sum of row-major split partials part[s][idx][j] (rows x l_pad each) into the
 // column-major output out[j * ld_out + idx], splits added in order (FP32).
-// Block: 32 rows, staged through shared memory for coalesced stores.
+// Block: kRedRows rows, staged through shared memory so that the stores of a
+// column are contiguous.
+constexpr int kRedRows = 16;
 __global__ void __launch_bounds__(256) reduce_rm_kernel(const float* __restrict__ part, int splits, int64_t rows,
                                                         int l_pad, float* __restrict__ out, int64_t ld_out)
 {
-    extern __shared__ float tile[];  // 32 x (l_pad + 1)
-    const int64_t r0 = (int64_t)blockIdx.x * 32;
-    const int nr = (int)min((int64_t)32, rows - r0);
+    extern __shared__ float tile[];  // kRedRows x (l_pad + 1)
+    const int64_t r0 = (int64_t)blockIdx.x * kRedRows;
+    const int nr = (int)min((int64_t)kRedRows, rows - r0);
     const int64_t stride = rows * l_pad;
     for (int e = threadIdx.x; e < nr * l_pad; e += blockDim.x) {
         const float* src = part + r0 * l_pad + e;
@@ -560,8 +571,8 @@ __global__ void __launch_bounds__(256) reduce_rm_kernel(const float* __restrict_
         tile[(e / l_pad) * (l_pad + 1) + e % l_pad] = acc;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 32 * l_pad; e += blockDim.x) {
-        const int j = e / 32, rr = e % 32;
+    for (int e = threadIdx.x; e < kRedRows * l_pad; e += blockDim.x) {
+        const int j = e / kRedRows, rr = e % kRedRows;
         if (rr < nr) out[(int64_t)j * ld_out + r0 + rr] = tile[rr * (l_pad + 1) + j];
     }
 }
@@ -602,7 +613,7 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
                    const float* Phi, const float* Plo, int64_t ldp, int l_pad, float* out, float* out_hi,
                    float* out_lo, int64_t ld_out, float* partial, int64_t want_splits, int64_t* splits_out,
                    int* status, double* fro2, int out_rowmajor, int out_cols, int bf16_panel, int a_bf16,
-                   int chunk_stages)
+                   int chunk_stages, const float* aff_h, const float* aff_u, const float* aff_r)
 {
     const bool bf = bf16_panel != 0;
     const bool abf = a_bf16 != 0;
@@ -679,6 +690,11 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
     p.out_cols = out_cols > 0 ? out_cols : l_pad;
     p.out_vec4 = (p.out_rowmajor && ((uintptr_t)p.out % 16) == 0 && (ld_out % 4) == 0) ? 1 : 0;
     if (out_rowmajor && !direct) return RSVDGB_ERR_INVALID_ARG;
+    // the affine epilogue needs the whole sum in one place: direct, unchunked, column-major
+    if ((aff_h || aff_r) && (!direct || p.chunk_stages > 0 || out_rowmajor)) return RSVDGB_ERR_UNSUPPORTED;
+    p.aff_h = aff_h;
+    p.aff_u = aff_u;
+    p.aff_r = aff_r;
     dim3 grid;
     if (!trans)
         grid = dim3((unsigned)std::min<int64_t>(std::max<int64_t>(sm_count / splits, 1), p.num_tiles),
@@ -717,9 +733,9 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
         default: return RSVDGB_ERR_UNSUPPORTED;
     }
     if (rc != RSVDGB_OK || !p.part_rm) return rc;
-    const size_t red_smem = 32 * (size_t)(l_pad + 1) * sizeof(float);
-    reduce_rm_kernel<<<(unsigned)ceil_div(lanes, 32), 256, red_smem, s>>>(partial, (int)splits, lanes, l_pad, out,
-                                                                          ld_out);
+    const size_t red_smem = kRedRows * (size_t)(l_pad + 1) * sizeof(float);
+    reduce_rm_kernel<<<(unsigned)ceil_div(lanes, kRedRows), 256, red_smem, s>>>(partial, (int)splits, lanes, l_pad,
+                                                                                out, ld_out);
     count_launches();
     return cudaGetLastError() == cudaSuccess ? RSVDGB_OK : RSVDGB_ERR_CUDA;
 }
