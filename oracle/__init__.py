@@ -86,6 +86,10 @@ def _load():
     lib.oracle_mlp_loss_grad.argtypes = [P, P, P, I64, ctypes.c_double, P]
     lib.oracle_mlp_loss_grad.restype = ctypes.c_double
     lib.oracle_set_num_threads.restype = None
+    lib.oracle_pqr.argtypes = [I64, I64, P, I64, I, P, P, P, P, P]
+    lib.oracle_pqr.restype = I
+    lib.oracle_id.argtypes = [I64, I64, P, I64, I, P, P, P]
+    lib.oracle_id.restype = I
     _lib = lib
     return lib
 
@@ -229,6 +233,62 @@ def rpca(A: np.ndarray, k: int, center: bool = True, scale: bool = True, p: int 
     lam = d * d / (m - 1)
     return {"rotation": W, "eigvals": lam, "sdev": np.sqrt(lam), "x": U * d[None, :],
             "center": mu, "scale": s, "sigma": d, "X": X}
+
+
+def pqr(X: np.ndarray, k: int, force_piv=None):
+    """QR with column pivoting, k steps (rsvd_oracle.c: oracle_pqr).
+    Returns (piv (k,), R (k x cols) in the original column order,
+    resid_chosen (k,), resid_max (k,))."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    rows, cols = X.shape
+    piv = np.zeros(k, dtype=np.int64)
+    R = np.zeros((k, cols))
+    rc_ = np.zeros(k)
+    rm_ = np.zeros(k)
+    fp = None if force_piv is None else np.ascontiguousarray(force_piv, dtype=np.int64)
+    rc = _load().oracle_pqr(rows, cols, _ptr(X), cols, k, _ptr(fp) if fp is not None else None, _ptr(piv), _ptr(R),
+                            _ptr(rc_), _ptr(rm_))
+    if rc:
+        raise RuntimeError(f"oracle pqr failed ({rc})")
+    return piv, R, rc_, rm_
+
+
+def id_decomp(X: np.ndarray, k: int, force_piv=None):
+    """Algorithm id: (J (k,), Z (k x cols)) with X ~ X[:, J] Z."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    rows, cols = X.shape
+    J = np.zeros(k, dtype=np.int64)
+    Z = np.zeros((k, cols))
+    fp = None if force_piv is None else np.ascontiguousarray(force_piv, dtype=np.int64)
+    rc = _load().oracle_id(rows, cols, _ptr(X), cols, k, _ptr(fp) if fp is not None else None, _ptr(J), _ptr(Z))
+    if rc:
+        raise RuntimeError(f"oracle id failed ({rc})")
+    return J, Z
+
+
+def rid(A: np.ndarray, k: int, p: int = 10, q: int = 0, sdist: str = "normal", seed: int = 0, force_piv=None):
+    """Algorithm rid (Sec. 7.2): [~, B] = rqb(A, k, p, q); [~, Z, J] = id(B, k);
+    C = A(:, J).  Column ID of an m x n A with m >= n (the row ID is the
+    column ID of A^T).  Returns (C (m x k), Z (k x n), J (k,), B)."""
+    m, n = A.shape
+    if m < n:
+        raise ValueError("m >= n expected (the row ID is the column ID of A^T)")
+    _, B = rqb(A, k, p=p, q=q, sdist=sdist, seed=seed)
+    J, Z = id_decomp(B, k, force_piv)
+    C = values(A)[:, J]
+    return C, Z, J, B
+
+
+def rcur(A: np.ndarray, k: int, p: int = 10, q: int = 0, sdist: str = "normal", seed: int = 0,
+         force_col_piv=None, force_row_piv=None):
+    """Algorithm rcur (Sec. 7.1): [C, Z, J] = rid(A, k, p, q);
+    [~, S, P] = qr(C^T) pivoted; I = P(1:k); R = A(I, :); U = Z pinv(R)
+    (numpy's pseudo-inverse).  Returns (C, U, R, J, I)."""
+    C, Z, J, _ = rid(A, k, p=p, q=q, sdist=sdist, seed=seed, force_piv=force_col_piv)
+    I, _, _, _ = pqr(np.ascontiguousarray(C.T), k, force_row_piv)
+    R = values(A)[I, :]
+    U = Z @ np.linalg.pinv(R)
+    return C, U, R, J, I
 
 
 def power_direct(A: np.ndarray, l: int, q: int, sdist: str = "normal", seed: int = 0) -> np.ndarray:

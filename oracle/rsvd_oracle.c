@@ -582,6 +582,116 @@ double oracle_fro2(const void* Adata, int dtype, int64_t m, int64_t n, int64_t l
     return total;
 }
 
+/* ------------------------------------------------------------------------ */
+/* QR with column pivoting, stopped after k steps (the "pivoted QR" of      */
+/* Algorithm id step 1 and Algorithm rcur step 2).  X is rows x cols,       */
+/* row-major with leading dimension ldx.  Householder reflections; at step  */
+/* t the pivot is the column of the trailing block (rows t..) with the      */
+/* largest 2-norm, recomputed exactly (ties: lowest original index).        */
+/* Outputs: piv[t] (original column index of the t-th pivot), R (k x cols,  */
+/* row-major, ld cols): row t of the triangular factor in the ORIGINAL      */
+/* column order, so that R(:, piv) is upper triangular.  With force_piv     */
+/* non-NULL the pivots are prescribed instead of chosen; resid_chosen[t]    */
+/* and resid_max[t] (if non-NULL) receive the 2-norm of the chosen column's */
+/* trailing part and the largest such norm at step t.  Returns 0, or 1 for  */
+/* bad arguments / an invalid prescribed pivot.                             */
+/* ------------------------------------------------------------------------ */
+int oracle_pqr(int64_t rows, int64_t cols, const double* X, int64_t ldx, int k, const int64_t* force_piv,
+               int64_t* piv, double* R, double* resid_chosen, double* resid_max)
+{
+    if (rows < 1 || cols < 1 || k < 1 || k > rows || k > cols || ldx < cols) return 1;
+    double* W = (double*)malloc((size_t)(rows * cols) * sizeof(double)); /* column-major */
+    char* used = (char*)calloc((size_t)cols, 1);
+    double* v = (double*)malloc((size_t)rows * sizeof(double));
+    if (!W || !used || !v) { free(W); free(used); free(v); return 2; }
+    for (int64_t i = 0; i < rows; ++i)
+        for (int64_t j = 0; j < cols; ++j) W[j * rows + i] = X[i * ldx + j];
+    int rc = 0;
+    for (int t = 0; t < k; ++t) {
+        /* trailing norms of the unused columns */
+        int64_t best = -1;
+        double bestn = -1.0;
+        for (int64_t j = 0; j < cols; ++j) {
+            if (used[j]) continue;
+            double s = 0.0;
+            for (int64_t i = t; i < rows; ++i) s += W[j * rows + i] * W[j * rows + i];
+            if (s > bestn) { bestn = s; best = j; }
+        }
+        int64_t p = best;
+        if (force_piv) {
+            p = force_piv[t];
+            if (p < 0 || p >= cols || used[p]) { rc = 1; break; }
+        }
+        double pn = 0.0;
+        for (int64_t i = t; i < rows; ++i) pn += W[p * rows + i] * W[p * rows + i];
+        if (resid_chosen) resid_chosen[t] = sqrt(pn);
+        if (resid_max) resid_max[t] = sqrt(bestn);
+        piv[t] = p;
+        used[p] = 1;
+        /* reflector H = I - 2 u u^T mapping W(t:, p) to -sign(x_t) ||x|| e_1 */
+        const double nrm = sqrt(pn);
+        double* x = W + p * rows;
+        if (nrm > 0.0) {
+            const double alpha = (x[t] >= 0.0) ? -nrm : nrm;
+            for (int64_t i = t; i < rows; ++i) v[i] = x[i];
+            v[t] -= alpha;
+            double vn2 = 0.0;
+            for (int64_t i = t; i < rows; ++i) vn2 += v[i] * v[i];
+            const double vn = sqrt(vn2);
+            for (int64_t i = t; i < rows; ++i) v[i] /= vn;
+#pragma omp parallel for schedule(static)
+            for (int64_t j = 0; j < cols; ++j) {
+                double* w = W + j * rows;
+                double dot = 0.0;
+                for (int64_t i = t; i < rows; ++i) dot += v[i] * w[i];
+                for (int64_t i = t; i < rows; ++i) w[i] -= 2.0 * dot * v[i];
+            }
+        }
+        for (int64_t j = 0; j < cols; ++j) R[(int64_t)t * cols + j] = W[j * rows + t];
+    }
+    free(W); free(used); free(v);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Interpolative decomposition, Algorithm id: [~, S, P] = qr(X) pivoted     */
+/* (k steps); T = S(1:k,1:k)^{-1} S(1:k, k+1:cols) by back substitution;    */
+/* Z(:, P) = [I_k, T]; J = P(1:k).  X rows x cols row-major (ld ldx); Z is  */
+/* k x cols row-major.  force_piv as in oracle_pqr.  Returns 0, 1 for bad   */
+/* arguments, 3 if S(1:k,1:k) has a zero diagonal entry.                    */
+/* ------------------------------------------------------------------------ */
+int oracle_id(int64_t rows, int64_t cols, const double* X, int64_t ldx, int k, const int64_t* force_piv,
+              int64_t* J, double* Z)
+{
+    double* R = (double*)malloc((size_t)k * (size_t)cols * sizeof(double));
+    char* used = (char*)calloc((size_t)cols, 1);
+    if (!R || !used) { free(R); free(used); return 2; }
+    int rc = oracle_pqr(rows, cols, X, ldx, k, force_piv, J, R, NULL, NULL);
+    if (!rc) {
+        for (int t = 0; t < k; ++t)
+            if (R[(int64_t)t * cols + J[t]] == 0.0) rc = 3;
+    }
+    if (!rc) {
+        for (int t = 0; t < k; ++t) used[J[t]] = 1;
+        for (int64_t j = 0; j < cols; ++j) {
+            if (used[j]) {
+                for (int a = 0; a < k; ++a) Z[(int64_t)a * cols + j] = 0.0;
+                continue;
+            }
+            /* S11 t = S(:, j), S11(a, b) = R(a, J[b]) upper triangular */
+            for (int a = k - 1; a >= 0; --a) {
+                double s = R[(int64_t)a * cols + j];
+                for (int b = a + 1; b < k; ++b) s -= R[(int64_t)a * cols + J[b]] * Z[(int64_t)b * cols + j];
+                Z[(int64_t)a * cols + j] = s / R[(int64_t)a * cols + J[a]];
+            }
+        }
+        for (int t = 0; t < k; ++t)
+            for (int a = 0; a < k; ++a) Z[(int64_t)a * cols + J[t]] = (a == t) ? 1.0 : 0.0;
+    }
+    free(R); free(used);
+    return rc;
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP
