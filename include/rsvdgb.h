@@ -204,6 +204,39 @@ int rsvdgb_rpca_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int6
                      int center, int scale, const rsvdgb_opts* opts, float* rotation, int64_t ldr, float* eigvals,
                      float* sdev, float* x, int64_t ldx, float* center_out, float* scale_out, rsvdgb_info* info);
 
+/*
+ * rid(A, k, p, q) of Sec. 7.2 -- Algorithm rid: the randomized column
+ * interpolative decomposition A ~ C Z with C = A(:, J).
+ *   A, m, n, lda, dtype, opts  as in rsvdgb_rsvd; m >= n is required (the
+ *          row ID is the column ID of A^T: call with A^T),
+ *          otherwise RSVDGB_ERR_UNSUPPORTED.
+ *   k      1 <= k < n, k <= 256.
+ *   C      device float, m x k row-major (ldc >= k): the k columns of A, or NULL.
+ *   Z      device float, k x n row-major (ldz >= n): the interpolation matrix
+ *          (Z(:, J) = I), or NULL.
+ *   J      device int64[k], required: the column indices, in pivot order.
+ * Steps: [~, B] = rqb(A, k, p, q) with opts' p and q; QR with column pivoting
+ * of the l x n factor B stopped after k steps (Algorithm id); Z(:, P) =
+ * [I, S11^{-1} S12]; C = A(:, J).  A pivot step that finds no remaining
+ * direction (rank of B below k) sets info->status = RSVDGB_ERR_BREAKDOWN.
+ */
+int rsvdgb_rid(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k,
+               const rsvdgb_opts* opts, float* C, int64_t ldc, float* Z, int64_t ldz, int64_t* J, rsvdgb_info* info);
+
+/*
+ * rcur(A, k, p, q) of Sec. 7.1 -- Algorithm rcur: A ~ C U R with C = A(:, J)
+ * and R = A(I, :).  Arguments as rsvdgb_rid, plus
+ *   U      device float, k x k row-major (ldu >= k), or NULL.
+ *   R      device float, k x n row-major (ldr >= n), or NULL.
+ *   I      device int64[k], required: the row indices, in pivot order.
+ * Steps: [C, Z, J] = rid(A, k, p, q); QR with column pivoting of C^T (k
+ * steps) gives I; R = A(I, :); U = Z pinv(R), with pinv(R) = Q_R S^{-T} from
+ * the CholeskyQR2 factorisation R^T = Q_R S (R of full row rank).
+ */
+int rsvdgb_rcur(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k,
+                const rsvdgb_opts* opts, float* C, int64_t ldc, float* U, int64_t ldu, float* R, int64_t ldr,
+                int64_t* J, int64_t* I, rsvdgb_info* info);
+
 /* One matrix of a batch: device pointer to A (m x n row-major, lda >= n). */
 typedef struct rsvdgb_matrix_desc {
     const void* A;

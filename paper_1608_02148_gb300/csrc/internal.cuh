@@ -226,6 +226,30 @@ void launch_scale_cols_small(cudaStream_t s, float* T, int l, int ncols, const f
 // eig = sigma^2 / (m_obs - 1), sdev = sigma / sqrt(m_obs - 1) (first k).
 void launch_pca_values(cudaStream_t s, const float* sigma, int k, int64_t m_obs, float* eig, float* sdev);
 
+// Interpolative / CUR decompositions (rid.cu).
+// Column-pivoted QR (k steps) of the r x N matrix X (column j at X + j*ldx,
+// r <= 256, k <= r): pivots (int, k), R rows (k x N row-major, optional),
+// one cooperative launch with a bounded grid barrier.  Workspace: nrm (N
+// doubles), Q (r*k floats), max_slots (double, int64) slots, one counter.
+int launch_pqr(cudaStream_t s, int sm_count, const float* X, int64_t ldx, int r, int64_t N, int k, int* piv,
+               float* R, double* nrm, float* Q, double* slot_val, int64_t* slot_idx, int max_slots,
+               unsigned int* bar, int* status);
+// Z (k x N, ld ldz) of the ID from R and the pivots (Algorithm id steps 2-5).
+void launch_id_solve(cudaStream_t s, const float* R, int64_t N, int k, const int* piv, float* Z, int64_t ldz,
+                     int* status);
+// C (rows x k, ld ldc) = columns idx of the logical matrix of the stored S.
+void launch_gather_cols(cudaStream_t s, const void* S, int64_t lda, int a_bf16, bool trans, int64_t rows,
+                        const int* idx, int k, float* C, int64_t ldc);
+// R (k x cols, ld ldr) = rows idx of the logical matrix; Rt its transpose
+// (column-major, ld ldt); either may be null.
+void launch_gather_rows(cudaStream_t s, const void* S, int64_t lda, int a_bf16, bool trans, int64_t cols,
+                        const int* idx, int k, float* R, int64_t ldr, float* Rt, int64_t ldt);
+// X (r x N column-major, ld ldx) = transpose of the column-major N x r Bt.
+void launch_transpose_cm(cudaStream_t s, const float* Bt, int64_t ldb, int64_t N, int r, float* X, int64_t ldx);
+// W (k x k row-major) = Z Q, Z k x N row-major, Q N x k column-major.
+void launch_zq(cudaStream_t s, const float* Z, int64_t ldz, const float* Q, int64_t ldq, int64_t N, int k, float* W);
+void launch_piv_to_i64(cudaStream_t s, const int* piv, int k, int64_t* out);
+
 // Batched rSVD (batched.cu): plan cache owned by the handle.
 struct BatchedPlan;
 void destroy_plan(BatchedPlan* pl);

@@ -115,6 +115,8 @@ struct Geom {
     int64_t ldm, ldn;
     const Affine* aff = nullptr;  // randomized PCA: products with X instead of A
     int64_t pca_nvar = 0;         // randomized PCA: number of variables (0: plain rSVD)
+    int rid_k = 0;                // interpolative / CUR decomposition of rank rid_k (0: none)
+    bool rid_cur = false;         // ... with the CUR step
     // stored matrix dimensions (rows x cols of the row-major S)
     int64_t sm() const { return trans ? n : m; }
     int64_t sn() const { return trans ? m : n; }
@@ -135,7 +137,15 @@ struct Work {
     double2* spart;
     double *hpart, *fpart;
     float* hvec;  // correction vector h of the current pass
+    // interpolative / CUR decompositions
+    float *Xb, *Rk, *Zw, *Qp, *Cw;
+    double *pnrm, *slot_v;
+    int64_t* slot_i;
+    int* piv;
+    unsigned int* bar;
 };
+
+constexpr int kPqrSlots = 1024;  // per-CTA maxima of the pivoted QR (its grid is at most this wide)
 
 int splits_for(int64_t tiles, int64_t K, int sm_count)
 {
@@ -224,6 +234,24 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w, int L_lo = 0)
     w.spart = nullptr;
     w.hpart = w.fpart = nullptr;
     w.hvec = nullptr;
+    w.Xb = w.Rk = w.Zw = w.Qp = w.Cw = nullptr;
+    w.pnrm = w.slot_v = nullptr;
+    w.slot_i = nullptr;
+    w.piv = nullptr;
+    w.bar = nullptr;
+    if (g.rid_k > 0) {
+        const int kk = g.rid_k;
+        w.Xb = c.take<float>(L * g.n);
+        w.Rk = c.take<float>((size_t)kk * g.n);
+        w.Zw = c.take<float>((size_t)kk * g.n);
+        w.Qp = c.take<float>((size_t)256 * kk);
+        w.pnrm = c.take<double>(std::max(g.m, g.n));
+        w.slot_v = c.take<double>(kPqrSlots);
+        w.slot_i = c.take<int64_t>(kPqrSlots);
+        w.piv = c.take<int>(2 * kk);
+        w.bar = c.take<unsigned int>(1);
+        if (g.rid_cur) w.Cw = c.take<float>((size_t)g.m * kk);
+    }
     if (g.pca_nvar > 0) {
         const bool vars_are_cols = (g.swap_uv == g.trans);
         const int64_t chunks = stats_chunks(vars_are_cols, g.sm(), g.sn(), sm_count);
@@ -546,6 +574,22 @@ struct Outputs {
     int64_t ldb;
     rsvdgb_info* info;
     int sigma_cols;  // 1: columns of the logical U scaled by sigma; 2: of V (PCA scores)
+    const struct RidSpec* rid;  // interpolative / CUR decomposition instead of the SVD of B
+};
+
+// Outputs of Algorithms rid / rcur (device pointers; C, Z, U, R may be null).
+struct RidSpec {
+    bool cur;
+    float* C;
+    int64_t ldc;  // m x k
+    float* Z;
+    int64_t ldz;  // k x n
+    int64_t* J;   // k column indices
+    float* U;
+    int64_t ldu;  // k x k
+    float* R;
+    int64_t ldr;  // k x n
+    int64_t* I;   // k row indices
 };
 
 // Randomized PCA on top of the rSVD (Algorithm rpca): centring / scaling
@@ -588,6 +632,46 @@ void sketch_features(rsvdgb_handle* h, const Geom& g, Work& w, int k, int p_max,
     const cudaStream_t s = h->stream;
     launch_chol_inv(s, w.G, g.l, 0.f, w.R1, w.T, w.status, w.breakdowns);
     launch_controller_features(s, w.R1, g.l, w.fro2, g.m, g.n, k, p_max, feats);
+}
+
+// Algorithm id on B (from B^T in Wt) and the rest of Algorithms rid / rcur.
+int rid_tail(rsvdgb_handle* h, const Geom& g, Work& w, int k, const RidSpec& r)
+{
+    const cudaStream_t s = h->stream;
+    const int sm = h->sm_count;
+    const int l = g.l;
+    // B (l x n, column j contiguous) from B^T
+    launch_transpose_cm(s, w.Wt, g.ldn, g.n, l, w.Xb, g.L);
+    int rc = launch_pqr(s, sm, w.Xb, g.L, l, g.n, k, w.piv, w.Rk, w.pnrm, w.Qp, w.slot_v, w.slot_i, kPqrSlots,
+                        w.bar, w.status);
+    if (rc) return rc;
+    float* Z = r.Z ? r.Z : w.Zw;
+    const int64_t ldz = r.Z ? r.ldz : g.n;
+    launch_id_solve(s, w.Rk, g.n, k, w.piv, Z, ldz, w.status);
+    launch_piv_to_i64(s, w.piv, k, r.J);
+    float* C = r.C ? r.C : (r.cur ? w.Cw : nullptr);
+    const int64_t ldc = r.C ? r.ldc : k;
+    if (C) launch_gather_cols(s, g.A, g.lda, g.a_bf16, g.trans, g.m, w.piv, k, C, ldc);
+    if (!r.cur) return RSVDGB_OK;
+    // row pivots: the pivoted QR of C^T (k x m; its column i is row i of C)
+    rc = launch_pqr(s, sm, C, ldc, k, g.m, k, w.piv + k, nullptr, w.pnrm, w.Qp, w.slot_v, w.slot_i, kPqrSlots,
+                    w.bar, w.status);
+    if (rc) return rc;
+    launch_piv_to_i64(s, w.piv + k, k, r.I);
+    // R = A(I, :) and R^T (n x k column-major, zero beyond column k) in Wt
+    RSVDGB_CUDA_TRY(cudaMemsetAsync(w.Wt, 0, sizeof(float) * (size_t)g.L * g.ldn, s));
+    launch_gather_rows(s, g.A, g.lda, g.a_bf16, g.trans, g.n, w.piv + k, k, r.R, r.ldr, w.Wt, g.ldn);
+    // U = Z pinv(R): R^T = Q_R S (CholeskyQR2), pinv(R) = Q_R S^{-T},
+    // U = (Z Q_R) (T1 T2)^T with S^{-1} = T1 T2
+    cholqr2(s, sm, w, w.Wt, g.ldn, g.n, k, w.Zt, w.Pt, g.use_tc ? (int)round_up(k, 16) : 0);
+    launch_zq(s, Z, ldz, w.Pt, g.ldn, g.n, k, w.M);
+    launch_small_matmul(s, w.T1, w.T2, w.RB, k);
+    launch_small_transpose(s, w.RB, w.Ut, k);
+    launch_small_matmul(s, w.M, w.Ut, w.Jt, k);
+    if (r.U)
+        RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(r.U, r.ldu * sizeof(float), w.Jt, k * sizeof(float), k * sizeof(float), k,
+                                          cudaMemcpyDeviceToDevice, s));
+    return RSVDGB_OK;
 }
 
 int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, const Outputs& o,
@@ -686,6 +770,14 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
         times_small(s, sm, w.Qt, g.ldm, g.m, l, w.T2, w.Yt, w.part);
     // step 10: B^T = A^T Q (n x l, column-major: row j of B is contiguous)
     apply_At(h, g, w, true);
+    if (o.rid) {
+        const int rc = rid_tail(h, g, w, k, *o.rid);
+        if (rc) return rc;
+        launch_finalize_info(s, nullptr, 0, k, nullptr, w.fro2, w.status, w.breakdowns, q, l - k,
+                             g.use_tc ? RSVDGB_ENGINE_TC : RSVDGB_ENGINE_SIMT, nullptr, o.info);
+        RSVDGB_CUDA_TRY(cudaGetLastError());
+        return RSVDGB_OK;
+    }
     if (o.Qrow) launch_colmajor_to_rowmajor(s, w.Yt, g.ldm, g.m, l, o.Qrow, o.ldq);
     if (o.Brow)
         RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(o.Brow, o.ldb * sizeof(float), w.Wt, g.ldn * sizeof(float),
@@ -1125,6 +1217,47 @@ int rsvdgb_rpca_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int6
     RSVDGB_CUDA_TRY(cudaStreamSynchronize(s));
     if (info) *info = hinfo;
     return hinfo.status;
+}
+
+static int rid_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k,
+                      const rsvdgb_opts* opts, const RidSpec& r, rsvdgb_info* info)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    rsvdgb_opts o;
+    if (opts)
+        o = *opts;
+    else
+        rsvdgb_default_opts(&o);
+    if (o.q < 0 || o.sdist < 0 || o.sdist > 2) return RSVDGB_ERR_INVALID_ARG;
+    if (m < n) return RSVDGB_ERR_UNSUPPORTED;  // the row ID is the column ID of A^T
+    Geom g{};
+    rc = make_geom(A, m, n, lda, dtype, o.layout, k, o.p, o.engine, o.prec, g);
+    if (rc) return rc;
+    if (k > 256 || !r.J || (r.cur && !r.I)) return RSVDGB_ERR_INVALID_ARG;
+    if ((r.C && r.ldc < k) || (r.Z && r.ldz < n) || (r.U && r.ldu < k) || (r.R && r.ldr < n))
+        return RSVDGB_ERR_INVALID_ARG;
+    g.rid_k = k;
+    g.rid_cur = r.cur;
+    Outputs out{};
+    out.info = info;
+    out.rid = &r;
+    return run_fp32(h, g, k, o.q, o.sdist, o.seed, out);
+}
+
+int rsvdgb_rid(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k,
+               const rsvdgb_opts* opts, float* C, int64_t ldc, float* Z, int64_t ldz, int64_t* J, rsvdgb_info* info)
+{
+    const RidSpec r{false, C, ldc, Z, ldz, J, nullptr, 0, nullptr, 0, nullptr};
+    return rid_common(h, A, m, n, lda, dtype, k, opts, r, info);
+}
+
+int rsvdgb_rcur(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k,
+                const rsvdgb_opts* opts, float* C, int64_t ldc, float* U, int64_t ldu, float* R, int64_t ldr,
+                int64_t* J, int64_t* I, rsvdgb_info* info)
+{
+    const RidSpec r{true, C, ldc, nullptr, 0, J, U, ldu, R, ldr, I};
+    return rid_common(h, A, m, n, lda, dtype, k, opts, r, info);
 }
 
 int rsvdgb_omega(rsvdgb_handle* h, int64_t rows, int l, uint64_t seed, int sdist, float* out, int64_t ld)

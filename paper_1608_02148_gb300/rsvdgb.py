@@ -31,7 +31,7 @@ EXPORTS = ["rsvdgb_create", "rsvdgb_destroy", "rsvdgb_set_stream", "rsvdgb_defau
            "rsvdgb_kernel_launches", "rsvdgb_pass_atx_noalloc", "rsvdgb_rsvd_batched",
            "rsvdgb_default_train_opts", "rsvdgb_controller_load", "rsvdgb_controller_set",
            "rsvdgb_controller_train", "rsvdgb_controller_features", "rsvdgb_mlp_forward", "rsvdgb_mlp_grad",
-           "rsvdgb_rpca", "rsvdgb_rpca_host"]
+           "rsvdgb_rpca", "rsvdgb_rpca_host", "rsvdgb_rid", "rsvdgb_rcur"]
 
 Q_MODE = {"fixed": 0, "learned": 1}
 MLP_PARAMS = 5410  # RSVDGB_MLP_PARAMS
@@ -110,6 +110,9 @@ def load(path: Path | str | None = None):
     pca_sig = [P, P, I64, I64, I64, I, I, I, I, ctypes.POINTER(RsvdgbOpts), P, I64, P, P, P, I64, P, P, P]
     lib.rsvdgb_rpca.argtypes = pca_sig
     lib.rsvdgb_rpca_host.argtypes = pca_sig
+    lib.rsvdgb_rid.argtypes = [P, P, I64, I64, I64, I, I, ctypes.POINTER(RsvdgbOpts), P, I64, P, I64, P, P]
+    lib.rsvdgb_rcur.argtypes = [P, P, I64, I64, I64, I, I, ctypes.POINTER(RsvdgbOpts), P, I64, P, I64, P, I64, P, P,
+                                P]
     lib.rsvdgb_rqb.argtypes = [P, P, I64, I64, I64, I, I, ctypes.POINTER(RsvdgbOpts), P, I64, P, I64, P]
     lib.rsvdgb_omega.argtypes = [P, I64, I, U64, I, P, I64]
     lib.rsvdgb_pass_ax.argtypes = [P, P, I64, I64, I64, I, P, I64, I, P, I64, I, I]
@@ -336,6 +339,44 @@ def rsvdgb_rpca_host(h: Handle, A_host, k, center=True, scale=True, retx=True, o
                               ctypes.byref(info))
     _check("rsvdgb_rpca_host", rc)
     return {"rotation": rot, "eigvals": eig, "sdev": sdev, "x": x, "center": cen, "scale": sca, "info": info}
+
+
+def rsvdgb_rid(h: Handle, A, k, opts: RsvdgbOpts | None = None, idx_only=False, sync_info=True):
+    """rid(A, k, p, q): returns dict C (m x k), Z (k x n), J (k,), info."""
+    torch = _torch()
+    lib = load()
+    opts = opts or make_opts()
+    m, n, lda = _pca_shape(A, opts)
+    f32 = dict(dtype=torch.float32, device=A.device)
+    C = None if idx_only else torch.empty(m, k, **f32)
+    Z = None if idx_only else torch.empty(k, n, **f32)
+    J = torch.empty(k, dtype=torch.int64, device=A.device)
+    info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=A.device)
+    rc = lib.rsvdgb_rid(h.ptr, A.data_ptr(), m, n, lda, _dtype_code(A), k, ctypes.byref(opts),
+                        C.data_ptr() if C is not None else None, k, Z.data_ptr() if Z is not None else None, n,
+                        J.data_ptr(), info.data_ptr())
+    _check("rsvdgb_rid", rc)
+    return {"C": C, "Z": Z, "J": J, "info": _info_from(info) if sync_info else info}
+
+
+def rsvdgb_rcur(h: Handle, A, k, opts: RsvdgbOpts | None = None, idx_only=False, sync_info=True):
+    """rcur(A, k, p, q): returns dict C (m x k), U (k x k), R (k x n), J, I, info."""
+    torch = _torch()
+    lib = load()
+    opts = opts or make_opts()
+    m, n, lda = _pca_shape(A, opts)
+    f32 = dict(dtype=torch.float32, device=A.device)
+    C = None if idx_only else torch.empty(m, k, **f32)
+    U = None if idx_only else torch.empty(k, k, **f32)
+    R = None if idx_only else torch.empty(k, n, **f32)
+    J = torch.empty(k, dtype=torch.int64, device=A.device)
+    I_ = torch.empty(k, dtype=torch.int64, device=A.device)
+    info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=A.device)
+    rc = lib.rsvdgb_rcur(h.ptr, A.data_ptr(), m, n, lda, _dtype_code(A), k, ctypes.byref(opts),
+                         C.data_ptr() if C is not None else None, k, U.data_ptr() if U is not None else None, k,
+                         R.data_ptr() if R is not None else None, n, J.data_ptr(), I_.data_ptr(), info.data_ptr())
+    _check("rsvdgb_rcur", rc)
+    return {"C": C, "U": U, "R": R, "J": J, "I": I_, "info": _info_from(info) if sync_info else info}
 
 
 def rsvdgb_rqb(h: Handle, A, k, opts: RsvdgbOpts | None = None):
