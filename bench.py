@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=40000, help="row sample for the oracle baseline")
     ap.add_argument("--batched", type=int, default=4096, help="matrices in the batched workload (0 = skip)")
     ap.add_argument("--rpca", type=int, default=1, help="time the randomized PCA workload (0 = skip)")
+    ap.add_argument("--rid", type=int, default=1, help="time the interpolative and CUR decompositions (0 = skip)")
     ap.add_argument("--variants", type=int, default=1,
                     help="time the other precision and the learned mode on the same A (0 = skip)")
     ap.add_argument("--controller-eval", type=int, default=16,
@@ -292,6 +293,54 @@ def run_rpca(rs, h, dev, stream, steps, peaks, cpu_baseline, e2e_steps):
     return out
 
 
+def run_rid(rs, h, A, wl, stream, steps, peaks, cpu_baseline):
+    """Algorithms rid and rcur (Sec. 7) on the benchmark matrix: rank k,
+    the workload's p and q (2q + 2 passes over A), then the column-pivoted QR
+    of B (and of C^T for rcur), the gathers and U = Z pinv(R)."""
+    import torch
+    m, n = A.shape
+    k = wl["k"]
+    opts = rs.make_opts(p=wl["p"], q=wl["q"], seed=2)
+    out = {"workload": f"rid / rcur of the {m}x{n} benchmark matrix, k={k} p={wl['p']} q={wl['q']}"}
+    a_bytes = m * n * 4
+    passes = 2 * wl["q"] + 2
+    for name, fn in (("rid", rs.rsvdgb_rid), ("rcur", rs.rsvdgb_rcur)):
+        for _ in range(2):
+            r = fn(h, A, k, opts=opts, sync_info=False)
+        torch.cuda.synchronize()
+        info = rs._info_from(r["info"])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        nsteps = max(3, steps // 2)
+        e0.record(stream)
+        for _ in range(nsteps):
+            fn(h, A, k, opts=opts, sync_info=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / nsteps
+        roof = passes * a_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3
+        Af = A.double()
+        if name == "rid":
+            err = float(torch.linalg.matrix_norm(Af - r["C"].double() @ r["Z"].double()))
+        else:
+            err = float(torch.linalg.matrix_norm(Af - r["C"].double() @ r["U"].double() @ r["R"].double()))
+        del Af
+        out[name] = {"ms": ms, "passes_over_A": passes, "hbm_roofline_ms": roof, "hbm_frac": roof / ms,
+                     "status": info.status, "err_fro": err}
+    if cpu_baseline:
+        import oracle
+        oracle.build()
+        rows = 20000
+        A_rows = A[:rows].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.rid(A_rows, k, p=wl["p"], q=wl["q"], seed=2)
+        t = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": t * (m / rows) * 1e3, "unit": "ms", "cores": oracle.num_threads(),
+                               "kind": "oracle",
+                               "sample": f"oracle rid on rows 0..{rows - 1} ({rows}x{n}), time x{m / rows:g}"}
+    return out
+
+
 def cpu_oracle_time(A_host_rows, wl, seed_omega):
     """Median-free single timing of the FP64 oracle rSVD on a row block."""
     import oracle
@@ -510,6 +559,14 @@ def main():
         except Exception as exc:
             batched = {"unavailable": str(exc)}
 
+    # ---------------- interpolative and CUR decompositions (Algorithms rid, rcur) ----------------
+    rid = None
+    if args.rid > 0 and rank == 0 and A.dtype == torch.float32:
+        try:
+            rid = run_rid(rs, h, A, wl, stream, args.steps, peaks, world == 1 and not args.no_cpu_baseline)
+        except Exception as exc:
+            rid = {"unavailable": str(exc)}
+
     # ---------------- randomized PCA (Algorithm rpca) ----------------
     rpca = None
     if args.rpca > 0 and rank == 0 and args.workload == "spiked200k":
@@ -570,6 +627,7 @@ def main():
                 "controller": controller,
                 "batched": batched,
                 "rpca": rpca,
+                "rid": rid,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                 "info": info.as_dict()}
         print(json.dumps(line), flush=True)

@@ -228,12 +228,13 @@ void launch_pca_values(cudaStream_t s, const float* sigma, int k, int64_t m_obs,
 
 // Interpolative / CUR decompositions (rid.cu).
 // Column-pivoted QR (k steps) of the r x N matrix X (column j at X + j*ldx,
-// r <= 256, k <= r): pivots (int, k), R rows (k x N row-major, optional),
-// one cooperative launch with a bounded grid barrier.  Workspace: nrm (N
-// doubles), Q (r*k floats), max_slots (double, int64) slots, one counter.
+// r <= 256, k <= r, r*k floats of shared memory per CTA): pivots (int, k),
+// R rows (k x N row-major, optional), one cooperative launch with a bounded
+// grid barrier.  Workspace: nrm (N doubles), max_slots (double, int64)
+// slots, one counter.
 int launch_pqr(cudaStream_t s, int sm_count, const float* X, int64_t ldx, int r, int64_t N, int k, int* piv,
-               float* R, double* nrm, float* Q, double* slot_val, int64_t* slot_idx, int max_slots,
-               unsigned int* bar, int* status);
+               float* R, double* nrm, double* slot_val, int64_t* slot_idx, int max_slots, unsigned int* bar,
+               int* status);
 // Z (k x N, ld ldz) of the ID from R and the pivots (Algorithm id steps 2-5).
 void launch_id_solve(cudaStream_t s, const float* R, int64_t N, int k, const int* piv, float* Z, int64_t ldz,
                      int* status);

@@ -10,8 +10,9 @@
 // by the square of each new row of R), and every step ends at a grid
 // barrier after which all CTAs take the same argmax of the per-CTA maxima.
 // The new direction q_t is the pivot column made orthogonal to q_0..q_{t-1}
-// by classical Gram-Schmidt applied twice (every CTA computes it, from the
-// same data in the same order, so all hold the same q_t; CTA 0 stores it).
+// by classical Gram-Schmidt applied twice; every CTA computes it from the
+// same data in the same order, so all hold the same q_t, each in its own
+// shared-memory copy of Q (r x k).
 // Row t of R is q_t^T x_j for all columns, which equals the Householder R of
 // the same pivots up to the sign of each row.  Every wait is bounded.
 #include "internal.cuh"
@@ -35,7 +36,6 @@ struct PqrArgs {
     int* piv;          // k pivots (CTA 0 writes; -1 after a breakdown)
     float* R;          // k x N row-major (ld N), or null
     double* nrm;       // N residual norms^2; -inf marks a chosen column
-    float* Q;          // q_t at Q + t * r
     double* slot_val;  // per-CTA maxima, two buffers of gridDim.x (by barrier parity)
     int64_t* slot_idx;
     unsigned int* bar;  // grid barrier counter (zero at launch)
@@ -125,7 +125,9 @@ __device__ void block_argmax_to_slot(double v, int64_t i, double* wv, int64_t* w
 
 __global__ void __launch_bounds__(kPqrThreads) pqr_kernel(PqrArgs a)
 {
-    extern __shared__ float qs[];  // r floats: the pivot column, then q_t
+    extern __shared__ float sm[];  // Q (r x k, column t = q_t), then r floats for the new column
+    float* Qs = sm;
+    float* qs = sm + (size_t)a.r * a.k;
     __shared__ float coef[256];
     __shared__ double wv[kPqrWarps];
     __shared__ int64_t wi[kPqrWarps];
@@ -157,11 +159,12 @@ __global__ void __launch_bounds__(kPqrThreads) pqr_kernel(PqrArgs a)
     if (!grid_barrier(a.bar, ++epoch * (unsigned)G, a.status, &flag)) return;
 
     for (int t = 0; t < a.k; ++t) {
-        if (threadIdx.x == 0) {
+        {
+            // global argmax of the per-CTA maxima, block-parallel
             double gv = -1.0;
             int64_t gi = -1;
             const int64_t base = (int64_t)(epoch & 1) * G;
-            for (int c = 0; c < G; ++c) {
+            for (int c = threadIdx.x; c < G; c += kPqrThreads) {
                 const double v = __ldcg(a.slot_val + base + c);
                 const int64_t i = __ldcg(a.slot_idx + base + c);
                 if (better(v, i, gv, gi)) {
@@ -169,9 +172,32 @@ __global__ void __launch_bounds__(kPqrThreads) pqr_kernel(PqrArgs a)
                     gi = i;
                 }
             }
-            piv_sh = (gi >= 0 && gv > 0.0) ? gi : -1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, gv, o);
+                const int64_t oi = __shfl_xor_sync(0xffffffffu, gi, o);
+                if (better(ov, oi, gv, gi)) {
+                    gv = ov;
+                    gi = oi;
+                }
+            }
+            if (lane == 0) {
+                wv[warp] = gv;
+                wi[warp] = gi;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double fv = -1.0;
+                int64_t fi = -1;
+                for (int w = 0; w < kPqrWarps; ++w)
+                    if (better(wv[w], wi[w], fv, fi)) {
+                        fv = wv[w];
+                        fi = wi[w];
+                    }
+                piv_sh = (fi >= 0 && fv > 0.0) ? fi : -1;
+            }
+            __syncthreads();
         }
-        __syncthreads();
         const int64_t p = piv_sh;
         if (p < 0) {
             // every remaining column is (numerically) in the span already
@@ -187,16 +213,16 @@ __global__ void __launch_bounds__(kPqrThreads) pqr_kernel(PqrArgs a)
         // classical Gram-Schmidt against q_0 .. q_{t-1}, twice
         for (int pass = 0; pass < 2; ++pass) {
             for (int s = warp; s < t; s += kPqrWarps) {
-                const float* qv = a.Q + (int64_t)s * r;
+                const float* qv = Qs + (int64_t)s * r;
                 float d = 0.f;
-                for (int i = lane; i < r; i += 32) d = fmaf(__ldcg(qv + i), qs[i], d);
+                for (int i = lane; i < r; i += 32) d = fmaf(qv[i], qs[i], d);
                 d = warp_sum_f(d);
                 if (lane == 0) coef[s] = d;
             }
             __syncthreads();
             for (int i = threadIdx.x; i < r; i += kPqrThreads) {
                 float acc = qs[i];
-                for (int s = 0; s < t; ++s) acc = fmaf(-coef[s], __ldcg(a.Q + (int64_t)s * r + i), acc);
+                for (int s = 0; s < t; ++s) acc = fmaf(-coef[s], Qs[(int64_t)s * r + i], acc);
                 qs[i] = acc;
             }
             __syncthreads();
@@ -225,31 +251,41 @@ __global__ void __launch_bounds__(kPqrThreads) pqr_kernel(PqrArgs a)
         const float inv = (float)(1.0 / nq);
         for (int i = threadIdx.x; i < r; i += kPqrThreads) {
             qs[i] *= inv;
-            if (b == 0) a.Q[(int64_t)t * r + i] = qs[i];
+            Qs[(int64_t)t * r + i] = qs[i];
         }
         __syncthreads();
-        // row t of R for this CTA's columns; downdate their residual norms
+        // row t of R for this CTA's columns; downdate their residual norms.
+        // Four columns per warp iteration, their loads issued together.
         bv = -1.0;
         bi = -1;
-        for (int64_t j = c0 + warp; j < c1; j += kPqrWarps) {
-            const double cur = a.nrm[j];
-            if (cur == -INFINITY) {  // a pivot of an earlier step
-                if (a.R && lane == 0) a.R[(int64_t)t * a.N + j] = 0.f;
-                continue;
+        for (int64_t j0 = c0 + 4 * warp; j0 < c1; j0 += 4 * kPqrWarps) {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int i = lane; i < r; i += 32) {
+                const float qi = qs[i];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (j0 + u < c1) d[u] = fmaf(qi, a.X[(j0 + u) * a.ldx + i], d[u]);
             }
-            const float* x = a.X + j * a.ldx;
-            float d = 0.f;
-            for (int i = lane; i < r; i += 32) d = fmaf(qs[i], x[i], d);
-            d = warp_sum_f(d);
-            double nn = fmax(cur - (double)d * (double)d, 0.0);
-            if (j == p) nn = -INFINITY;
-            if (lane == 0) {
-                if (a.R) a.R[(int64_t)t * a.N + j] = d;
-                a.nrm[j] = nn;
-            }
-            if (j != p && better(nn, j, bv, bi)) {
-                bv = nn;
-                bi = j;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t j = j0 + u;
+                if (j >= c1) break;
+                const float du = warp_sum_f(d[u]);
+                const double cur = a.nrm[j];
+                if (cur == -INFINITY) {  // a pivot of an earlier step
+                    if (a.R && lane == 0) a.R[(int64_t)t * a.N + j] = 0.f;
+                    continue;
+                }
+                double nn = fmax(cur - (double)du * (double)du, 0.0);
+                if (j == p) nn = -INFINITY;
+                if (lane == 0) {
+                    if (a.R) a.R[(int64_t)t * a.N + j] = du;
+                    a.nrm[j] = nn;
+                }
+                if (j != p && better(nn, j, bv, bi)) {
+                    bv = nn;
+                    bi = j;
+                }
             }
         }
         block_argmax_to_slot(bv, bi, wv, wi, a, (int)((epoch + 1) & 1));
@@ -258,30 +294,44 @@ __global__ void __launch_bounds__(kPqrThreads) pqr_kernel(PqrArgs a)
 }
 
 // Z (k x N, row-major ld ldz): Z(:, piv[t]) = e_t; other columns solve
-// S11 z = R(:, j) with S11(a, b) = R(a, piv[b]) upper triangular.
-__global__ void __launch_bounds__(128) id_solve_kernel(const float* __restrict__ R, int64_t N, int k,
-                                                       const int* __restrict__ piv, float* __restrict__ Z,
-                                                       int64_t ldz, int* status)
+// S11 z = R(:, j) with S11(a, b) = R(a, piv[b]) upper triangular, by back
+// substitution: one warp per column, the lanes sharing each row's dot
+// product; z in shared memory (k floats per warp).
+constexpr int kSolveWarps = 4;
+__global__ void __launch_bounds__(32 * kSolveWarps) id_solve_kernel(const float* __restrict__ R, int64_t N, int k,
+                                                                     const int* __restrict__ piv,
+                                                                     float* __restrict__ Z, int64_t ldz, int* status)
 {
-    extern __shared__ int pv[];  // k pivots
+    extern __shared__ int pv[];  // k pivots, then kSolveWarps x k floats
+    float* zs = reinterpret_cast<float*>(pv + k);
     for (int t = threadIdx.x; t < k; t += blockDim.x) pv[t] = piv[t];
     __syncthreads();
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * kSolveWarps + warp;
     if (j >= N) return;
+    float* z = zs + warp * k;
     int pos = -1;
-    for (int t = 0; t < k; ++t)
+    for (int t = lane; t < k; t += 32)
         if (pv[t] == (int)j) pos = t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pos = max(pos, __shfl_xor_sync(0xffffffffu, pos, o));
     if (pos >= 0) {
-        for (int a = 0; a < k; ++a) Z[(int64_t)a * ldz + j] = (a == pos) ? 1.f : 0.f;
+        for (int a = lane; a < k; a += 32) Z[(int64_t)a * ldz + j] = (a == pos) ? 1.f : 0.f;
         return;
     }
     for (int a = k - 1; a >= 0; --a) {
-        float s = R[(int64_t)a * N + j];
-        for (int c = a + 1; c < k; ++c) s = fmaf(-__ldg(R + (int64_t)a * N + pv[c]), Z[(int64_t)c * ldz + j], s);
-        const float d = __ldg(R + (int64_t)a * N + pv[a]);
-        const float z = s / d;
-        if (!isfinite(z)) atomicExch(status, RSVDGB_ERR_BREAKDOWN);
-        Z[(int64_t)a * ldz + j] = z;
+        const float* Ra = R + (int64_t)a * N;
+        float s = 0.f;
+        for (int c = a + 1 + lane; c < k; c += 32) s = fmaf(__ldg(Ra + pv[c]), z[c], s);
+        s = warp_sum_f(s);
+        const float d = __ldg(Ra + pv[a]);
+        const float za = (__ldg(Ra + j) - s) / d;
+        if (lane == 0) {
+            z[a] = za;
+            Z[(int64_t)a * ldz + j] = za;
+            if (!isfinite(za)) atomicExch(status, RSVDGB_ERR_BREAKDOWN);
+        }
+        __syncwarp();
     }
 }
 
@@ -382,29 +432,33 @@ __global__ void piv_to_i64_kernel(const int* __restrict__ piv, int k, int64_t* _
 
 }  // namespace
 
-int pqr_max_ctas(int sm_count)
+int pqr_max_ctas(int sm_count, size_t smem)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pqr_kernel, kPqrThreads, 256 * sizeof(float)) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(pqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pqr_kernel, kPqrThreads, smem) != cudaSuccess)
         return 0;
     return std::min(per_sm, 4) * sm_count;
 }
 
 int launch_pqr(cudaStream_t s, int sm_count, const float* X, int64_t ldx, int r, int64_t N, int k, int* piv,
-               float* R, double* nrm, float* Q, double* slot_val, int64_t* slot_idx, int max_slots,
-               unsigned int* bar, int* status)
+               float* R, double* nrm, double* slot_val, int64_t* slot_idx, int max_slots, unsigned int* bar,
+               int* status)
 {
     if (r < 1 || r > 256 || k < 1 || k > r || k > 256 || N < k) return RSVDGB_ERR_INVALID_ARG;
-    const int cap = pqr_max_ctas(sm_count);
+    const size_t smem = ((size_t)r * k + r) * sizeof(float);
+    if (smem > 200 * 1024) return RSVDGB_ERR_UNSUPPORTED;
+    const int cap = pqr_max_ctas(sm_count, smem);
     if (cap <= 0) return RSVDGB_ERR_CUDA;
-    int G = (int)std::min<int64_t>(std::min<int64_t>(cap, max_slots / 2), ceil_div(N, 8));
+    // about 32 columns per CTA: fewer CTAs make the per-step barrier cheaper
+    int G = (int)std::min<int64_t>(std::min<int64_t>(cap, max_slots / 2), ceil_div(N, 32));
     G = std::max(G, 1);
     if (cudaMemsetAsync(bar, 0, sizeof(unsigned int), s) != cudaSuccess) return RSVDGB_ERR_CUDA;
-    PqrArgs a{X, ldx, r, N, k, piv, R, nrm, Q, slot_val, slot_idx, bar, status};
+    PqrArgs a{X, ldx, r, N, k, piv, R, nrm, slot_val, slot_idx, bar, status};
     void* params[] = {&a};
-    if (cudaLaunchCooperativeKernel((const void*)pqr_kernel, dim3(G), dim3(kPqrThreads), params,
-                                    (size_t)r * sizeof(float), s) != cudaSuccess)
+    if (cudaLaunchCooperativeKernel((const void*)pqr_kernel, dim3(G), dim3(kPqrThreads), params, smem, s) !=
+        cudaSuccess)
         return RSVDGB_ERR_CUDA;
     count_launches();
     return RSVDGB_OK;
@@ -413,7 +467,9 @@ int launch_pqr(cudaStream_t s, int sm_count, const float* X, int64_t ldx, int r,
 void launch_id_solve(cudaStream_t s, const float* R, int64_t N, int k, const int* piv, float* Z, int64_t ldz,
                      int* status)
 {
-    id_solve_kernel<<<(unsigned)ceil_div(N, 128), 128, (size_t)k * sizeof(int), s>>>(R, N, k, piv, Z, ldz, status);
+    const size_t smem = (size_t)k * sizeof(int) + (size_t)kSolveWarps * k * sizeof(float);
+    id_solve_kernel<<<(unsigned)ceil_div(N, kSolveWarps), 32 * kSolveWarps, smem, s>>>(R, N, k, piv, Z, ldz,
+                                                                                        status);
     count_launches();
 }
 

@@ -138,7 +138,7 @@ struct Work {
     double *hpart, *fpart;
     float* hvec;  // correction vector h of the current pass
     // interpolative / CUR decompositions
-    float *Xb, *Rk, *Zw, *Qp, *Cw;
+    float *Xb, *Rk, *Zw, *Cw;
     double *pnrm, *slot_v;
     int64_t* slot_i;
     int* piv;
@@ -234,7 +234,7 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w, int L_lo = 0)
     w.spart = nullptr;
     w.hpart = w.fpart = nullptr;
     w.hvec = nullptr;
-    w.Xb = w.Rk = w.Zw = w.Qp = w.Cw = nullptr;
+    w.Xb = w.Rk = w.Zw = w.Cw = nullptr;
     w.pnrm = w.slot_v = nullptr;
     w.slot_i = nullptr;
     w.piv = nullptr;
@@ -244,7 +244,6 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w, int L_lo = 0)
         w.Xb = c.take<float>(L * g.n);
         w.Rk = c.take<float>((size_t)kk * g.n);
         w.Zw = c.take<float>((size_t)kk * g.n);
-        w.Qp = c.take<float>((size_t)256 * kk);
         w.pnrm = c.take<double>(std::max(g.m, g.n));
         w.slot_v = c.take<double>(kPqrSlots);
         w.slot_i = c.take<int64_t>(kPqrSlots);
@@ -642,8 +641,8 @@ int rid_tail(rsvdgb_handle* h, const Geom& g, Work& w, int k, const RidSpec& r)
     const int l = g.l;
     // B (l x n, column j contiguous) from B^T
     launch_transpose_cm(s, w.Wt, g.ldn, g.n, l, w.Xb, g.L);
-    int rc = launch_pqr(s, sm, w.Xb, g.L, l, g.n, k, w.piv, w.Rk, w.pnrm, w.Qp, w.slot_v, w.slot_i, kPqrSlots,
-                        w.bar, w.status);
+    int rc = launch_pqr(s, sm, w.Xb, g.L, l, g.n, k, w.piv, w.Rk, w.pnrm, w.slot_v, w.slot_i, kPqrSlots, w.bar,
+                        w.status);
     if (rc) return rc;
     float* Z = r.Z ? r.Z : w.Zw;
     const int64_t ldz = r.Z ? r.ldz : g.n;
@@ -654,8 +653,8 @@ int rid_tail(rsvdgb_handle* h, const Geom& g, Work& w, int k, const RidSpec& r)
     if (C) launch_gather_cols(s, g.A, g.lda, g.a_bf16, g.trans, g.m, w.piv, k, C, ldc);
     if (!r.cur) return RSVDGB_OK;
     // row pivots: the pivoted QR of C^T (k x m; its column i is row i of C)
-    rc = launch_pqr(s, sm, C, ldc, k, g.m, k, w.piv + k, nullptr, w.pnrm, w.Qp, w.slot_v, w.slot_i, kPqrSlots,
-                    w.bar, w.status);
+    rc = launch_pqr(s, sm, C, ldc, k, g.m, k, w.piv + k, nullptr, w.pnrm, w.slot_v, w.slot_i, kPqrSlots, w.bar,
+                    w.status);
     if (rc) return rc;
     launch_piv_to_i64(s, w.piv + k, k, r.I);
     // R = A(I, :) and R^T (n x k column-major, zero beyond column k) in Wt
