@@ -46,11 +46,13 @@ WORKLOADS = {
 }
 
 # DRAM bytes (read + write) per byte of A of the FP32 tensor-core pass kernel,
-# from one ncu capture on the 50000 x 2000 workload (profiles/tc_kernels_spiked50k.md):
-# A-side pass 410.2 + 49.0 MB, A^T-side pass 445.2 + 3.1 MB per 400 MB of A.  The
-# traffic scales with the rows processed, so the full-size launch carries the
-# same ratio.  Set to None when the pass kernel changes.
-TC_PASS_TRAFFIC_PER_A_BYTE = ((410.2 + 49.0) + (445.2 + 3.1)) / (2 * 400.0)
+# averaged over the six passes of one rSVD, from one ncu capture on the
+# 50000 x 2000 workload (profiles/tc_kernels_spiked50k.md): sketch 410.2 + 48.1,
+# A-side power passes 410.2 + 48.7, A^T-side power passes 445.2 + 3.5, chunked
+# projection 473.8 + 44.5 MB per 400 MB of A.  The traffic scales with the rows
+# processed, so the full-size launches carry the same ratio.  Set to None when
+# the pass kernel changes.
+TC_PASS_TRAFFIC_PER_A_BYTE = ((410.2 + 48.1) + 2 * (410.2 + 48.7) + 2 * (445.2 + 3.5) + (473.8 + 44.5)) / (6 * 400.0)
 
 # FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 SIMT_FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
