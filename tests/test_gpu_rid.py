@@ -165,3 +165,31 @@ def test_rid_rcur_argument_errors(rs, handle):
     rc = lib.rsvdgb_rcur(handle.ptr, A2.data_ptr(), 300, 100, 100, 0, 5, ctypes.byref(o), None, 5, None, 5, None,
                          100, J.data_ptr(), None, None)
     assert rc == rs.RSVDGB_ERR_INVALID_ARG
+
+
+def test_rid_rcur_full_size_properties(rs, handle):
+    """200000 x 2000 (the benchmark's matrix), k = 100, p = 10, q = 2: C and
+    R are bit-exact gathers, Z(:, J) = I, the indices are distinct, and the
+    ID / CUR errors stay within a small factor of the rank-k rSVD error of
+    the same matrix (an ID is not optimal, Sec. 7)."""
+    import torch
+    m, n, k = 200000, 2000, 100
+    A = inputs.spiked_noise(m, n, 1.0 / np.arange(1, n + 1), 1e-3, seed=0x160802148 + 2000, device="cuda")
+    o = rs.make_opts(p=10, q=2, seed=2)
+    r = rs.rsvdgb_rid(handle, A, k, opts=o)
+    c = rs.rsvdgb_rcur(handle, A, k, opts=o)
+    d, U, V, info = rs.rsvdgb_rsvd(handle, A, k, opts=o)
+    torch.cuda.synchronize()
+    assert r["info"].status == 0 and c["info"].status == 0 and info.status == 0
+    J = r["J"]
+    assert torch.unique(J).numel() == k and torch.unique(c["I"]).numel() == k
+    assert torch.equal(r["C"], A[:, J])
+    assert torch.equal(c["R"], A[c["I"], :])
+    Z = r["Z"]
+    assert torch.equal(Z[:, J], torch.eye(k, device="cuda"))
+    A64 = A.double()
+    e_svd = float(torch.linalg.matrix_norm(A64 - (U.double() * d.double()) @ V.double().T))
+    e_id = float(torch.linalg.matrix_norm(A64 - r["C"].double() @ Z.double()))
+    e_cur = float(torch.linalg.matrix_norm(A64 - c["C"].double() @ c["U"].double() @ c["R"].double()))
+    assert e_svd <= e_id <= 3.0 * e_svd, (e_id, e_svd)
+    assert e_svd <= e_cur <= 3.0 * e_svd, (e_cur, e_svd)
