@@ -291,6 +291,72 @@ def rcur(A: np.ndarray, k: int, p: int = 10, q: int = 0, sdist: str = "normal", 
     return C, U, R, J, I
 
 
+def soft_threshold(X, tau):
+    """Elementwise shrinkage sign(x) max(|x| - tau, 0) (Algorithm rrpca
+    steps 8 and 10)."""
+    return np.sign(X) * np.maximum(np.abs(X) - tau, 0.0)
+
+
+def predict_rank(d, inv_mu, k, kmax, n_small):
+    """Rank prediction of the inexact augmented Lagrange multiplier method
+    (the rrpca step 7 the paper delegates to it): svp = number of computed
+    singular values above 1/mu; the next target rank is svp + 1 if svp < k,
+    else svp + round(0.05 min(m, n)), capped at kmax.  Returns (next k, svp)."""
+    svp = int(np.sum(d > inv_mu))
+    nk = svp + 1 if svp < k else svp + int(round(0.05 * n_small))
+    return max(1, min(nk, kmax)), svp
+
+
+def rrpca(A: np.ndarray, lam=None, maxiter: int = 50, tol: float = 1e-5, p: int = 10, q: int = 2, k0: int = 2,
+          rho: float = 1.5, seed: int = 0, sdist: str = "normal", svd=None):
+    """Algorithm rrpca (Sec. 5.2): robust PCA A = L + S by the inexact
+    augmented Lagrange multiplier method with a randomized SVD, in FP64.
+
+    Readings where the paper is garbled or silent (following the IALM method
+    it cites): mu_0 = 1.25 / ||A||_2 (numpy's 2-norm), multiplier
+    Z_0 = A / max(||A||_2, max|a_ij| / lambda), lambda = max(m, n)^(-1/2) by
+    default, mu <- min(rho mu, 1e7 mu_0), target rank from predict_rank, stop
+    when ||A - L - S||_F <= tol ||A||_F or after maxiter iterations.  Each
+    iteration's rSVD uses the test matrix of seed + iteration.  svd (for the
+    pins) replaces the randomized SVD by a callable (X, k) -> (d, U, V).
+    Returns dict L, S, iters, err, k, svp, mu."""
+    M = values(A)
+    m, n = M.shape
+    ns = min(m, n)
+    if lam is None:
+        lam = 1.0 / math.sqrt(max(m, n))
+    norm2 = float(np.linalg.norm(M, 2))
+    mu = 1.25 / norm2
+    mu_bar = mu * 1e7
+    Z = M / max(norm2, float(np.abs(M).max()) / lam)
+    S = np.zeros_like(M)
+    L = np.zeros_like(M)
+    normM = float(np.linalg.norm(M))
+    kmax = min(ns - 1, 224 - p)
+    k = min(k0, kmax)
+    err = float("inf")
+    svp = 0
+    it = 0
+    for it in range(1, maxiter + 1):
+        X = np.ascontiguousarray(M - S + Z / mu)
+        if svd is None:
+            d, U, V = rsvd(X, k, p=p, q=q, sdist=sdist, seed=seed + it)
+        else:
+            d, U, V = svd(X, k)
+        k_next, svp = predict_rank(d, 1.0 / mu, k, kmax, ns)
+        ds = np.maximum(d[:svp] - 1.0 / mu, 0.0)
+        L = (U[:, :svp] * ds[None, :]) @ V[:, :svp].T
+        S = soft_threshold(M - L + Z / mu, lam / mu)
+        R = M - L - S
+        Z = Z + mu * R
+        mu = min(rho * mu, mu_bar)
+        err = float(np.linalg.norm(R)) / normM
+        k = k_next
+        if err < tol:
+            break
+    return {"L": L, "S": S, "iters": it, "err": err, "k": k, "svp": svp, "mu": mu}
+
+
 def power_direct(A: np.ndarray, l: int, q: int, sdist: str = "normal", seed: int = 0) -> np.ndarray:
     """Algorithm poweriter_direct: Y = (A A^T)^q A Omega (m >= n)."""
     ptr, code, m, n, lda = _amat(A)

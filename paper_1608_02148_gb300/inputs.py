@@ -232,3 +232,19 @@ def pca_data(m: int, n: int, rank: int, seed: int, decay: float = 0.85, noise_st
     if zero_var_cols > 0:
         A[:, n - zero_var_cols:] = mu[None, n - zero_var_cols:]
     return A.contiguous()
+
+
+def low_rank_plus_sparse(m: int, n: int, rank: int, density: float, seed: int, magnitude: float = 1.0):
+    """A = L0 + S0 for robust PCA: L0 = F G^T / sqrt(rank) with F (m x rank)
+    and G (n x rank) i.i.d. N(0, 1), so the entries of L0 are N(0, 1); S0
+    holds gross corruptions on a random fraction `density` of the entries,
+    uniform in [-5 magnitude, 5 magnitude], zero elsewhere.  float64 numpy
+    (L0, S0, A).  The robust-PCA example of Sec. 5 (a 300 x 300 rank-5
+    matrix with 20 % corrupted entries) is low_rank_plus_sparse(300, 300, 5, 0.2, seed)."""
+    rng = np.random.default_rng(seed)
+    F = rng.standard_normal((m, rank))
+    G = rng.standard_normal((n, rank))
+    L0 = F @ G.T / math.sqrt(rank)
+    mask = rng.random((m, n)) < density
+    S0 = np.where(mask, rng.uniform(-5.0 * magnitude, 5.0 * magnitude, (m, n)), 0.0)
+    return L0, S0, L0 + S0
