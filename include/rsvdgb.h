@@ -237,6 +237,50 @@ int rsvdgb_rcur(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t l
                 const rsvdgb_opts* opts, float* C, int64_t ldc, float* U, int64_t ldu, float* R, int64_t ldr,
                 int64_t* J, int64_t* I, rsvdgb_info* info);
 
+/* Options of rsvdgb_rrpca (Algorithm rrpca, Sec. 5.2). */
+typedef struct rsvdgb_rrpca_opts {
+    float lambda;     /* weight of ||S||_1; <= 0: 1 / sqrt(max(m, n)) (Sec. 5)       */
+    float tol;        /* stop when ||A - L - S||_F <= tol ||A||_F; default 1e-5     */
+    float rho;        /* mu <- min(rho mu, 1e7 mu_0) per iteration; default 1.5     */
+    int32_t maxiter;  /* default 50                                                 */
+    int32_t k0;       /* initial target rank; default 2 (Algorithm rrpca step 1)    */
+    int32_t reserved[3];
+} rsvdgb_rrpca_opts;
+
+/* Host-side report of rsvdgb_rrpca. */
+typedef struct rsvdgb_rrpca_result {
+    int32_t iters;    /* iterations run                                   */
+    int32_t rank;     /* singular values kept in L at the last iteration  */
+    int32_t k_next;   /* predicted target rank after the last iteration   */
+    int32_t status;   /* RSVDGB_OK or the device status of an rSVD        */
+    double err;       /* ||A - L - S||_F / ||A||_F at the last iteration  */
+    double mu;        /* penalty parameter after the last iteration       */
+    double reserved[2];
+} rsvdgb_rrpca_result;
+
+void rsvdgb_default_rrpca_opts(rsvdgb_rrpca_opts* o);
+
+/*
+ * rrpca(A, lambda, maxiter, tol, p, q) of Sec. 5.4 -- Algorithm rrpca: robust
+ * PCA A = L + S (low-rank plus sparse) by the inexact augmented Lagrange
+ * multiplier method with one randomized SVD (rsvdgb_rsvd, opts' p and q,
+ * Omega seed opts->seed + iteration) per iteration.
+ *   A      device float, m x n row-major (lda >= n; opts->layout must be
+ *          row-major, dtype FP32).  Read only.
+ *   L, S   device float, m x n row-major (ldl, lds >= n): the low-rank and the
+ *          sparse part.  S is required (it holds the iterate); L may be NULL.
+ *   res    host rsvdgb_rrpca_result or NULL.
+ * Readings of the steps the paper leaves to the cited method: mu_0 = 1.25 /
+ * ||A||_2 (||A||_2 from a rank-1 rSVD of A), Z_0 = A / max(||A||_2,
+ * max|a_ij| / lambda), target rank predicted from the number of singular
+ * values above 1/mu (next = that + 1 when it is below the target, else
+ * that + 5 % of min(m, n)), capped so that k + p <= 224.  The loop runs on
+ * the host and synchronises the handle's stream twice per iteration.
+ * Returns RSVDGB_OK, an argument / CUDA error, or the status of an rSVD.
+ */
+int rsvdgb_rrpca(rsvdgb_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, const rsvdgb_rrpca_opts* ro,
+                 const rsvdgb_opts* opts, float* L, int64_t ldl, float* S, int64_t lds, rsvdgb_rrpca_result* res);
+
 /* One matrix of a batch: device pointer to A (m x n row-major, lda >= n). */
 typedef struct rsvdgb_matrix_desc {
     const void* A;

@@ -251,6 +251,21 @@ void launch_transpose_cm(cudaStream_t s, const float* Bt, int64_t ldb, int64_t N
 void launch_zq(cudaStream_t s, const float* Z, int64_t ldz, const float* Q, int64_t ldq, int64_t N, int k, float* W);
 void launch_piv_to_i64(cudaStream_t s, const int* piv, int k, int64_t* out);
 
+// Robust PCA (rrpca.cu).
+int64_t ialm_blocks(int64_t m, int64_t n);
+// *amax (bits of max|a|, start from 0) and *sumsq = ||A||_F^2 (part: nblocks doubles).
+void launch_absmax_sumsq(cudaStream_t s, const float* A, int64_t lda, int64_t m, int64_t n, unsigned int* amax,
+                         double* part, int nblocks, double* sumsq);
+// Z = A / dual, S = 0, X = A + Z / mu0 (Z, X: m x n with ld n).
+void launch_ialm_init(cudaStream_t s, const float* A, int64_t lda, int64_t m, int64_t n, float inv_dual,
+                      float inv_mu0, float* S, int64_t lds, float* Z, float* X);
+// One fused IALM update (mode 0; *err2 = ||A - L - S||_F^2, part: ialm_blocks
+// doubles) or the reconstruction of L = U diag(sig) V^T into Lout (mode 1).
+void launch_ialm_step(cudaStream_t s, const float* A, int64_t lda, int64_t m, int64_t n, const float* U, int64_t ldu,
+                      const float* V, int64_t ldv, const float* sig, int kl, float mu, float inv_mu,
+                      float inv_mu_next, float thr, float* S, int64_t lds, float* Z, float* X, double* part,
+                      double* err2, int mode, float* Lout, int64_t ldl);
+
 // Batched rSVD (batched.cu): plan cache owned by the handle.
 struct BatchedPlan;
 void destroy_plan(BatchedPlan* pl);

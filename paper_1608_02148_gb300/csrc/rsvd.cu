@@ -57,6 +57,8 @@ struct rsvdgb_handle {
     size_t ws_bytes = 0;
     void* host_stage = nullptr;  // device buffers for the *_host entry points
     size_t host_stage_bytes = 0;
+    void* aux = nullptr;  // iterates of rsvdgb_rrpca (kept apart from ws, which its rSVDs resize)
+    size_t aux_bytes = 0;
     PassProfile prof;
     BatchedPlan* batched = nullptr;  // plan of the last batch layout
     float* ctl_params = nullptr;     // learned (q, p) controller (device, kMlpParams floats)
@@ -953,6 +955,7 @@ int rsvdgb_destroy(rsvdgb_handle* h)
     cudaStreamSynchronize(h->stream);
     if (h->ws) cudaFree(h->ws);
     if (h->host_stage) cudaFree(h->host_stage);
+    if (h->aux) cudaFree(h->aux);
     for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
     destroy_plan(h->batched);
     if (h->ctl_params) cudaFree(h->ctl_params);
@@ -1037,23 +1040,26 @@ int rsvdgb_rqb(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t ld
 }  // extern "C"
 
 namespace {
-// Device staging buffer of the *_host entry points (grows on demand).
-int ensure_host_stage(rsvdgb_handle* h, size_t bytes)
+// A handle-owned device buffer that grows on demand.
+int ensure_buffer(rsvdgb_handle* h, void** buf, size_t* have, size_t bytes)
 {
-    if (bytes <= h->host_stage_bytes) return RSVDGB_OK;
-    if (h->host_stage) {
+    if (bytes <= *have) return RSVDGB_OK;
+    if (*buf) {
         cudaStreamSynchronize(h->stream);
-        cudaFree(h->host_stage);
-        h->host_stage = nullptr;
-        h->host_stage_bytes = 0;
+        cudaFree(*buf);
+        *buf = nullptr;
+        *have = 0;
     }
-    if (cudaMalloc(&h->host_stage, bytes) != cudaSuccess) {
+    if (cudaMalloc(buf, bytes) != cudaSuccess) {
         cudaGetLastError();
         return RSVDGB_ERR_NOMEM;
     }
-    h->host_stage_bytes = bytes;
+    *have = bytes;
     return RSVDGB_OK;
 }
+
+// Device staging buffer of the *_host entry points.
+int ensure_host_stage(rsvdgb_handle* h, size_t bytes) { return ensure_buffer(h, &h->host_stage, &h->host_stage_bytes, bytes); }
 }  // namespace
 
 extern "C" {
@@ -1257,6 +1263,140 @@ int rsvdgb_rcur(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t l
 {
     const RidSpec r{true, C, ldc, nullptr, 0, J, U, ldu, R, ldr, I};
     return rid_common(h, A, m, n, lda, dtype, k, opts, r, info);
+}
+
+void rsvdgb_default_rrpca_opts(rsvdgb_rrpca_opts* o)
+{
+    if (!o) return;
+    *o = rsvdgb_rrpca_opts{};
+    o->lambda = 0.f;
+    o->tol = 1e-5f;
+    o->rho = 1.5f;
+    o->maxiter = 50;
+    o->k0 = 2;
+}
+
+int rsvdgb_rrpca(rsvdgb_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, const rsvdgb_rrpca_opts* ro_in,
+                 const rsvdgb_opts* opts, float* L, int64_t ldl, float* S, int64_t lds, rsvdgb_rrpca_result* res)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    rsvdgb_opts o;
+    if (opts)
+        o = *opts;
+    else
+        rsvdgb_default_opts(&o);
+    rsvdgb_rrpca_opts ro;
+    if (ro_in)
+        ro = *ro_in;
+    else
+        rsvdgb_default_rrpca_opts(&ro);
+    if (!A || !S || m < 2 || n < 2 || lda < n || lds < n || (L && ldl < n)) return RSVDGB_ERR_INVALID_ARG;
+    if (ro.maxiter < 1 || !(ro.tol > 0.f) || !(ro.rho >= 1.f) || ro.k0 < 1 || o.p < 0 || o.q < 0)
+        return RSVDGB_ERR_INVALID_ARG;
+    if (o.layout != RSVDGB_ROW_MAJOR || o.q_mode != RSVDGB_Q_FIXED) return RSVDGB_ERR_UNSUPPORTED;
+    if (!aligned(A, 4) || !aligned(S, 4)) return RSVDGB_ERR_INVALID_ARG;
+    const int64_t ns = std::min(m, n);
+    const int kmax = (int)std::min<int64_t>(ns - 1, kMaxL - o.p);
+    if (kmax < 1) return RSVDGB_ERR_UNSUPPORTED;
+    const cudaStream_t s = h->stream;
+    const int nb_abs = 4 * h->sm_count;
+    const int64_t nb = std::max<int64_t>(ialm_blocks(m, n), nb_abs);
+    // aux: Z, X (m x n), U (m x kmax), V (n x kmax), d, sig, partial sums, scalars, rSVD info
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (size_t)round_up((int64_t)off, 256);
+        size_t at = off;
+        off += bytes;
+        return at;
+    };
+    const size_t oZ = take((size_t)m * n * 4), oX = take((size_t)m * n * 4), oU = take((size_t)m * kmax * 4),
+                 oV = take((size_t)n * kmax * 4), oD = take((size_t)kmax * 4 + 64), oSig = take((size_t)kmax * 4),
+                 oPart = take((size_t)nb * 8), oE = take(8), oSq = take(8), oMax = take(4),
+                 oInfo = take(sizeof(rsvdgb_info));
+    rc = ensure_buffer(h, &h->aux, &h->aux_bytes, off);
+    if (rc) return rc;
+    char* base = (char*)h->aux;
+    float *Z = (float*)(base + oZ), *X = (float*)(base + oX), *U = (float*)(base + oU), *V = (float*)(base + oV),
+          *d = (float*)(base + oD), *sig = (float*)(base + oSig);
+    double *part = (double*)(base + oPart), *err2 = (double*)(base + oE), *sumsq = (double*)(base + oSq);
+    unsigned int* amax = (unsigned int*)(base + oMax);
+    rsvdgb_info* dinfo = (rsvdgb_info*)(base + oInfo);
+
+    // ||A||_2 from a rank-1 rSVD, max |a_ij| and ||A||_F
+    rc = rsvdgb_rsvd(h, A, m, n, lda, RSVDGB_F32, 1, 1, 1, &o, d, U, kmax, V, kmax, dinfo);
+    if (rc) return rc;
+    RSVDGB_CUDA_TRY(cudaMemsetAsync(amax, 0, 4, s));
+    launch_absmax_sumsq(s, A, lda, m, n, amax, part, nb_abs, sumsq);
+    float h_norm2 = 0.f;
+    unsigned int h_amax = 0;
+    double h_sumsq = 0.0;
+    RSVDGB_CUDA_TRY(cudaMemcpyAsync(&h_norm2, d, 4, cudaMemcpyDeviceToHost, s));
+    RSVDGB_CUDA_TRY(cudaMemcpyAsync(&h_amax, amax, 4, cudaMemcpyDeviceToHost, s));
+    RSVDGB_CUDA_TRY(cudaMemcpyAsync(&h_sumsq, sumsq, 8, cudaMemcpyDeviceToHost, s));
+    RSVDGB_CUDA_TRY(cudaStreamSynchronize(s));
+    float maxabs;
+    std::memcpy(&maxabs, &h_amax, 4);
+    const double normA = std::sqrt(h_sumsq);
+    const double norm2 = (double)h_norm2;
+    if (!(norm2 > 0.0) || !(normA > 0.0)) return RSVDGB_ERR_INVALID_ARG;  // A = 0
+    const double lam = ro.lambda > 0.f ? (double)ro.lambda : 1.0 / std::sqrt((double)std::max(m, n));
+    double mu = 1.25 / norm2;
+    const double mu_bar = 1e7 * mu;
+    const double dual = std::max(norm2, (double)maxabs / lam);
+    launch_ialm_init(s, A, lda, m, n, (float)(1.0 / dual), (float)(1.0 / mu), S, lds, Z, X);
+
+    int k = std::min(ro.k0, kmax), svp = 0, it = 0, status = RSVDGB_OK;
+    double err = 0.0;
+    std::vector<float> hd(kmax), hsig(kmax);
+    for (it = 1; it <= ro.maxiter; ++it) {
+        rsvdgb_opts oi = o;
+        oi.seed = o.seed + (uint64_t)it;
+        rc = rsvdgb_rsvd(h, X, m, n, n, RSVDGB_F32, k, k, k, &oi, d, U, kmax, V, kmax, dinfo);
+        if (rc) return rc;
+        rsvdgb_info hinfo;
+        RSVDGB_CUDA_TRY(cudaMemcpyAsync(hd.data(), d, sizeof(float) * k, cudaMemcpyDeviceToHost, s));
+        RSVDGB_CUDA_TRY(cudaMemcpyAsync(&hinfo, dinfo, sizeof(hinfo), cudaMemcpyDeviceToHost, s));
+        RSVDGB_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hinfo.status != RSVDGB_OK) {
+            status = hinfo.status;
+            break;
+        }
+        // predicted rank: singular values above 1/mu are kept, shrunk by 1/mu
+        const double inv_mu = 1.0 / mu;
+        svp = 0;
+        for (int t = 0; t < k; ++t) svp += (double)hd[t] > inv_mu;
+        int knext = svp < k ? svp + 1 : svp + (int)std::lround(0.05 * (double)ns);
+        knext = std::max(1, std::min(knext, kmax));
+        for (int t = 0; t < svp; ++t) hsig[t] = (float)std::max((double)hd[t] - inv_mu, 0.0);
+        if (svp > 0) RSVDGB_CUDA_TRY(cudaMemcpyAsync(sig, hsig.data(), sizeof(float) * svp, cudaMemcpyHostToDevice, s));
+        const double mu_next = std::min(ro.rho * mu, mu_bar);
+        launch_ialm_step(s, A, lda, m, n, U, kmax, V, kmax, sig, svp, (float)mu, (float)inv_mu, (float)(1.0 / mu_next),
+                         (float)(lam * inv_mu), S, lds, Z, X, part, err2, 0, nullptr, 0);
+        double he2 = 0.0;
+        RSVDGB_CUDA_TRY(cudaMemcpyAsync(&he2, err2, 8, cudaMemcpyDeviceToHost, s));
+        RSVDGB_CUDA_TRY(cudaStreamSynchronize(s));
+        err = std::sqrt(he2) / normA;
+        mu = mu_next;
+        k = knext;
+        if (err < (double)ro.tol) break;
+    }
+    if (it > ro.maxiter) it = ro.maxiter;
+    if (L && status == RSVDGB_OK)
+        launch_ialm_step(s, A, lda, m, n, U, kmax, V, kmax, sig, svp, 0.f, 0.f, 0.f, 0.f, nullptr, 0, nullptr, nullptr,
+                         nullptr, nullptr, 1, L, ldl);
+    RSVDGB_CUDA_TRY(cudaGetLastError());
+    RSVDGB_CUDA_TRY(cudaStreamSynchronize(s));
+    if (res) {
+        *res = rsvdgb_rrpca_result{};
+        res->iters = it;
+        res->rank = svp;
+        res->k_next = k;
+        res->status = status;
+        res->err = err;
+        res->mu = mu;
+    }
+    return status;
 }
 
 int rsvdgb_omega(rsvdgb_handle* h, int64_t rows, int l, uint64_t seed, int sdist, float* out, int64_t ld)

@@ -31,7 +31,8 @@ EXPORTS = ["rsvdgb_create", "rsvdgb_destroy", "rsvdgb_set_stream", "rsvdgb_defau
            "rsvdgb_kernel_launches", "rsvdgb_pass_atx_noalloc", "rsvdgb_rsvd_batched",
            "rsvdgb_default_train_opts", "rsvdgb_controller_load", "rsvdgb_controller_set",
            "rsvdgb_controller_train", "rsvdgb_controller_features", "rsvdgb_mlp_forward", "rsvdgb_mlp_grad",
-           "rsvdgb_rpca", "rsvdgb_rpca_host", "rsvdgb_rid", "rsvdgb_rcur"]
+           "rsvdgb_rpca", "rsvdgb_rpca_host", "rsvdgb_rid", "rsvdgb_rcur", "rsvdgb_default_rrpca_opts",
+           "rsvdgb_rrpca"]
 
 Q_MODE = {"fixed": 0, "learned": 1}
 MLP_PARAMS = 5410  # RSVDGB_MLP_PARAMS
@@ -47,6 +48,17 @@ class RsvdgbOpts(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("layout", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("q_mode", ctypes.c_int32), ("p_max", ctypes.c_int32), ("q_max", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 3)]
+
+
+class RsvdgbRrpcaOpts(ctypes.Structure):
+    _fields_ = [("lam", ctypes.c_float), ("tol", ctypes.c_float), ("rho", ctypes.c_float),
+                ("maxiter", ctypes.c_int32), ("k0", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class RsvdgbRrpcaResult(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("rank", ctypes.c_int32), ("k_next", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("err", ctypes.c_double), ("mu", ctypes.c_double),
+                ("reserved", ctypes.c_double * 2)]
 
 
 class RsvdgbTrainOpts(ctypes.Structure):
@@ -110,6 +122,10 @@ def load(path: Path | str | None = None):
     pca_sig = [P, P, I64, I64, I64, I, I, I, I, ctypes.POINTER(RsvdgbOpts), P, I64, P, P, P, I64, P, P, P]
     lib.rsvdgb_rpca.argtypes = pca_sig
     lib.rsvdgb_rpca_host.argtypes = pca_sig
+    lib.rsvdgb_default_rrpca_opts.argtypes = [ctypes.POINTER(RsvdgbRrpcaOpts)]
+    lib.rsvdgb_default_rrpca_opts.restype = None
+    lib.rsvdgb_rrpca.argtypes = [P, P, I64, I64, I64, ctypes.POINTER(RsvdgbRrpcaOpts), ctypes.POINTER(RsvdgbOpts), P,
+                                 I64, P, I64, ctypes.POINTER(RsvdgbRrpcaResult)]
     lib.rsvdgb_rid.argtypes = [P, P, I64, I64, I64, I, I, ctypes.POINTER(RsvdgbOpts), P, I64, P, I64, P, P]
     lib.rsvdgb_rcur.argtypes = [P, P, I64, I64, I64, I, I, ctypes.POINTER(RsvdgbOpts), P, I64, P, I64, P, I64, P, P,
                                 P]
@@ -377,6 +393,31 @@ def rsvdgb_rcur(h: Handle, A, k, opts: RsvdgbOpts | None = None, idx_only=False,
                          R.data_ptr() if R is not None else None, n, J.data_ptr(), I_.data_ptr(), info.data_ptr())
     _check("rsvdgb_rcur", rc)
     return {"C": C, "U": U, "R": R, "J": J, "I": I_, "info": _info_from(info) if sync_info else info}
+
+
+def make_rrpca_opts(lam=None, tol=1e-5, rho=1.5, maxiter=50, k0=2) -> RsvdgbRrpcaOpts:
+    o = RsvdgbRrpcaOpts()
+    load().rsvdgb_default_rrpca_opts(ctypes.byref(o))
+    o.lam = 0.0 if lam is None else lam
+    o.tol, o.rho, o.maxiter, o.k0 = tol, rho, maxiter, k0
+    return o
+
+
+def rsvdgb_rrpca(h: Handle, A, ropts: RsvdgbRrpcaOpts | None = None, opts: RsvdgbOpts | None = None, want_L=True):
+    """rrpca(A, lambda, maxiter, tol, p, q) on a row-major FP32 device tensor:
+    returns dict L (or None), S, result (iters, rank, err, mu, status)."""
+    torch = _torch()
+    lib = load()
+    opts = opts or make_opts()
+    ropts = ropts or make_rrpca_opts()
+    m, n = A.shape
+    S = torch.empty(m, n, dtype=torch.float32, device=A.device)
+    L = torch.empty(m, n, dtype=torch.float32, device=A.device) if want_L else None
+    res = RsvdgbRrpcaResult()
+    rc = lib.rsvdgb_rrpca(h.ptr, A.data_ptr(), m, n, _rowmajor_ld(A), ctypes.byref(ropts), ctypes.byref(opts),
+                          L.data_ptr() if L is not None else None, n, S.data_ptr(), n, ctypes.byref(res))
+    _check("rsvdgb_rrpca", rc)
+    return {"L": L, "S": S, "result": res}
 
 
 def rsvdgb_rqb(h: Handle, A, k, opts: RsvdgbOpts | None = None):
