@@ -547,6 +547,31 @@ def main():
     except Exception as exc:  # a variant the build does not serve
         variants = {other: {"unavailable": str(exc)}}
 
+    # ---------------- the other test matrices of Sec. 2.3 on the same A ----------------
+    if args.variants:
+        for sd in ("unif", "rademacher"):
+            try:
+                o4 = rs.make_opts(p=wl["p"], q=wl["q"], seed=rank, prec=args.prec, engine=args.engine, sdist=sd)
+                for _ in range(2):
+                    rs.rsvdgb_rsvd(h, A, k, opts=o4, out=bufs, sync_info=False)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                nv = max(3, args.steps // 2)
+                e0.record(stream)
+                for _ in range(nv):
+                    rs.rsvdgb_rsvd(h, A, k, opts=o4, out=bufs, sync_info=False)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                info4 = rs._info_from(bufs[3])
+                err_main = float(np.sqrt(max(info.err2_k, 0.0)))
+                err4 = float(np.sqrt(max(info4.err2_k, 0.0)))
+                variants[f"{args.prec}_omega_{sd}"] = {
+                    "ms": e0.elapsed_time(e1) / nv, "err_k_fro": err4,
+                    "err_ratio_vs_" + args.prec: err4 / err_main if err_main > 0 else None}
+            except Exception as exc:
+                variants[f"{args.prec}_omega_{sd}"] = {"unavailable": str(exc)}
+
     # ---------------- learned (q, p) on the same A: the packaged controller ----------------
     ctl_path = os.path.join(ROOT, "paper_1608_02148_gb300", "controller_default.bin")
     if os.path.exists(ctl_path) and args.variants:
