@@ -248,3 +248,13 @@ def low_rank_plus_sparse(m: int, n: int, rank: int, density: float, seed: int, m
     mask = rng.random((m, n)) < density
     S0 = np.where(mask, rng.uniform(-5.0 * magnitude, 5.0 * magnitude, (m, n)), 0.0)
     return L0, S0, L0 + S0
+
+
+def rrpca_example(seed: int, m: int = 300, n: int = 300, rank: int = 5, density: float = 0.2):
+    """The robust-PCA simulation of Sec. 5.5: L = L1 L2 with L1 (m x rank) and
+    L2 (rank x n) i.i.d. N(0, 1); S i.i.d. uniform on [-500, 500] kept with
+    probability 0.2 (Bernoulli mask); A = L + S.  float64 numpy (L, S, A)."""
+    rng = np.random.default_rng(seed)
+    L = rng.standard_normal((m, rank)) @ rng.standard_normal((rank, n))
+    S = rng.uniform(-500.0, 500.0, (m, n)) * (rng.random((m, n)) < density)
+    return L, S, L + S

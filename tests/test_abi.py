@@ -66,3 +66,34 @@ def test_status_strings_and_sketch_width(lib):
 def test_null_handle_is_rejected_without_gpu(lib):
     assert lib.rsvdgb_destroy(None) == 1
     assert lib.rsvdgb_rsvd(None, None, 10, 10, 10, 0, 2, 2, 2, None, None, None, 0, None, 0, None) == 1
+
+
+def test_rrpca_structs_and_defaults(lib):
+    """rrpca(A, lambda = NULL, maxiter = 50, tol = 1e-5, p = 10, q = 2) of
+    Sec. 5.4; k = 2 at the start (Algorithm rrpca step 1)."""
+    from paper_1608_02148_gb300 import rsvdgb
+    assert ctypes.sizeof(rsvdgb.RsvdgbRrpcaOpts) == 32
+    assert ctypes.sizeof(rsvdgb.RsvdgbRrpcaResult) == 48
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))["rrpca_defaults"]
+    o = rsvdgb.RsvdgbRrpcaOpts()
+    lib.rsvdgb_default_rrpca_opts(ctypes.byref(o))
+    assert o.maxiter == gold["maxiter"] and abs(o.tol - gold["tol"]) < 1e-12
+    assert o.k0 == gold["k0"] and o.lam == 0.0  # 0: lambda = max(m, n)^(-1/2)
+
+
+def test_new_entry_points_reject_a_null_handle(lib):
+    assert lib.rsvdgb_rpca(None, None, 10, 10, 10, 0, 2, 1, 1, None, None, 2, None, None, None, 2, None, None,
+                           None) == 1
+    assert lib.rsvdgb_rid(None, None, 10, 10, 10, 0, 2, None, None, 2, None, 10, None, None) == 1
+    assert lib.rsvdgb_rrpca(None, None, 10, 10, 10, None, None, None, 10, None, 10, None) == 1
+
+
+def test_header_compiles_as_c():
+    """include/rsvdgb.h is a plain C header (no C++ or CUDA types)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    res = subprocess.run([cc, "-std=c11", "-fsyntax-only", "-x", "c", HEADER], capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr

@@ -77,3 +77,20 @@ def test_rrpca_without_L_and_argument_errors(rs, handle):
     rc = lib.rsvdgb_rrpca(handle.ptr, A.data_ptr(), 200, 150, 150, ctypes.byref(ro), ctypes.byref(o), None, 150,
                           None, 150, ctypes.byref(res))
     assert rc == rs.RSVDGB_ERR_INVALID_ARG
+
+
+def test_rrpca_the_papers_simulation_case(rs, handle):
+    """Sec. 5.5: 300 x 300, rank 5, 20 % of the entries uniform on [-500, 500]."""
+    import torch
+    L0, S0, A64 = inputs.rrpca_example(4)
+    A = A64.astype(np.float32)
+    r = rs.rsvdgb_rrpca(handle, torch.from_numpy(A).cuda(), opts=rs.make_opts(p=10, q=2, seed=3))
+    torch.cuda.synchronize()
+    res = r["result"]
+    assert res.status == 0 and res.err < 1e-5 and res.rank == 5
+    ref = oracle.rrpca(A, p=10, q=2, seed=3)
+    L = r["L"].cpu().numpy().astype(np.float64)
+    S = r["S"].cpu().numpy().astype(np.float64)
+    tol_L = 10 * 1e-5 * np.linalg.norm(A64) / np.linalg.norm(L0)
+    assert rel(L, ref["L"]) < tol_L and rel(L, L0) < tol_L, (rel(L, ref["L"]), rel(L, L0), tol_L)
+    assert rel(S, ref["S"]) < 1e-4 and rel(S, S0) < 1e-4

@@ -2,6 +2,9 @@
 the inexact augmented Lagrange multiplier method) against facts fixed by the
 mathematics and by library routines.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -48,3 +51,20 @@ def test_recovers_low_rank_and_sparse_parts(m, n, rank, density):
     assert np.linalg.norm(r["S"] - S0) < 1e-4 * np.linalg.norm(S0)
     assert np.linalg.matrix_rank(r["L"], tol=1e-6 * np.linalg.norm(r["L"], 2)) == rank
     assert np.linalg.norm(A - r["L"] - r["S"]) <= 1e-5 * np.linalg.norm(A)
+
+
+def test_the_papers_simulation_case():
+    """The simulation of Sec. 5.5 (sizes, rank, corruption range and
+    fraction from tests/golden): recovery of L to the stopping tolerance
+    scaled by ||A|| / ||L|| and of S to 1e-4, rank exact."""
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+    ex = gold["rrpca_example"]
+    m, n = ex["shape"]
+    for seed in (1, 2):
+        L0, S0, A = inputs.rrpca_example(seed, m, n, ex["rank"], ex["sparse_fraction"])
+        assert np.abs(S0).max() <= ex["sparse_range"][1]
+        r = oracle.rrpca(A, seed=3)
+        assert r["err"] < 1e-5 and r["svp"] == ex["rank"]
+        tol_L = 10 * 1e-5 * np.linalg.norm(A) / np.linalg.norm(L0)
+        assert np.linalg.norm(r["L"] - L0) < tol_L * np.linalg.norm(L0)
+        assert np.linalg.norm(r["S"] - S0) < 1e-4 * np.linalg.norm(S0)
