@@ -215,6 +215,8 @@ int rsvdgb_rpca_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int6
  *   Z      device float, k x n row-major (ldz >= n): the interpolation matrix
  *          (Z(:, J) = I), or NULL.
  *   J      device int64[k], required: the column indices, in pivot order.
+ *          After a breakdown (below) the entries from the failed step on
+ *          are -1, and C's matching columns and all of Z are zero.
  * Steps: [~, B] = rqb(A, k, p, q) with opts' p and q; QR with column pivoting
  * of the l x n factor B stopped after k steps (Algorithm id); Z(:, P) =
  * [I, S11^{-1} S12]; C = A(:, J).  A pivot step that finds no remaining
@@ -276,7 +278,9 @@ void rsvdgb_default_rrpca_opts(rsvdgb_rrpca_opts* o);
  * values above 1/mu (next = that + 1 when it is below the target, else
  * that + 5 % of min(m, n)), capped so that k + p <= 224.  The loop runs on
  * the host and synchronises the handle's stream twice per iteration.
- * Returns RSVDGB_OK, an argument / CUDA error, or the status of an rSVD.
+ * Returns RSVDGB_OK, an argument / CUDA error (RSVDGB_ERR_INVALID_ARG also
+ * for A = 0, checked before any rSVD runs), RSVDGB_ERR_NONFINITE for an A
+ * with a NaN or infinity, or the status of an rSVD.
  */
 int rsvdgb_rrpca(rsvdgb_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, const rsvdgb_rrpca_opts* ro,
                  const rsvdgb_opts* opts, float* L, int64_t ldl, float* S, int64_t lds, rsvdgb_rrpca_result* res);

@@ -296,7 +296,8 @@ __global__ void __launch_bounds__(kPqrThreads) pqr_kernel(PqrArgs a)
 // Z (k x N, row-major ld ldz): Z(:, piv[t]) = e_t; other columns solve
 // S11 z = R(:, j) with S11(a, b) = R(a, piv[b]) upper triangular, by back
 // substitution: one warp per column, the lanes sharing each row's dot
-// product; z in shared memory (k floats per warp).
+// product; z in shared memory (k floats per warp).  A pivot list cut short
+// by a breakdown (entries -1) leaves Z = 0.
 constexpr int kSolveWarps = 4;
 __global__ void __launch_bounds__(32 * kSolveWarps) id_solve_kernel(const float* __restrict__ R, int64_t N, int k,
                                                                      const int* __restrict__ piv,
@@ -311,10 +312,17 @@ __global__ void __launch_bounds__(32 * kSolveWarps) id_solve_kernel(const float*
     if (j >= N) return;
     float* z = zs + warp * k;
     int pos = -1;
-    for (int t = lane; t < k; t += 32)
+    bool short_piv = false;  // the pivoted QR stopped early (status already set)
+    for (int t = lane; t < k; t += 32) {
         if (pv[t] == (int)j) pos = t;
+        short_piv |= pv[t] < 0;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) pos = max(pos, __shfl_xor_sync(0xffffffffu, pos, o));
+    if (__any_sync(0xffffffffu, short_piv)) {
+        for (int a = lane; a < k; a += 32) Z[(int64_t)a * ldz + j] = 0.f;
+        return;
+    }
     if (pos >= 0) {
         for (int a = lane; a < k; a += 32) Z[(int64_t)a * ldz + j] = (a == pos) ? 1.f : 0.f;
         return;
@@ -360,8 +368,8 @@ __global__ void gather_cols_kernel(const void* __restrict__ S, int64_t lda, bool
         i = e / k;
         t = e % k;
     }
-    const int64_t j = idx[t];
-    C[i * ldc + t] = elem<BF>(S, trans ? j * lda + i : i * lda + j);
+    const int64_t j = idx[t];  // -1 after a pivoted-QR breakdown: zero column
+    C[i * ldc + t] = j < 0 ? 0.f : elem<BF>(S, trans ? j * lda + i : i * lda + j);
 }
 
 // R (k x cols, row-major ldr) = rows idx of the logical matrix; Rt (if not
@@ -374,8 +382,8 @@ __global__ void gather_rows_kernel(const void* __restrict__ S, int64_t lda, bool
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= cols * k) return;
     const int64_t t = e / cols, j = e % cols;
-    const int64_t i = idx[t];
-    const float v = elem<BF>(S, trans ? j * lda + i : i * lda + j);
+    const int64_t i = idx[t];  // -1 after a pivoted-QR breakdown: zero row
+    const float v = i < 0 ? 0.f : elem<BF>(S, trans ? j * lda + i : i * lda + j);
     if (R) R[t * ldr + j] = v;
     if (Rt) Rt[t * ldt + j] = v;
 }

@@ -1323,23 +1323,27 @@ int rsvdgb_rrpca(rsvdgb_handle* h, const float* A, int64_t m, int64_t n, int64_t
     unsigned int* amax = (unsigned int*)(base + oMax);
     rsvdgb_info* dinfo = (rsvdgb_info*)(base + oInfo);
 
-    // ||A||_2 from a rank-1 rSVD, max |a_ij| and ||A||_F
-    rc = rsvdgb_rsvd(h, A, m, n, lda, RSVDGB_F32, 1, 1, 1, &o, d, U, kmax, V, kmax, dinfo);
-    if (rc) return rc;
+    // max |a_ij| and ||A||_F first: A = 0 or a non-finite A stops here,
+    // before any rSVD runs on it; then ||A||_2 from a rank-1 rSVD
     RSVDGB_CUDA_TRY(cudaMemsetAsync(amax, 0, 4, s));
     launch_absmax_sumsq(s, A, lda, m, n, amax, part, nb_abs, sumsq);
-    float h_norm2 = 0.f;
     unsigned int h_amax = 0;
     double h_sumsq = 0.0;
-    RSVDGB_CUDA_TRY(cudaMemcpyAsync(&h_norm2, d, 4, cudaMemcpyDeviceToHost, s));
     RSVDGB_CUDA_TRY(cudaMemcpyAsync(&h_amax, amax, 4, cudaMemcpyDeviceToHost, s));
     RSVDGB_CUDA_TRY(cudaMemcpyAsync(&h_sumsq, sumsq, 8, cudaMemcpyDeviceToHost, s));
     RSVDGB_CUDA_TRY(cudaStreamSynchronize(s));
+    const double normA = std::sqrt(h_sumsq);
+    if (!std::isfinite(normA)) return RSVDGB_ERR_NONFINITE;
+    if (!(normA > 0.0)) return RSVDGB_ERR_INVALID_ARG;  // A = 0
     float maxabs;
     std::memcpy(&maxabs, &h_amax, 4);
-    const double normA = std::sqrt(h_sumsq);
+    rc = rsvdgb_rsvd(h, A, m, n, lda, RSVDGB_F32, 1, 1, 1, &o, d, U, kmax, V, kmax, dinfo);
+    if (rc) return rc;
+    float h_norm2 = 0.f;
+    RSVDGB_CUDA_TRY(cudaMemcpyAsync(&h_norm2, d, 4, cudaMemcpyDeviceToHost, s));
+    RSVDGB_CUDA_TRY(cudaStreamSynchronize(s));
     const double norm2 = (double)h_norm2;
-    if (!(norm2 > 0.0) || !(normA > 0.0)) return RSVDGB_ERR_INVALID_ARG;  // A = 0
+    if (!(norm2 > 0.0)) return RSVDGB_ERR_BREAKDOWN;
     const double lam = ro.lambda > 0.f ? (double)ro.lambda : 1.0 / std::sqrt((double)std::max(m, n));
     double mu = 1.25 / norm2;
     const double mu_bar = 1e7 * mu;

@@ -193,3 +193,32 @@ def test_rid_rcur_full_size_properties(rs, handle):
     e_cur = float(torch.linalg.matrix_norm(A64 - c["C"].double() @ c["U"].double() @ c["R"].double()))
     assert e_svd <= e_id <= 3.0 * e_svd, (e_id, e_svd)
     assert e_svd <= e_cur <= 3.0 * e_svd, (e_cur, e_svd)
+
+
+def test_rid_maximal_rank_and_rank_deficiency(rs, handle):
+    """k = n - 1 with l = n (the sketch spans the whole row space): Z matches
+    the oracle's at the same pivots.  A with only 5 nonzero columns and
+    k = 8: a pivot step finds no direction left; the status says so, the
+    missing indices are -1 and their columns of C are zero."""
+    import torch
+    A = planted(400, 40, seed=6)
+    r = rs.rsvdgb_rid(handle, to_dev(A), 39, opts=rs.make_opts(p=5, q=1, seed=2))
+    torch.cuda.synchronize()
+    assert r["info"].status == 0
+    J = r["J"].cpu().numpy()
+    np.testing.assert_array_equal(r["C"].cpu().numpy(), A[:, J])
+    _, Bo = oracle.rqb(A, 39, p=5, q=1, seed=2)
+    check_pivots(Bo, J)
+    _, Z_o = oracle.id_decomp(Bo, 39, force_piv=J)
+    assert rel(r["Z"].cpu().numpy().astype(np.float64), Z_o) < 1e-3
+    D = np.zeros((300, 60), np.float32)
+    cols = [3, 17, 29, 41, 55]
+    D[:, cols] = np.random.default_rng(0).standard_normal((300, 5))
+    r2 = rs.rsvdgb_rid(handle, to_dev(D), 8, opts=rs.make_opts(p=4, q=1, seed=2))
+    torch.cuda.synchronize()
+    assert r2["info"].status == 4  # RSVDGB_ERR_BREAKDOWN
+    J2 = r2["J"].cpu().numpy()
+    C2 = r2["C"].cpu().numpy()
+    assert np.all(J2[5:] == -1) and set(J2[J2 >= 0].tolist()) <= set(cols)
+    np.testing.assert_array_equal(C2[:, J2 < 0], 0.0)
+    np.testing.assert_array_equal(C2[:, J2 >= 0], D[:, J2[J2 >= 0]])

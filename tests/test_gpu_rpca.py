@@ -202,3 +202,18 @@ def test_rpca_full_size_properties(rs, handle):
     assert float(torch.max(torch.abs(W.T @ W - torch.eye(k, dtype=torch.float64, device="cuda")))) <= 1e-4
     assert float(eig.sum()) <= n * (1 + 1e-5)
     assert bool(torch.all(eig[1:] <= eig[:-1] * (1 + 1e-6)))
+
+
+def test_rpca_maximal_rank(rs, handle):
+    """k = n - 1: the sketch spans all variables, so rpca returns the exact
+    leading principal components (numpy's correlation eigenvalues)."""
+    import torch
+    A = data(500, 30)
+    r = rs.rsvdgb_rpca(handle, to_dev(A), 29, opts=rs.make_opts(p=5, q=1, seed=4))
+    torch.cuda.synchronize()
+    assert r["info"].status == 0
+    w = np.linalg.eigvalsh(np.corrcoef(A.astype(np.float64).T))[::-1]
+    eig = r["eigvals"].cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(eig - w[:29])) <= 5e-5 * w[0], np.max(np.abs(eig - w[:29])) / w[0]
+    W = r["rotation"].cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(W.T @ W - np.eye(29))) < 1e-4

@@ -94,3 +94,20 @@ def test_rrpca_the_papers_simulation_case(rs, handle):
     tol_L = 10 * 1e-5 * np.linalg.norm(A64) / np.linalg.norm(L0)
     assert rel(L, ref["L"]) < tol_L and rel(L, L0) < tol_L, (rel(L, ref["L"]), rel(L, L0), tol_L)
     assert rel(S, ref["S"]) < 1e-4 and rel(S, S0) < 1e-4
+
+
+def test_rrpca_iteration_cap_and_zero_matrix(rs, handle):
+    import torch
+    _, _, A64 = inputs.low_rank_plus_sparse(200, 150, 4, 0.1, seed=2)
+    A = torch.from_numpy(A64.astype(np.float32)).cuda()
+    r = rs.rsvdgb_rrpca(handle, A, ropts=rs.make_rrpca_opts(maxiter=1), opts=rs.make_opts(seed=1))
+    torch.cuda.synchronize()
+    assert r["result"].iters == 1 and r["result"].status == 0 and r["result"].err > 1e-5
+    with pytest.raises(rs.RsvdgbError) as e:
+        rs.rsvdgb_rrpca(handle, torch.zeros(100, 80, device="cuda"))
+    assert e.value.status == rs.RSVDGB_ERR_INVALID_ARG
+    An = A.clone()
+    An[17, 4] = float("nan")
+    with pytest.raises(rs.RsvdgbError) as e:
+        rs.rsvdgb_rrpca(handle, An)
+    assert e.value.status == 5  # RSVDGB_ERR_NONFINITE
