@@ -89,6 +89,50 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int target, int* status
     return *flag != 0;
 }
 
+// One stage of a butterfly reduce-scatter over the warp: lanes with bit O
+// set keep the upper half of their 2 O partial sums, the others the lower
+// half, each adding the partner's copy of the half it keeps.
+template <int O>
+__device__ __forceinline__ void reduce_scatter_stage(float (&v)[32], int lane)
+{
+    const bool up = (lane & O) != 0;
+#pragma unroll
+    for (int k = 0; k < O; ++k) {
+        const float send = up ? v[k] : v[k + O];
+        const float keep = up ? v[k + O] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+    }
+}
+
+// For the 32 columns j0 .. j0 + 31 of X (those below c1): w^T x_j with w
+// (r floats, shared memory), or ||x_j||^2 when SQ.  Each lane sums its rows
+// i = lane (mod 32) of all 32 columns (one coalesced 128-byte load per
+// column and row block); five reduce-scatter stages (31 shuffles) then
+// leave column j0 + L's total in lane L.  Called by whole warps.
+template <bool SQ>
+__device__ __forceinline__ float dots32(const PqrArgs& a, const float* w, int64_t j0, int64_t c1, int lane)
+{
+    float v[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = 0.f;
+    const float* x0 = a.X + j0 * a.ldx;
+    for (int i = lane; i < a.r; i += 32) {
+        const float wi = SQ ? 0.f : w[i];
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+            if (j0 + c < c1) {
+                const float x = x0[(int64_t)c * a.ldx + i];
+                v[c] = fmaf(SQ ? x : wi, x, v[c]);
+            }
+    }
+    reduce_scatter_stage<16>(v, lane);
+    reduce_scatter_stage<8>(v, lane);
+    reduce_scatter_stage<4>(v, lane);
+    reduce_scatter_stage<2>(v, lane);
+    reduce_scatter_stage<1>(v, lane);
+    return v[0];
+}
+
 // Block-wide argmax of per-warp candidates; thread 0 writes the CTA slot of
 // buffer buf.  The maxima gathered after barrier e sit in buffer e & 1: a CTA
 // that runs ahead cannot overwrite them before every CTA has read them, since
@@ -123,7 +167,7 @@ __device__ void block_argmax_to_slot(double v, int64_t i, double* wv, int64_t* w
     }
 }
 
-__global__ void __launch_bounds__(kPqrThreads) pqr_kernel(PqrArgs a)
+__global__ void __launch_bounds__(kPqrThreads, 1) pqr_kernel(PqrArgs a)
 {
     extern __shared__ float sm[];  // Q (r x k, column t = q_t), then r floats for the new column
     float* Qs = sm;
@@ -141,18 +185,20 @@ __global__ void __launch_bounds__(kPqrThreads) pqr_kernel(PqrArgs a)
     const int64_t c0 = a.N * b / G, c1 = a.N * (b + 1) / G;
     unsigned int epoch = 0;
 
-    // residual norms of this CTA's columns, and their maximum
+    // residual norms of this CTA's columns (lane L of a warp owns column
+    // j0 + L of each 32-column block), and their maximum
     double bv = -1.0;
     int64_t bi = -1;
-    for (int64_t j = c0 + warp; j < c1; j += kPqrWarps) {
-        const float* x = a.X + j * a.ldx;
-        float s = 0.f;
-        for (int i = lane; i < r; i += 32) s = fmaf(x[i], x[i], s);
-        const double sd = warp_sum_d((double)s);
-        if (lane == 0) a.nrm[j] = sd;
-        if (better(sd, j, bv, bi)) {
-            bv = sd;
-            bi = j;
+    for (int64_t j0 = c0 + 32 * warp; j0 < c1; j0 += 32 * kPqrWarps) {
+        const float s = dots32<true>(a, nullptr, j0, c1, lane);
+        const int64_t j = j0 + lane;
+        if (j < c1) {
+            const double sd = (double)s;
+            a.nrm[j] = sd;
+            if (better(sd, j, bv, bi)) {
+                bv = sd;
+                bi = j;
+            }
         }
     }
     block_argmax_to_slot(bv, bi, wv, wi, a, (int)((epoch + 1) & 1));
@@ -254,38 +300,27 @@ __global__ void __launch_bounds__(kPqrThreads) pqr_kernel(PqrArgs a)
             Qs[(int64_t)t * r + i] = qs[i];
         }
         __syncthreads();
-        // row t of R for this CTA's columns; downdate their residual norms.
-        // Four columns per warp iteration, their loads issued together.
+        // row t of R for this CTA's columns; downdate their residual norms,
+        // each lane its own column (the FP64 work is not repeated across
+        // the warp: GB300's FP64 pipe is a small fraction of its FP32 one)
         bv = -1.0;
         bi = -1;
-        for (int64_t j0 = c0 + 4 * warp; j0 < c1; j0 += 4 * kPqrWarps) {
-            float d[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int i = lane; i < r; i += 32) {
-                const float qi = qs[i];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (j0 + u < c1) d[u] = fmaf(qi, a.X[(j0 + u) * a.ldx + i], d[u]);
+        for (int64_t j0 = c0 + 32 * warp; j0 < c1; j0 += 32 * kPqrWarps) {
+            const float du = dots32<false>(a, qs, j0, c1, lane);
+            const int64_t j = j0 + lane;
+            if (j >= c1) continue;
+            const double cur = a.nrm[j];
+            if (cur == -INFINITY) {  // a pivot of an earlier step
+                if (a.R) a.R[(int64_t)t * a.N + j] = 0.f;
+                continue;
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t j = j0 + u;
-                if (j >= c1) break;
-                const float du = warp_sum_f(d[u]);
-                const double cur = a.nrm[j];
-                if (cur == -INFINITY) {  // a pivot of an earlier step
-                    if (a.R && lane == 0) a.R[(int64_t)t * a.N + j] = 0.f;
-                    continue;
-                }
-                double nn = fmax(cur - (double)du * (double)du, 0.0);
-                if (j == p) nn = -INFINITY;
-                if (lane == 0) {
-                    if (a.R) a.R[(int64_t)t * a.N + j] = du;
-                    a.nrm[j] = nn;
-                }
-                if (j != p && better(nn, j, bv, bi)) {
-                    bv = nn;
-                    bi = j;
-                }
+            double nn = fmax(cur - (double)du * (double)du, 0.0);
+            if (j == p) nn = -INFINITY;
+            if (a.R) a.R[(int64_t)t * a.N + j] = du;
+            a.nrm[j] = nn;
+            if (j != p && better(nn, j, bv, bi)) {
+                bv = nn;
+                bi = j;
             }
         }
         block_argmax_to_slot(bv, bi, wv, wi, a, (int)((epoch + 1) & 1));
@@ -459,8 +494,9 @@ int launch_pqr(cudaStream_t s, int sm_count, const float* X, int64_t ldx, int r,
     if (smem > 200 * 1024) return RSVDGB_ERR_UNSUPPORTED;
     const int cap = pqr_max_ctas(sm_count, smem);
     if (cap <= 0) return RSVDGB_ERR_CUDA;
-    // about 32 columns per CTA: fewer CTAs make the per-step barrier cheaper
-    int G = (int)std::min<int64_t>(std::min<int64_t>(cap, max_slots / 2), ceil_div(N, 32));
+    // one 32-column block per warp and step where the columns allow it:
+    // fewer CTAs make the per-step barrier cheaper
+    int G = (int)std::min<int64_t>(std::min<int64_t>(cap, max_slots / 2), ceil_div(N, 32 * kPqrWarps));
     G = std::max(G, 1);
     if (cudaMemsetAsync(bar, 0, sizeof(unsigned int), s) != cudaSuccess) return RSVDGB_ERR_CUDA;
     PqrArgs a{X, ldx, r, N, k, piv, R, nrm, slot_val, slot_idx, bar, status};
