@@ -1,0 +1,164 @@
+"""Planted mistakes in the oracle are caught by its pins.
+
+The oracle is trusted because its pins (closed forms, library routines,
+brute force, the paper's identities) would fail if it computed something
+else.  This file checks that claim.  Each case copies the oracle (its C
+source and its Python side), the input generators and the CPU pin tests into
+a scratch tree, plants ONE plausible mistake in the copy of the oracle (a
+wrong constant, a dropped term, a flipped sign, a transposed index, an
+off-by-one loop bound, a missing derivative factor), runs the pins of that
+part in a child pytest, and requires at least one of them to fail.  An
+unmodified copy, run the same way, must pass.  The repository's own oracle is
+never touched.  Mutations that would read or write outside an array are not
+used."""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+C = "oracle/rsvd_oracle.c"
+PY = "oracle/__init__.py"
+
+RSVD = ["test_oracle_philox_library.py", "test_oracle_pins.py"]
+RID = ["test_oracle_rid.py"]
+RPCA = ["test_oracle_rpca.py"]
+RRPCA = ["test_oracle_rrpca.py"]
+CTL = ["test_oracle_controller.py"]
+
+# (name, file, [(original text, planted text)], pin files)
+MUTANTS = [
+    # test matrix (Sec. 2.3): the generator and the reading of its words
+    ("philox_same_multiplier", C, [("0xD2511F53u * (uint64_t)c[0]", "0xCD9E8D57u * (uint64_t)c[0]")], RSVD),
+    ("philox_key_increment", C, [("k[1] += 0xBB67AE85u;", "k[1] += 0xBB67AE86u;")], RSVD),
+    ("philox_nine_rounds", C, [("round < 10", "round < 9")], RSVD),
+    ("philox_word_order", C, [("hi1 ^ c[1] ^ k[0]", "hi1 ^ c[3] ^ k[0]"), ("hi0 ^ c[3] ^ k[1]", "hi0 ^ c[1] ^ k[1]")],
+     RSVD),
+    ("omega_column_in_last_word", C, [("(uint32_t)j, 0u};", "0u, (uint32_t)j};")], RSVD),
+    ("omega_sin_for_cos", C, [("v[2 * h] = rad * cos(theta);", "v[2 * h] = rad * sin(theta);")], RSVD),
+    ("omega_uniform_without_half", C, [("((double)x + 0.5)", "((double)x + 0.25)")], RSVD),
+    ("omega_rademacher_bit_30", C, [("(x[t] & 0x80000000u)", "(x[t] & 0x40000000u)")], RSVD),
+    # stored values of A
+    ("bf16_shift", C, [("[off] << 16;", "[off] << 15;")], RSVD),
+    # naive products (Algorithm rqb step 3, Algorithm sub_iterations)
+    ("gemm_ax_drops_last_term", C, [("for (int64_t t = 0; t < n; ++t) {\n                const double a = arow[t];",
+                                     "for (int64_t t = 0; t < n - 1; ++t) {\n                const double a = arow[t];")],
+     RSVD),
+    ("gemm_atx_drops_last_row", C, [("for (int64_t i = 0; i < m; ++i) {\n            const double* x = X + i * l;",
+                                     "for (int64_t i = 0; i < m - 1; ++i) {\n            const double* x = X + i * l;")],
+     RSVD),
+    # Householder QR
+    ("qr_reflector_sign", C, [("v[j] -= alpha;", "v[j] += alpha;")], RSVD),
+    ("qr_r_diagonal_sign", C, [("rdiag[j] = alpha;", "rdiag[j] = -alpha;")], RSVD),
+    ("qr_q_reflectors_in_forward_order", C, [("for (int64_t j = l - 1; j >= 0; --j) {",
+                                              "for (int64_t j = 0; j < l; ++j) {")], RSVD),
+    # one-sided Jacobi SVD
+    ("jacobi_rotation_sign", C, [("wa[i] = c * x - sn * y;", "wa[i] = c * x + sn * y;")], RSVD),
+    ("jacobi_loose_tolerance", C, [("const double tol = 1e-15;", "const double tol = 1e-7;")], RSVD),
+    ("jacobi_sorted_ascending", C, [("sv[order[d]] < sv[key]", "sv[order[d]] > sv[key]")], RSVD),
+    ("jacobi_right_vectors_not_rotated", C, [("vb[i] = sn * x + c * y;", "vb[i] = y;")], RSVD),
+    # Algorithms rqb / sub_iterations / rSVD
+    ("rqb_one_power_iteration_short", C, [("for (int j = 0; j < q; ++j) {\n        if ((rc = oracle_householder_qr",
+                                           "for (int j = 0; j < q - 1; ++j) {\n        if ((rc = oracle_householder_qr")],
+     RSVD),
+    ("rqb_b_wrong_index", C, [("B[r * n + c] = Z[c * l + r];", "B[r * n + c] = Z[r * n + c];")], RSVD),
+    ("rsvd_u_transposed_operand", C, [("Q[i * l + t] * Ut[t * l + c];", "Q[i * l + t] * Ut[c * l + t];")], RSVD),
+    ("sketch_width_plus_one", C, [("const int64_t l = (int64_t)k + (int64_t)p;",
+                                   "const int64_t l = (int64_t)k + (int64_t)p + 1;")], RSVD),
+    ("residual_without_sigma", C, [("lr += U[i * k + c] * d[c] * V[j * k + c];", "lr += U[i * k + c] * V[j * k + c];")],
+     RSVD),
+    ("power_direct_extra_iteration", C, [("for (int j = 0; j < q; ++j) {\n        gemm_AtX(&A, Y, l, X);",
+                                          "for (int j = 0; j <= q; ++j) {\n        gemm_AtX(&A, Y, l, X);")], RSVD),
+    # pivoted QR and the interpolative decomposition (Algorithms id, rid, rcur)
+    ("pqr_norm_of_whole_column", C, [("for (int64_t i = t; i < rows; ++i) s += W[j * rows + i] * W[j * rows + i];",
+                                      "for (int64_t i = 0; i < rows; ++i) s += W[j * rows + i] * W[j * rows + i];")],
+     RID),
+    ("pqr_ties_to_highest_index", C, [("if (s > bestn) { bestn = s; best = j; }",
+                                       "if (s >= bestn) { bestn = s; best = j; }")], RID),
+    ("id_back_substitution_sign", C, [("s -= R[(int64_t)a * cols + J[b]] * Z[(int64_t)b * cols + j];",
+                                       "s += R[(int64_t)a * cols + J[b]] * Z[(int64_t)b * cols + j];")], RID),
+    ("rcur_rows_from_column_pivots", PY, [("R = values(A)[I, :]", "R = values(A)[J, :]")], RID),
+    # randomized PCA (Algorithm rpca)
+    ("rpca_eigenvalues_over_m", PY, [("lam = d * d / (m - 1)", "lam = d * d / m")], RPCA),
+    ("rpca_scale_over_m", PY, [("np.sum(Xc * Xc, axis=0) / (m - 1)", "np.sum(Xc * Xc, axis=0) / m")], RPCA),
+    ("rpca_scores_without_sigma", PY, [('"x": U * d[None, :]', '"x": U')], RPCA),
+    # robust PCA (Algorithm rrpca)
+    ("rrpca_no_singular_value_shrinkage", PY, [("ds = np.maximum(d[:svp] - 1.0 / mu, 0.0)", "ds = d[:svp]")], RRPCA),
+    ("rrpca_threshold_times_mu", PY, [("soft_threshold(M - L + Z / mu, lam / mu)", "soft_threshold(M - L + Z / mu, lam * mu)")],
+     RRPCA),
+    ("rrpca_multiplier_sign", PY, [("Z = Z + mu * R", "Z = Z - mu * R")], RRPCA),
+    # controller network
+    ("mlp_standardise_by_multiplying", C, [("(x[t] - P[MLP_MU + t]) / P[MLP_SD + t]",
+                                            "(x[t] - P[MLP_MU + t]) * P[MLP_SD + t]")], CTL),
+    ("mlp_missing_relu_derivative", C, [("d1[t] = h1[t] > 0.0 ? a : 0.0;", "d1[t] = a;")], CTL),
+    ("mlp_pinball_weights_swapped", C, [("(u < 0.0) ? tau - 1.0 : tau", "(u < 0.0) ? tau : tau - 1.0")], CTL),
+    ("mlp_w2_gradient_uses_h2", C, [("grad[MLP_W2 - MLP_W1 + j * MLP_H + t] += d2[j] * h1[t];",
+                                     "grad[MLP_W2 - MLP_W1 + j * MLP_H + t] += d2[j] * h2[t];")], CTL),
+]
+
+COPY = ["oracle/__init__.py", "oracle/rsvd_oracle.c", "paper_1608_02148_gb300/__init__.py",
+        "paper_1608_02148_gb300/inputs.py", "tests/conftest.py", "tests/helpers.py", "pytest.ini"]
+ALL_PINS = sorted({f for m in MUTANTS for f in m[3]})
+
+
+def make_tree(dst: Path, edits):
+    for rel in COPY + ["tests/" + f for f in ALL_PINS]:
+        (dst / rel).parent.mkdir(parents=True, exist_ok=True)
+        shutil.copy2(ROOT / rel, dst / rel)
+    shutil.copytree(ROOT / "tests" / "golden", dst / "tests" / "golden")
+    for rel, subs in edits:
+        path = dst / rel
+        text = path.read_text()
+        for old, new in subs:
+            assert text.count(old) == 1, f"{rel}: the text to mutate must occur exactly once: {old!r}"
+            text = text.replace(old, new)
+        path.write_text(text)
+
+
+def run_pins(root: Path, files):
+    env = {k: v for k, v in os.environ.items() if k not in ("PYTHONPATH", "PYTEST_ADDOPTS")}
+    env["OMP_NUM_THREADS"] = "2"
+    # build first, so that a mutant that does not compile is reported as such
+    b = subprocess.run([sys.executable, "-c", "import oracle; oracle.build()"], cwd=root, env=env,
+                       capture_output=True, text=True, timeout=300)
+    if b.returncode != 0:
+        return "build-failed", b.stderr[-2000:]
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]
+                       + ["tests/" + f for f in files], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=900)
+    out = r.stdout[-3000:] + r.stderr[-1000:]
+    if r.returncode == 0:
+        return "passed", out
+    if r.returncode == 1:
+        return "failed", out
+    return f"error rc={r.returncode}", out
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    jobs = {"control": ([], ALL_PINS)}
+    for name, rel, subs, files in MUTANTS:
+        jobs[name] = ([(rel, subs)], files)
+    roots = {}
+    for name, (edits, _) in jobs.items():
+        roots[name] = tmp_path_factory.mktemp("mut_" + name)
+        make_tree(roots[name], edits)
+    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        futs = {name: ex.submit(run_pins, roots[name], files) for name, (_, files) in jobs.items()}
+        return {name: f.result() for name, f in futs.items()}
+
+
+def test_unmodified_copy_passes_every_pin(outcomes):
+    status, out = outcomes["control"]
+    assert status == "passed", out
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(outcomes, name):
+    status, out = outcomes[name]
+    assert status == "failed", f"{name}: {status}\n{out}"

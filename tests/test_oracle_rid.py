@@ -31,6 +31,25 @@ def test_pqr_matches_lapack_column_pivoting(rows, cols, k):
     assert np.all(np.diff(best) <= 1e-12)  # trailing norms of the pivots never grow
 
 
+def test_pqr_ties_go_to_the_lowest_index_as_in_lapack():
+    """Equal trailing norms: the pivot is the lowest column index, the choice
+    of LAPACK's dgeqp3 (its idamax returns the first maximum).  Columns 3, 9
+    and 14 are exact copies of the column of largest norm; each later tie
+    (copies of the second-largest column) goes the same way."""
+    rng = np.random.default_rng(17)
+    X = rng.standard_normal((25, 20))
+    X[:, 3] *= 10.0
+    X[:, 9] = X[:, 3]
+    X[:, 14] = X[:, 3]
+    X[:, 6] *= 5.0
+    X[:, 11] = X[:, 6]
+    piv, _, _, _ = oracle.pqr(X, 4)
+    _, _, P = sl.qr(X, pivoting=True, mode="economic")
+    assert piv[0] == 3 and P[0] == 3
+    assert piv[1] == 6 and P[1] == 6
+    assert 9 not in piv[:2] and 14 not in piv[:2] and 11 not in piv[:2]
+
+
 def test_pqr_prescribed_pivots_report_residuals():
     X = np.random.default_rng(5).standard_normal((20, 40))
     piv, _, _, _ = oracle.pqr(X, 5)
