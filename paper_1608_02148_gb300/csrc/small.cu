@@ -21,8 +21,6 @@
 namespace rsvdgb {
 namespace {
 
-constexpr int kSmallThreads = 1024;
-
 // ---------------------------------------------------------------------------
 // Cholesky by symmetric Gaussian elimination on [G | I].
 //
@@ -43,7 +41,6 @@ __global__ void __launch_bounds__(TD * TD)
     chol_inv_kernel(const float* __restrict__ G, int l, float shift_rel, float* __restrict__ R,
                     float* __restrict__ T, int* status, int* breakdowns)
 {
-    constexpr int kCholThreads = TD * TD;
     __shared__ float rowbuf[2][256];
     __shared__ float dinv[256];
     __shared__ float maxdiag;
