@@ -100,6 +100,12 @@ MUTANTS = [
                                      "grad[MLP_W2 - MLP_W1 + j * MLP_H + t] += d2[j] * h2[t];")], CTL),
 ]
 
+# Caught only by the comparison with the library generator (the bijection,
+# avalanche and distribution pins accept them): skipped where Triton, which
+# supplies that generator, is not installed.
+LIBRARY_ONLY = {"philox_same_multiplier", "philox_key_increment", "philox_nine_rounds",
+                "omega_uniform_without_half"}
+
 COPY = ["oracle/__init__.py", "oracle/rsvd_oracle.c", "paper_1608_02148_gb300/__init__.py",
         "paper_1608_02148_gb300/inputs.py", "tests/conftest.py", "tests/helpers.py", "pytest.ini"]
 ALL_PINS = sorted({f for m in MUTANTS for f in m[3]})
@@ -160,5 +166,7 @@ def test_unmodified_copy_passes_every_pin(outcomes):
 
 @pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
 def test_planted_mistake_fails_a_pin(outcomes, name):
+    if name in LIBRARY_ONLY:
+        pytest.importorskip("triton")
     status, out = outcomes[name]
     assert status == "failed", f"{name}: {status}\n{out}"
