@@ -82,6 +82,8 @@ MUTANTS = [
     ("id_back_substitution_sign", C, [("s -= R[(int64_t)a * cols + J[b]] * Z[(int64_t)b * cols + j];",
                                        "s += R[(int64_t)a * cols + J[b]] * Z[(int64_t)b * cols + j];")], RID),
     ("rcur_rows_from_column_pivots", PY, [("R = values(A)[I, :]", "R = values(A)[J, :]")], RID),
+    ("rcur_best_fit_middle_factor", PY, [("U = Z @ np.linalg.pinv(R)",
+                                          "U = np.linalg.pinv(C) @ values(A) @ np.linalg.pinv(R)")], RID),
     # randomized PCA (Algorithm rpca)
     ("rpca_eigenvalues_over_m", PY, [("lam = d * d / (m - 1)", "lam = d * d / m")], RPCA),
     ("rpca_scale_over_m", PY, [("np.sum(Xc * Xc, axis=0) / (m - 1)", "np.sum(Xc * Xc, axis=0) / m")], RPCA),
@@ -91,6 +93,9 @@ MUTANTS = [
     ("rrpca_threshold_times_mu", PY, [("soft_threshold(M - L + Z / mu, lam / mu)", "soft_threshold(M - L + Z / mu, lam * mu)")],
      RRPCA),
     ("rrpca_multiplier_sign", PY, [("Z = Z + mu * R", "Z = Z - mu * R")], RRPCA),
+    ("rrpca_lambda_from_min_dim", PY, [("lam = 1.0 / math.sqrt(max(m, n))", "lam = 1.0 / math.sqrt(min(m, n))")],
+     RRPCA),
+    ("rrpca_rank_grows_by_two", PY, [("nk = svp + 1 if svp < k", "nk = svp + 2 if svp < k")], RRPCA),
     # controller network
     ("mlp_standardise_by_multiplying", C, [("(x[t] - P[MLP_MU + t]) / P[MLP_SD + t]",
                                             "(x[t] - P[MLP_MU + t]) * P[MLP_SD + t]")], CTL),

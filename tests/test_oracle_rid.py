@@ -118,3 +118,20 @@ def test_rid_bf16_values_promote_exactly():
     C2, Z2, J2, _ = oracle.rid(inputs.bf16_to_f32(bits), 5, p=5, q=1, seed=3)
     np.testing.assert_array_equal(J1, J2)
     np.testing.assert_array_equal(Z1, Z2)
+
+
+def test_rcur_middle_factor_is_the_least_squares_fit_of_z():
+    """Algorithm rcur steps 5-6: U = Z pinv(R), i.e. the minimiser of
+    ||U R - Z||_F (R of full row rank), here solved by LAPACK's least squares
+    (scipy) on a matrix that is not of rank k, where other choices of U (for
+    instance pinv(C) A pinv(R), the best U for the given C and R) differ."""
+    rng = np.random.default_rng(11)
+    A = inputs.planted(200, 70, np.exp(-0.15 * np.arange(70)), seed=6, dtype=np.float64)
+    A = A + 1e-3 * rng.standard_normal(A.shape)
+    k = 8
+    C, U, R, J, I = oracle.rcur(A, k, p=6, q=1, seed=5)
+    _, Z, _, _ = oracle.rid(A, k, p=6, q=1, seed=5)
+    U_ls = sl.lstsq(R.T, Z.T)[0].T
+    np.testing.assert_allclose(U, U_ls, rtol=0, atol=1e-9 * np.abs(U_ls).max())
+    U_best = np.linalg.pinv(C) @ A @ np.linalg.pinv(R)
+    assert np.abs(U_best - U).max() > 1e-6 * np.abs(U).max()

@@ -68,3 +68,19 @@ def test_the_papers_simulation_case():
         tol_L = 10 * 1e-5 * np.linalg.norm(A) / np.linalg.norm(L0)
         assert np.linalg.norm(r["L"] - L0) < tol_L * np.linalg.norm(L0)
         assert np.linalg.norm(r["S"] - S0) < 1e-4 * np.linalg.norm(S0)
+
+
+def test_default_lambda_is_the_papers():
+    """lambda = max(m, n)^(-1/2) by default (Sec. 5, with the rrpca()
+    signature of Sec. 5.4), checked on a rectangular case where the choice
+    changes the result."""
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+    assert gold["rrpca_defaults"]["lambda"] == "max(m, n)^(-1/2)"
+    L0, S0, A = inputs.low_rank_plus_sparse(160, 60, 3, 0.05, seed=4)
+    m, n = A.shape
+    r = oracle.rrpca(A, seed=2, maxiter=40)
+    r_max = oracle.rrpca(A, lam=max(m, n) ** -0.5, seed=2, maxiter=40)
+    r_min = oracle.rrpca(A, lam=min(m, n) ** -0.5, seed=2, maxiter=40)
+    np.testing.assert_array_equal(r["S"], r_max["S"])
+    np.testing.assert_array_equal(r["L"], r_max["L"])
+    assert np.abs(r["S"] - r_min["S"]).max() > 1e-6 * np.abs(r["S"]).max()
