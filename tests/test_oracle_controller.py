@@ -111,3 +111,25 @@ def test_features_of_an_exact_low_rank_matrix():
     assert abs(f[12] - 1.0) < 1e-12
     assert abs(f[13]) < 0.3
     assert f[11] < -6  # r_l / r_1 at the FP32 storage level of A: rank r < l
+
+
+@pytest.mark.parametrize("r", [1, 3, 4, 5, 7, 8, 9, 12, 13, 17, 18, 27])
+def test_decay_features_sit_at_their_indices(r):
+    """The QR factor of a sketch of rank r has R_jj = 0 (to rounding) exactly
+    for j > r, so log10(r_j / r_1) is ordinary for j <= r and far below for
+    j > r.  With k = 8, p_max = 20 (l = 28) the decay features read the
+    indices ceil(k/4), ceil(k/2), ceil(3k/4), k, k + 1, k + p_max/4,
+    k + p_max/2 and l = 2, 4, 6, 8, 9, 13, 18, 28; sweeping r across them
+    fixes each index (an index off by one moves a feature across a rank
+    boundary)."""
+    rng = np.random.default_rng(100 + r)
+    m, n, k = 200, 60, 8
+    A = rng.standard_normal((m, r)) @ rng.standard_normal((r, n))
+    f = oracle.controller_features(A, k, p_max=20, seed=6)
+    for t, j in zip(range(4, 12), (2, 4, 6, 8, 9, 13, 18, 28)):
+        if j <= r:
+            assert f[t] > -4, (t, j, f[t])
+        else:
+            assert f[t] < -10, (t, j, f[t])
+    if k <= r < 28:  # log10(r_k / r_l): r_k ordinary, r_l beyond the rank
+        assert f[14] > 10, f[14]

@@ -97,6 +97,9 @@ MUTANTS = [
      RRPCA),
     ("rrpca_rank_grows_by_two", PY, [("nk = svp + 1 if svp < k", "nk = svp + 2 if svp < k")], RRPCA),
     # controller network
+    ("features_half_index_off_by_one", PY, [("lr((k + 1) // 2)", "lr((k + 3) // 2)")], CTL),
+    ("features_quarter_oversampling_index", PY, [("lr(k + max(p_max // 4, 1))", "lr(k + max(p_max // 4, 1) + 1)")],
+     CTL),
     ("mlp_standardise_by_multiplying", C, [("(x[t] - P[MLP_MU + t]) / P[MLP_SD + t]",
                                             "(x[t] - P[MLP_MU + t]) * P[MLP_SD + t]")], CTL),
     ("mlp_missing_relu_derivative", C, [("d1[t] = h1[t] > 0.0 ? a : 0.0;", "d1[t] = a;")], CTL),
