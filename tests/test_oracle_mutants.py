@@ -79,6 +79,10 @@ MUTANTS = [
      RID),
     ("pqr_ties_to_highest_index", C, [("if (s > bestn) { bestn = s; best = j; }",
                                        "if (s >= bestn) { bestn = s; best = j; }")], RID),
+    ("pqr_reports_squared_norms", C, [("resid_chosen[t] = sqrt(pn);", "resid_chosen[t] = pn;"),
+                                      ("resid_max[t] = sqrt(bestn);", "resid_max[t] = bestn;")], RID),
+    ("rid_p_and_q_swapped", PY, [("_, B = rqb(A, k, p=p, q=q, sdist=sdist, seed=seed)",
+                                  "_, B = rqb(A, k, p=q, q=p, sdist=sdist, seed=seed)")], RID),
     ("id_back_substitution_sign", C, [("s -= R[(int64_t)a * cols + J[b]] * Z[(int64_t)b * cols + j];",
                                        "s += R[(int64_t)a * cols + J[b]] * Z[(int64_t)b * cols + j];")], RID),
     ("rcur_rows_from_column_pivots", PY, [("R = values(A)[I, :]", "R = values(A)[J, :]")], RID),

@@ -135,3 +135,30 @@ def test_rcur_middle_factor_is_the_least_squares_fit_of_z():
     np.testing.assert_allclose(U, U_ls, rtol=0, atol=1e-9 * np.abs(U_ls).max())
     U_best = np.linalg.pinv(C) @ A @ np.linalg.pinv(R)
     assert np.abs(U_best - U).max() > 1e-6 * np.abs(U).max()
+
+
+def test_pqr_reports_two_norms_of_the_trailing_columns():
+    """At step 0 the trailing part of every column is the whole column, so
+    the reported largest residual is the largest column 2-norm (numpy), and
+    at step 1 it is the largest norm of the columns projected off the first
+    pivot."""
+    X = np.random.default_rng(8).standard_normal((30, 45))
+    piv, _, chosen, best = oracle.pqr(X, 3)
+    norms = np.linalg.norm(X, axis=0)
+    assert abs(best[0] - norms.max()) <= 1e-13 * norms.max()
+    assert abs(chosen[0] - norms[piv[0]]) <= 1e-13 * norms.max()
+    q0 = X[:, piv[0]] / norms[piv[0]]
+    P = X - np.outer(q0, q0 @ X)
+    P[:, piv[0]] = 0.0
+    assert abs(best[1] - np.linalg.norm(P, axis=0).max()) <= 1e-12 * norms.max()
+
+
+def test_rid_factors_the_rqb_factor_with_the_papers_p_and_q():
+    """Algorithm rid step 1 is rqb(A, k, p, q) with the same p and q as
+    everywhere (the listing's swapped order is read as a typo): B has
+    l = k + p rows and is the B of rqb with those arguments."""
+    A = inputs.planted(150, 60, inputs.exp_spectrum(60, 0.1), seed=3, dtype=np.float64)
+    C, Z, J, B = oracle.rid(A, 5, p=7, q=1, seed=2)
+    _, B_rqb = oracle.rqb(A, 5, p=7, q=1, seed=2)
+    assert B.shape == (12, 60)
+    np.testing.assert_array_equal(B, B_rqb)
