@@ -108,6 +108,7 @@ def test_features_of_an_exact_low_rank_matrix():
     f = oracle.controller_features(A, k, p_max=20, seed=4)
     assert f.shape == (16,)
     assert abs(f[0] - math.log10(m)) < 1e-12 and abs(f[2] - math.log10(k)) < 1e-12
+    assert abs(f[1] - math.log10(n)) < 1e-12 and abs(f[3] - k / n) < 1e-12 and abs(f[15] - 20 / k) < 1e-12
     assert abs(f[12] - 1.0) < 1e-12
     assert abs(f[13]) < 0.3
     assert f[11] < -6  # r_l / r_1 at the FP32 storage level of A: rank r < l
@@ -133,3 +134,8 @@ def test_decay_features_sit_at_their_indices(r):
             assert f[t] < -10, (t, j, f[t])
     if k <= r < 28:  # log10(r_k / r_l): r_k ordinary, r_l beyond the rank
         assert f[14] > 10, f[14]
+    # energy of the first k diagonal entries: all of it iff the rank is <= k
+    if r <= k:
+        assert abs(f[12] - 1.0) < 1e-12, f[12]
+    else:
+        assert f[12] < 1.0 - 1e-6, f[12]

@@ -69,6 +69,9 @@ MUTANTS = [
     ("rsvd_u_transposed_operand", C, [("Q[i * l + t] * Ut[t * l + c];", "Q[i * l + t] * Ut[c * l + t];")], RSVD),
     ("sketch_width_plus_one", C, [("const int64_t l = (int64_t)k + (int64_t)p;",
                                    "const int64_t l = (int64_t)k + (int64_t)p + 1;")], RSVD),
+    ("wide_rule_off_by_one", C, [("*transposed = (m < n);", "*transposed = (m < n - 1);")], RSVD),
+    ("sign_convention_smallest_entry", PY, [("i = int(np.argmax(np.abs(V[:, c])))",
+                                             "i = int(np.argmin(np.abs(V[:, c])))")], RSVD),
     ("residual_without_sigma", C, [("lr += U[i * k + c] * d[c] * V[j * k + c];", "lr += U[i * k + c] * V[j * k + c];")],
      RSVD),
     ("power_direct_extra_iteration", C, [("for (int j = 0; j < q; ++j) {\n        gemm_AtX(&A, Y, l, X);",
@@ -104,6 +107,9 @@ MUTANTS = [
     ("features_half_index_off_by_one", PY, [("lr((k + 1) // 2)", "lr((k + 3) // 2)")], CTL),
     ("features_quarter_oversampling_index", PY, [("lr(k + max(p_max // 4, 1))", "lr(k + max(p_max // 4, 1) + 1)")],
      CTL),
+    ("features_energy_of_k_plus_one", PY, [("e_k = float(np.sum(r[:k] ** 2))", "e_k = float(np.sum(r[:k + 1] ** 2))")],
+     CTL),
+    ("features_p_max_over_l", PY, [("         p_max / k]", "         p_max / l]")], CTL),
     ("mlp_standardise_by_multiplying", C, [("(x[t] - P[MLP_MU + t]) / P[MLP_SD + t]",
                                             "(x[t] - P[MLP_MU + t]) * P[MLP_SD + t]")], CTL),
     ("mlp_missing_relu_derivative", C, [("d1[t] = h1[t] > 0.0 ? a : 0.0;", "d1[t] = a;")], CTL),

@@ -328,16 +328,27 @@ def test_invariances():
     assert np.allclose(U3c, Uc[perm], atol=1e-10)
 
 
-def test_wide_matrix_is_transpose_problem():
+@pytest.mark.parametrize("m,n", [(50, 130), (59, 60)])
+def test_wide_matrix_is_transpose_problem(m, n):
     """m < n: the method factors A^T and swaps U and V (Sec. 3.3, m >= n
-    without loss of generality)."""
-    A = inputs.planted(50, 130, inputs.exp_spectrum(50, 0.1), seed=6, dtype=np.float64)
+    without loss of generality); one column more than rows is already wide."""
+    A = inputs.planted(m, n, inputs.exp_spectrum(m, 0.1), seed=6, dtype=np.float64)
     d, U, V = oracle.rsvd(A, 8, p=5, q=1, seed=3)
     dt, Ut, Vt = oracle.rsvd(np.ascontiguousarray(A.T), 8, p=5, q=1, seed=3)
     assert np.allclose(d, dt, rtol=1e-13)
     assert np.allclose(np.abs(U), np.abs(Vt), atol=1e-12)
     assert np.allclose(np.abs(V), np.abs(Ut), atol=1e-12)
-    assert U.shape == (50, 8) and V.shape == (130, 8)
+    assert U.shape == (m, 8) and V.shape == (n, 8)
+
+
+def test_sign_canonicalisation_convention():
+    """Each pair (u_i, v_i) is flipped so that the entry of v_i of largest
+    magnitude is positive (the comparison convention for singular vectors)."""
+    U = np.array([[1.0, 2.0], [3.0, 4.0]])
+    V = np.array([[0.1, 0.9], [-0.8, 0.2], [0.3, -0.3]])
+    Uc, Vc = oracle.canonical_signs(U, V)
+    np.testing.assert_array_equal(Vc, [[-0.1, 0.9], [0.8, 0.2], [-0.3, -0.3]])
+    np.testing.assert_array_equal(Uc, [[-1.0, 2.0], [-3.0, 4.0]])
 
 
 def test_bf16_storage_is_exact_promotion():
