@@ -153,10 +153,10 @@ int rsvdgb_rsvd(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t l
                 const rsvdgb_opts* opts, float* d, float* U, int64_t ldu, float* V, int64_t ldv, rsvdgb_info* info);
 
 /*
- * Same as rsvdgb_rsvd, but A, d, U, V and info are HOST pointers (pinned
- * memory gives full copy bandwidth; pageable memory works).  The call copies A
- * to a device buffer owned by the handle, runs the factorisation, copies the
- * results back and synchronises.  Returns the device status (info->status) if
+ * rsvd() of Sec. 3.6 (Algorithm rSVD) as rsvdgb_rsvd, but A, d, U, V and
+ * info are HOST pointers (pinned memory gives full copy bandwidth; pageable
+ * memory works).  The call copies A to a device buffer owned by the handle,
+ * runs the factorisation, copies the results back and synchronises.  Returns the device status (info->status) if
  * the launches succeeded.
  */
 int rsvdgb_rsvd_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k, int nu,
@@ -196,8 +196,9 @@ int rsvdgb_rpca(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t l
                 float* x, int64_t ldx, float* center_out, float* scale_out, rsvdgb_info* info);
 
 /*
- * Same as rsvdgb_rpca with HOST pointers for A and every output (staged
- * through a device buffer owned by the handle; the call synchronises).
+ * rpca() of Sec. 4.4 (Algorithm rpca) as rsvdgb_rpca, with HOST pointers
+ * for A and every output (staged through a device buffer owned by the
+ * handle; the call synchronises).
  * Returns the device status (info->status) if the launches succeeded.
  */
 int rsvdgb_rpca_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k,
@@ -260,6 +261,9 @@ typedef struct rsvdgb_rrpca_result {
     double reserved[2];
 } rsvdgb_rrpca_result;
 
+/* Defaults of the rrpca() signature of Sec. 5.4: lambda <= 0 (that is,
+ * max(m, n)^(-1/2), Sec. 5), maxiter 50, tol 1e-5; k0 = 2 (Algorithm rrpca
+ * step 1); rho = 1.5 (a reading of the cited IALM method). */
 void rsvdgb_default_rrpca_opts(rsvdgb_rrpca_opts* o);
 
 /*
@@ -344,7 +348,9 @@ int rsvdgb_rqb(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t ld
 int rsvdgb_omega(rsvdgb_handle* h, int64_t rows, int l, uint64_t seed, int sdist, float* out, int64_t ld);
 
 /*
- * Kernel-level access to the two passes over A, for tests and tuning:
+ * Kernel-level access to the two passes over A (the products A Omega of
+ * Algorithm rqb step 3 and A^T Q, A Q of Algorithm sub_iterations), for tests
+ * and tuning:
  *   rsvdgb_pass_ax  : Y (m x l) = A X,    X device float n x l row-major (ldx)
  *   rsvdgb_pass_atx : Z (n x l) = A^T X,  X device float m x l row-major (ldx)
  * Outputs row-major with leading dimension ldy / ldz.  `engine` and `prec`
@@ -408,36 +414,40 @@ typedef struct rsvdgb_train_opts {
     int32_t reserved[4];
 } rsvdgb_train_opts;
 
-/* Defaults of rsvdgb_train_opts. */
+/* Defaults of rsvdgb_train_opts (no counterpart in the paper). */
 void rsvdgb_default_train_opts(rsvdgb_train_opts* o);
 
-/* Load a parameter file (format above) into the handle; the learned mode of
+/* No counterpart in the paper (q and p are the user's, Sec. 3.4).  Load a
+ * parameter file (format above) into the handle; the learned mode of
  * rsvdgb_rsvd then uses it.  RSVDGB_ERR_INVALID_ARG for a missing or
  * malformed file.  Synchronises the handle's stream. */
 int rsvdgb_controller_load(rsvdgb_handle* h, const char* path);
 
-/* Same from host memory (RSVDGB_MLP_PARAMS floats). */
+/* As rsvdgb_controller_load, from host memory (RSVDGB_MLP_PARAMS floats);
+ * no counterpart in the paper. */
 int rsvdgb_controller_set(rsvdgb_handle* h, const float* params_host);
 
-/* Train on a data set file and write the parameter file.  The data set is
- * 8 bytes "RSVDDS01", int32 n, int32 RSVDGB_MLP_FEATURES, then n x 16 float32
- * features (as rsvdgb_controller_features writes them) and n x 2 float32
- * targets (q, log2 p).  Training runs on the handle's GPU (minibatch pinball
+/* No counterpart in the paper.  Train on a data set file and write the
+ * parameter file.  The data set is 8 bytes "RSVDDS01", int32 n, int32
+ * RSVDGB_MLP_FEATURES, then n x 16 float32 features (as
+ * rsvdgb_controller_features writes them) and n x 2 float32 targets
+ * (q, log2 p).  Training runs on the handle's GPU (minibatch pinball
  * loss, hand-written forward/backward kernels, Adam); the trained parameters
  * are also loaded into the handle.  final_loss (host, may be NULL) receives
  * the mean loss over the data set.  Synchronises. */
 int rsvdgb_controller_train(rsvdgb_handle* h, const char* dataset_path, const rsvdgb_train_opts* opts,
                             const char* out_path, float* final_loss);
 
-/* The 16 controller features of A (device output feats[16]): pass 1 with the
- * sketch width k + opts->p_max (clamped to min(m, n)), the CholeskyQR factor
- * of the sketch and ||A||_F^2, as the learned mode computes them.  Arguments
+/* No counterpart in the paper.  The 16 controller features of A (device
+ * output feats[16]): pass 1 (Algorithm rqb step 3) with the sketch width
+ * k + opts->p_max (clamped to min(m, n)), the CholeskyQR factor of the
+ * sketch and ||A||_F^2, as the learned mode computes them.  Arguments
  * as rsvdgb_rsvd; asynchronous. */
 int rsvdgb_controller_features(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int k,
                                const rsvdgb_opts* opts, float* feats);
 
-/* Network evaluation and gradient on device arrays (P: RSVDGB_MLP_PARAMS
- * floats; X: n x 16; Y: n x 2; out: n x 2).  rsvdgb_mlp_grad writes the
+/* No counterpart in the paper.  Network evaluation and gradient on device
+ * arrays (P: RSVDGB_MLP_PARAMS floats; X: n x 16; Y: n x 2; out: n x 2).  rsvdgb_mlp_grad writes the
  * gradient of the mean pinball loss (quantile tau) with respect to the
  * trainable parameters (RSVDGB_MLP_PARAMS - 32 floats, W1 first) and the mean
  * loss (device float).  Asynchronous. */

@@ -97,3 +97,22 @@ def test_header_compiles_as_c():
         pytest.skip("no C compiler")
     res = subprocess.run([cc, "-std=c11", "-fsyntax-only", "-x", "c", HEADER], capture_output=True, text=True)
     assert res.returncode == 0, res.stderr
+
+
+# Library plumbing with no operation of the method behind it.
+_PLUMBING = {"rsvdgb_create", "rsvdgb_destroy", "rsvdgb_set_stream", "rsvdgb_status_string"}
+
+
+def test_every_entry_point_cites_its_passage():
+    """Each declared call's comment (the nearest one above it) cites the
+    passage of the paper that defines its operation, or states that it has
+    no counterpart in the paper; only handle plumbing is exempt."""
+    text = open(HEADER).read()
+    for m in re.finditer(r"^(?:int|void|const char\*|int64_t)\s+(rsvdgb_[a-z0-9_]+)\s*\(", text, flags=re.M):
+        name = m.group(1)
+        if name in _PLUMBING:
+            continue
+        before = text[:m.start()]
+        end = before.rfind("*/")
+        comment = before[before.rfind("/*", 0, end):end]
+        assert re.search(r"Sec\. \d|Algorithm \w|Eq\. \w|counterpart|not part of the paper", comment), name
