@@ -116,3 +116,23 @@ def test_every_entry_point_cites_its_passage():
         end = before.rfind("*/")
         comment = before[before.rfind("/*", 0, end):end]
         assert re.search(r"Sec\. \d|Algorithm \w|Eq\. \w|counterpart|not part of the paper", comment), name
+
+
+def test_product_path_fails_loudly_without_library_or_gpu(lib, tmp_path, monkeypatch):
+    """No fallback: a missing library is an error, and so is a handle on a
+    machine without a usable GPU (the C call reports it; nothing runs on the
+    CPU instead)."""
+    import torch
+
+    from paper_1608_02148_gb300 import rsvdgb
+    monkeypatch.setattr(rsvdgb, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        rsvdgb.load(tmp_path / "librsvdgb.so")
+    monkeypatch.undo()
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError):
+        rsvdgb.Handle(0)
+    h = ctypes.c_void_p()
+    assert lib.rsvdgb_create(ctypes.byref(h), 0, None) == 3  # RSVDGB_ERR_CUDA
+    assert not h.value
