@@ -53,6 +53,8 @@ MUTANTS = [
      RSVD),
     # Householder QR
     ("qr_reflector_sign", C, [("v[j] -= alpha;", "v[j] += alpha;")], RSVD),
+    ("qr_norm_from_row_zero", C, [("for (int64_t i = j; i < m; ++i) nrm2 += x[i] * x[i];",
+                                   "for (int64_t i = 0; i < m; ++i) nrm2 += x[i] * x[i];")], RSVD),
     ("qr_r_diagonal_sign", C, [("rdiag[j] = alpha;", "rdiag[j] = -alpha;")], RSVD),
     ("qr_q_reflectors_in_forward_order", C, [("for (int64_t j = l - 1; j >= 0; --j) {",
                                               "for (int64_t j = 0; j < l; ++j) {")], RSVD),
@@ -61,11 +63,24 @@ MUTANTS = [
     ("jacobi_loose_tolerance", C, [("const double tol = 1e-15;", "const double tol = 1e-7;")], RSVD),
     ("jacobi_sorted_ascending", C, [("sv[order[d]] < sv[key]", "sv[order[d]] > sv[key]")], RSVD),
     ("jacobi_right_vectors_not_rotated", C, [("vb[i] = sn * x + c * y;", "vb[i] = y;")], RSVD),
+    ("jacobi_larger_root", C, [("((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta))",
+                                "((zeta >= 0.0) ? 1.0 : -1.0) * (fabs(zeta) + sqrt(1.0 + zeta * zeta))")], RSVD),
+    ("jacobi_cosine_without_root", C, [("const double c = 1.0 / sqrt(1.0 + t * t);",
+                                        "const double c = 1.0 / (1.0 + t * t);")], RSVD),
+    ("jacobi_left_vectors_not_normalised", C, [("(sv[src] > 0.0) ? W[src * rows + i] / sv[src] : 0.0;",
+                                                "W[src * rows + i];")], RSVD),
+    ("jacobi_rotations_transposed", C, [("J[i * cols + c] = V[src * cols + i];", "J[i * cols + c] = V[i * cols + src];")],
+     RSVD),
     # Algorithms rqb / sub_iterations / rSVD
     ("rqb_one_power_iteration_short", C, [("for (int j = 0; j < q; ++j) {\n        if ((rc = oracle_householder_qr",
                                            "for (int j = 0; j < q - 1; ++j) {\n        if ((rc = oracle_householder_qr")],
      RSVD),
     ("rqb_b_wrong_index", C, [("B[r * n + c] = Z[c * l + r];", "B[r * n + c] = Z[r * n + c];")], RSVD),
+    ("rqb_test_matrix_perturbed", C, [("for (int64_t e = 0; e < n * l; ++e) X[e] = (double)omega_f[e];\n    /* step 3",
+                                       "for (int64_t e = 0; e < n * l; ++e) X[e] = (double)omega_f[e] * (1.0 + 1e-9 * (double)(e % 7));"
+                                       "\n    /* step 3")], RSVD),
+    ("rsvd_singular_values_shifted", C, [("for (int64_t c = 0; c < k; ++c) d[c] = s[c];",
+                                          "for (int64_t c = 0; c < k; ++c) d[c] = s[c > 0 ? c - 1 : 0];")], RSVD),
     ("rsvd_u_transposed_operand", C, [("Q[i * l + t] * Ut[t * l + c];", "Q[i * l + t] * Ut[c * l + t];")], RSVD),
     ("sketch_width_plus_one", C, [("const int64_t l = (int64_t)k + (int64_t)p;",
                                    "const int64_t l = (int64_t)k + (int64_t)p + 1;")], RSVD),
