@@ -178,15 +178,7 @@ def make_matrix(wl, seed, device):
     m, n = wl["m"], wl["n"]
     if wl.get("step"):
         # step spectrum on structured orthogonal factors, noise, stored BF16
-        import torch
-        sigma = np.where(np.arange(1, n + 1) <= wl["step"], 1.0, 1e-2)
-        A = inputs.planted_reflector(m, n, sigma, seed, device=device)
-        gen = torch.Generator(device=device)
-        gen.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
-        for r0 in range(0, m, 8192):  # noise in row blocks
-            blk = A[r0:r0 + 8192]
-            blk.add_(torch.randn(blk.shape, generator=gen, device=device, dtype=torch.float32), alpha=wl["noise"])
-        return A.to(torch.bfloat16) if wl.get("dtype") == "bf16" else A
+        return inputs.step_noise(m, n, wl["step"], wl["noise"], seed, device=device, bf16=wl.get("dtype") == "bf16")
     if wl["noise"] > 0:
         sigma = 1.0 / np.arange(1, n + 1, dtype=np.float64)
         return inputs.spiked_noise(m, n, sigma, wl["noise"], seed, device=device)

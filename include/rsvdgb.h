@@ -380,10 +380,13 @@ int rsvdgb_pass_atx(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64
  *   problem with n * ldz * 4 bytes above that size is rejected with
  *   RSVDGB_ERR_INVALID_ARG before anything is queued.
  *   The first call on a device looks up the array's device address (once per
- *   device); make that first call before any stream capture.  All calls on a
- *   device share the array and it keeps the last call's contents, so calls
- *   that overlap on the GPU (other streams, other host threads) race.
- * Returns RSVDGB_OK once queued, RSVDGB_ERR_INVALID_ARG or RSVDGB_ERR_CUDA.
+ *   device and CUDA context: again after a cudaDeviceReset); make that first
+ *   call before any stream capture.  All calls on a device share the array
+ *   and it keeps the last call's contents, so calls that overlap on the GPU
+ *   (other streams, other host threads) race.
+ * Returns RSVDGB_OK once queued, RSVDGB_ERR_INVALID_ARG, or RSVDGB_ERR_CUDA
+ * (also, without queueing anything, when an earlier CUDA error is still
+ * pending on the calling thread: it is left for its owner to read).
  */
 int rsvdgb_pass_atx_noalloc(void* cuda_stream, const void* A, int64_t m, int64_t n, int64_t lda, int dtype,
                             const float* X, int64_t ldx, int l, float* Z, int64_t ldz);

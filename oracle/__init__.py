@@ -319,7 +319,8 @@ def rrpca(A: np.ndarray, lam=None, maxiter: int = 50, tol: float = 1e-5, p: int 
     when ||A - L - S||_F <= tol ||A||_F or after maxiter iterations.  Each
     iteration's rSVD uses the test matrix of seed + iteration.  svd (for the
     pins) replaces the randomized SVD by a callable (X, k) -> (d, U, V).
-    Returns dict L, S, iters, err, k, svp, mu."""
+    Returns dict L, S, Z (the last multiplier; Z_0 when maxiter = 0), iters,
+    err, k, svp, mu and mu_hist (mu before each iteration, then the last)."""
     M = values(A)
     m, n = M.shape
     ns = min(m, n)
@@ -337,6 +338,7 @@ def rrpca(A: np.ndarray, lam=None, maxiter: int = 50, tol: float = 1e-5, p: int 
     err = float("inf")
     svp = 0
     it = 0
+    mu_hist = [mu]
     for it in range(1, maxiter + 1):
         X = np.ascontiguousarray(M - S + Z / mu)
         if svd is None:
@@ -350,11 +352,12 @@ def rrpca(A: np.ndarray, lam=None, maxiter: int = 50, tol: float = 1e-5, p: int 
         R = M - L - S
         Z = Z + mu * R
         mu = min(rho * mu, mu_bar)
+        mu_hist.append(mu)
         err = float(np.linalg.norm(R)) / normM
         k = k_next
         if err < tol:
             break
-    return {"L": L, "S": S, "iters": it, "err": err, "k": k, "svp": svp, "mu": mu}
+    return {"L": L, "S": S, "Z": Z, "iters": it, "err": err, "k": k, "svp": svp, "mu": mu, "mu_hist": mu_hist}
 
 
 def power_direct(A: np.ndarray, l: int, q: int, sdist: str = "normal", seed: int = 0) -> np.ndarray:

@@ -182,6 +182,22 @@ def planted_reflector(m: int, n: int, sigma, seed: int, device="cpu"):
     return A.to(torch.float32).contiguous()
 
 
+def step_noise(m: int, n: int, step: int, noise_std: float, seed: int, device="cpu", bf16: bool = True):
+    """Step spectrum (sigma = 1 for i <= step, 1e-2 beyond) on two-reflector
+    orthogonal factors (planted_reflector) plus i.i.d. N(0, noise_std^2)
+    noise added in row blocks, stored BF16 (or float32)."""
+    import torch
+
+    sigma = np.where(np.arange(1, min(m, n) + 1) <= step, 1.0, 1e-2)
+    A = planted_reflector(m, n, sigma, seed, device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+    for r0 in range(0, m, 8192):
+        blk = A[r0:r0 + 8192]
+        blk.add_(torch.randn(blk.shape, generator=gen, device=device, dtype=torch.float32), alpha=noise_std)
+    return A.to(torch.bfloat16) if bf16 else A
+
+
 def controller_spectrum(rng, k: int, count: int):
     """A random spectrum of one of three families (descending, sigma_1 = 1):
     exponential exp(-r (i - 1)), r log-uniform in [1e-3, 0.5]; power law

@@ -484,19 +484,41 @@ def rsvdgb_kernel_launches() -> int:
 
 def rsvdgb_pass_atx_noalloc(A, X, Z=None, stream=None):
     """Z = A^T X with no device allocation inside the library (static
-    scratch).  Z may be preallocated by the caller (n x l float32)."""
+    scratch).  A: m x n (float32 or bfloat16, row-major, on a CUDA device);
+    X: m x l float32 row-major on the same device; Z (optional, allocated here
+    when None): n x l float32 with unit column stride on that device.  Every
+    argument is checked here, before anything is queued, and the call runs
+    with A's device current (the library looks up its scratch on the current
+    device)."""
     torch = _torch()
+    if not isinstance(A, torch.Tensor) or A.dim() != 2 or A.device.type != "cuda":
+        raise ValueError("A must be a 2-D tensor on a CUDA device")
     m, n = A.shape
+    lda = _rowmajor_ld(A)
+    dt = _dtype_code(A)
+    if not isinstance(X, torch.Tensor) or X.dim() != 2 or X.dtype != torch.float32 or X.shape[0] != m:
+        raise ValueError(f"X must be a float32 matrix with {m} rows")
+    if X.device != A.device:
+        raise ValueError("X must be on A's device")
+    ldx = _rowmajor_ld(X)
     l = X.shape[1]
     if Z is None:
         Z = torch.empty(n, l, dtype=torch.float32, device=A.device)
-    if n * Z.stride(0) * 4 > NOALLOC_SCRATCH_BYTES:
-        raise ValueError(f"A^T X with n={n}, ldz={Z.stride(0)} needs {n * Z.stride(0) * 4} bytes of scratch; "
+    if not isinstance(Z, torch.Tensor) or Z.dim() != 2 or tuple(Z.shape) != (n, l) or Z.dtype != torch.float32:
+        raise ValueError(f"Z must be a float32 tensor of shape ({n}, {l})")
+    if Z.device != A.device:
+        raise ValueError("Z must be on A's device")
+    ldz = _rowmajor_ld(Z)
+    if m < 1 or n < 1 or l < 1:
+        raise ValueError("empty A^T X")
+    if n * ldz * 4 > NOALLOC_SCRATCH_BYTES:
+        raise ValueError(f"A^T X with n={n}, ldz={ldz} needs {n * ldz * 4} bytes of scratch; "
                          f"the static scratch holds {NOALLOC_SCRATCH_BYTES}")
-    if stream is None:
-        stream = torch.cuda.current_stream(A.device)
-    rc = load().rsvdgb_pass_atx_noalloc(ctypes.c_void_p(stream.cuda_stream), A.data_ptr(), m, n, _rowmajor_ld(A),
-                                        _dtype_code(A), X.data_ptr(), _rowmajor_ld(X), l, Z.data_ptr(), Z.stride(0))
+    with torch.cuda.device(A.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(A.device)
+        rc = load().rsvdgb_pass_atx_noalloc(ctypes.c_void_p(stream.cuda_stream), A.data_ptr(), m, n, lda, dt,
+                                            X.data_ptr(), ldx, l, Z.data_ptr(), ldz)
     _check("rsvdgb_pass_atx_noalloc", rc)
     return Z
 

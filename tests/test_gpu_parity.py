@@ -75,6 +75,15 @@ def check_rsvd(rs, handle, A_np, k, p=10, q=2, sdist="normal", seed=0, layout="r
         tol_v = subspace_tol(sB, nv_, sB[0])
         assert sin_theta(V, V_o[:, :nv_]) <= tol_v, (sin_theta(V, V_o[:, :nv_]), tol_v)
         assert np.max(np.abs(V.T @ V - np.eye(nv_))) < 1e-4
+    # the whole l-dimensional basis Q against the oracle's (rqb runs the same
+    # steps up to Q), within max(1e-4, 10 u32 kappa(B))
+    if layout == "row" and m >= n:
+        Q, _, info_q = rs.rsvdgb_rqb(handle, A_dev, k, opts=opts)
+        torch.cuda.synchronize()
+        assert info_q.status == 0
+        tol_q = max(1e-4, 10 * 2.0 ** -24 * sB[0] / max(sB[-1], 1e-30))
+        sq = sin_theta(Q.cpu().numpy(), Qo)
+        assert sq <= tol_q, (sq, tol_q)
     # ||A||_F^2 and the error identity reported in info
     fa = oracle.fro2(A_or)
     assert abs(info.fro2_A - fa) <= 1e-5 * fa
@@ -165,7 +174,8 @@ def test_exact_rank_gpu(rs, handle):
     A = inputs.planted(2000, 1000, sigma, seed=11)
     d, U, V, info = rs.rsvdgb_rsvd(handle, to_dev(A), 25, opts=rs.make_opts(p=5, q=0))
     d = d.cpu().numpy()
-    assert np.max(np.abs(d - sigma) / sigma) < 1e-5
+    assert info.status == 0
+    assert np.max(np.abs(d - sigma) / sigma) < 1e-6, np.max(np.abs(d - sigma) / sigma)
 
 
 def test_rqb_q_orthonormal_and_b_projection(rs, handle):

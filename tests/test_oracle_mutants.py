@@ -117,6 +117,12 @@ MUTANTS = [
     ("rrpca_multiplier_sign", PY, [("Z = Z + mu * R", "Z = Z - mu * R")], RRPCA),
     ("rrpca_lambda_from_min_dim", PY, [("lam = 1.0 / math.sqrt(max(m, n))", "lam = 1.0 / math.sqrt(min(m, n))")],
      RRPCA),
+    ("rrpca_multiplier_spectral_only", PY, [("Z = M / max(norm2, float(np.abs(M).max()) / lam)", "Z = M / norm2")],
+     RRPCA),
+    ("rrpca_multiplier_entry_term_times_lambda", PY, [("Z = M / max(norm2, float(np.abs(M).max()) / lam)",
+                                                       "Z = M / max(norm2, float(np.abs(M).max()) * lam)")], RRPCA),
+    ("rrpca_penalty_cap_1e6", PY, [("mu_bar = mu * 1e7", "mu_bar = mu * 1e6")], RRPCA),
+    ("rrpca_penalty_growth_1_6", PY, [("rho: float = 1.5,", "rho: float = 1.6,")], RRPCA),
     ("rrpca_rank_grows_by_two", PY, [("nk = svp + 1 if svp < k", "nk = svp + 2 if svp < k")], RRPCA),
     # controller network
     ("features_half_index_off_by_one", PY, [("lr((k + 1) // 2)", "lr((k + 3) // 2)")], CTL),

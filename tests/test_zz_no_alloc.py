@@ -40,3 +40,33 @@ def test_noalloc_atx_matches_regular_entry_point_twice():
         assert rc == 1
     finally:
         h.close()
+
+
+def test_noalloc_atx_rejects_bad_operands_before_queueing():
+    """Wrong shapes, dtypes, strides or devices of X and Z raise in the binding
+    before the C call, so nothing is queued and nothing is written."""
+    import torch
+    from paper_1608_02148_gb300 import build, rsvdgb as rs
+
+    build.build()
+    m, n, l = 300, 40, 8
+    A = torch.randn(m, n, device="cuda")
+    X = torch.randn(m, l, device="cuda")
+    bad_z = [
+        torch.zeros(n - 1, l, device="cuda"),                       # too few rows
+        torch.zeros(n, l + 1, device="cuda"),                       # too many columns
+        torch.zeros(n, l, dtype=torch.bfloat16, device="cuda"),     # not float32
+        torch.zeros(l, n, device="cuda").t(),                       # column stride not 1
+        torch.zeros(n, l),                                          # on the host
+    ]
+    for Z in bad_z:
+        before = Z.clone()
+        with pytest.raises(ValueError):
+            rs.rsvdgb_pass_atx_noalloc(A, X, Z)
+        assert torch.equal(Z, before)
+    for Xb in (torch.randn(m + 1, l, device="cuda"), X.to(torch.bfloat16), X.cpu()):
+        with pytest.raises(ValueError):
+            rs.rsvdgb_pass_atx_noalloc(A, Xb)
+    with pytest.raises(ValueError):
+        rs.rsvdgb_pass_atx_noalloc(A.cpu(), X.cpu())
+    torch.cuda.synchronize()
