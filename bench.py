@@ -47,12 +47,14 @@ WORKLOADS = {
 
 # DRAM bytes (read + write) per byte of A of the FP32 tensor-core pass kernel,
 # averaged over the six passes of one rSVD, from one ncu capture on the
-# 50000 x 2000 workload (profiles/tc_kernels_spiked50k.md): sketch 410.2 + 48.1,
-# A-side power passes 410.2 + 48.7, A^T-side power passes 445.2 + 3.5, chunked
-# projection 473.8 + 44.5 MB per 400 MB of A.  The traffic scales with the rows
-# processed, so the full-size launches carry the same ratio.  Set to None when
-# the pass kernel changes.
-TC_PASS_TRAFFIC_PER_A_BYTE = ((410.2 + 48.1) + 2 * (410.2 + 48.7) + 2 * (445.2 + 3.5) + (473.8 + 44.5)) / (6 * 400.0)
+# 50000 x 2000 workload (the pass kernel's ncu summary under profiles/).  The
+# traffic scales with the rows processed, so the full-size launches carry the
+# same ratio.  None until the current pass kernel has been captured.
+TC_PASS_TRAFFIC_PER_A_BYTE = None
+
+# The roofline the method's target is stated against: bytes of A per pass x
+# passes at 8 TB/s (nominal HBM3e); the measured copy bandwidth is the other.
+NOMINAL_HBM_TBS = 8.0
 
 # FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 SIMT_FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -489,7 +491,7 @@ def main():
     l = rs.rsvdgb_sketch_width(m, n, k, wl["p"])
     achieved_gbs = (pass_bytes / max(pass_n, 1)) / (pass_avg_ms * 1e-3) / 1e9
     achieved_tflops = (2.0 * m * n * l) / (pass_avg_ms * 1e-3) / 1e12
-    engine = "tc" if info.engine == 2 else "simt"
+    engine = {1: "simt", 2: "tc_fp16x3", 3: "tc_tf32"}.get(info.engine, str(info.engine))
     if engine == "simt":
         roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": SIMT_FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved_tflops / SIMT_FP32_PEAK_TFLOPS, "traffic": None,
@@ -505,10 +507,11 @@ def main():
                     "frac": achieved_gbs / hbm, "traffic": traffic, "peak_source": peak_kind,
                     "traffic_source": "ncu dram bytes on the 50000x2000 workload, scaled by rows"
                     if traffic is not None else None,
-                    "kernel": "tc_pass_kernel (pass over A, tcgen05 3xTF32)",
+                    "kernel": ("tc_pass_kernel (pass over A, tcgen05: the first pass 3xTF32 measuring max|A|, "
+                               "the later passes scaled FP16x3)" if engine == "tc_fp16x3" else
+                               "tc_pass_kernel (pass over A, tcgen05 3xTF32)"),
                     "tensor_view": {"achieved_tflops_algorithmic": achieved_tflops,
-                                    "tf32_flops_issued_per_algorithmic":
-                                        (2.0 if A.dtype == torch.bfloat16 else 3.0) * (((l + 15) // 16) * 16) / l}}
+                                    "mma_products_per_k_step": 2 if A.dtype == torch.bfloat16 else 3}}
 
     # ---------------- the other precision at equal error (same A, same Omega) ----------------
     variants = {}
@@ -682,6 +685,13 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "hbm_roofline": {"time_ms": roof_ms, "frac_of_step": roof_ms / ms_per_step,
                                  "peak_gbs": hbm, "peak_source": peak_kind},
+                "hbm_roofline_nominal": {"time_ms": passes * a_bytes / (NOMINAL_HBM_TBS * 1e12) * 1e3,
+                                         "frac_of_step": passes * a_bytes / (NOMINAL_HBM_TBS * 1e12) * 1e3
+                                         / ms_per_step,
+                                         "peak_gbs": NOMINAL_HBM_TBS * 1e3,
+                                         "pass_kernel_frac": achieved_gbs / (NOMINAL_HBM_TBS * 1e3)
+                                         if achieved_gbs else None,
+                                         "peak_source": "nominal HBM3e (bytes of A per pass x passes / 8 TB/s)"},
                 "roofline": roofline,
                 "pass_kernels": {"launches": pass_n, "avg_ms": pass_avg_ms, "share_of_step":
                                  pass_ms / max(elapsed, 1e-9) if world == 1 else None},

@@ -67,8 +67,13 @@ enum { RSVDGB_PREC_FP32 = 0, RSVDGB_PREC_BF16_SKETCH = 1 };
 enum { RSVDGB_ROW_MAJOR = 0, RSVDGB_COL_MAJOR = 1 };
 
 /* Kernel family for the passes over A. AUTO picks the tensor-core kernels
- * where they apply; SIMT forces the FP32 FMA kernels. */
-enum { RSVDGB_ENGINE_AUTO = 0, RSVDGB_ENGINE_SIMT = 1, RSVDGB_ENGINE_TC = 2 };
+ * where they apply; SIMT forces the FP32 FMA kernels.  TC computes the
+ * FP32-accurate products of every pass after the first as scaled FP16x3
+ * (A and each panel column multiplied by a power of two, split into FP16
+ * hi + lo, three FP16 products: the same accuracy as 3xTF32 at half the
+ * tensor-core time); the first pass, which measures max|A| for that scale,
+ * is 3xTF32.  TC_TF32 keeps 3xTF32 for every pass. */
+enum { RSVDGB_ENGINE_AUTO = 0, RSVDGB_ENGINE_SIMT = 1, RSVDGB_ENGINE_TC = 2, RSVDGB_ENGINE_TC_TF32 = 3 };
 
 /* How q and p are chosen.  FIXED: opts.q and opts.p.  LEARNED: the handle's
  * controller (rsvdgb_controller_load / rsvdgb_controller_set) predicts them
@@ -105,7 +110,7 @@ typedef struct rsvdgb_info {
     double err2_QB;      /* ||A - Q B||_F^2 = fro2_A - fro2_B                  */
     double err2_k;       /* ||A - U_k S_k V_k^T||_F^2 = fro2_A - sum_k s_i^2   */
     int32_t breakdowns;  /* Cholesky breakdowns met (each retried with a shift) */
-    int32_t engine;      /* kernel family that ran the passes: RSVDGB_ENGINE_SIMT or _TC */
+    int32_t engine;      /* kernel family that ran the passes: RSVDGB_ENGINE_SIMT, _TC or _TC_TF32 */
     int32_t jacobi_sweeps; /* sweeps of the one-sided Jacobi SVD of the l x l factor */
     int32_t reserved[5];
 } rsvdgb_info;

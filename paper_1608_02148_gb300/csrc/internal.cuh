@@ -138,12 +138,52 @@ bool tc_pass_supported(int64_t m, int64_t n, int64_t lda, int l_pad, const void*
 // chunk_stages > 0 bounds each tensor-memory accumulation chain to that many
 // 32-wide K stages; the chunks are summed in the output in FP32 (the tensor
 // core's accumulation truncates, which biases long sums toward zero).
+// Options of the scaled FP16x3 form and of FP16 output splits:
+//   h16: the products run as scaled FP16x3; Phi / Plo are then the FP16 hi /
+//        lo parts (uint16, leading dimension ldp elements) of the panel with
+//        column j scaled by 1 / pinv[j] (a power of two); A is scaled by the
+//        power of two that brings the max|A| held in *amax_in (float bits)
+//        into [2^13, 2^14);
+//   amax_out: the pass also accumulates max|a| into *amax_out (float bits;
+//        zero it beforehand); a pass taking statistics is never FP16x3;
+//   out_h16 / out_l16: a direct column-major output also gets its FP16 hi /
+//        lo split (same layout as out), column j scaled by split_sc[j] (or by
+//        split_sc_const when split_sc is null).
+struct TcExtra {
+    int h16 = 0;
+    const unsigned int* amax_in = nullptr;
+    const float* pinv = nullptr;
+    unsigned int* amax_out = nullptr;
+    uint16_t* out_h16 = nullptr;
+    uint16_t* out_l16 = nullptr;
+    const float* split_sc = nullptr;
+    float split_sc_const = 0.f;
+};
 int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int64_t m, int64_t n, int64_t lda,
                    const float* Phi, const float* Plo, int64_t ldp, int l_pad, float* out, float* out_hi,
                    float* out_lo, int64_t ld_out, float* partial, int64_t want_splits, int64_t* splits_out,
                    int* status, double* fro2, int out_rowmajor = 0, int out_cols = 0, int bf16_panel = 0,
                    int a_bf16 = 0, int chunk_stages = 0, const float* aff_h = nullptr,
-                   const float* aff_u = nullptr, const float* aff_r = nullptr);
+                   const float* aff_u = nullptr, const float* aff_r = nullptr, const TcExtra* x = nullptr);
+// Z = X T (xt.cu) for a column-major rows x l matrix X (ld) and an l x l
+// row-major upper triangular T (entries below the diagonal must be zero),
+// in FP32 FMA; Z column-major (ld) over l_pad columns, rows beyond `rows` up
+// to ld and columns beyond l written as zero.  split 1: Zh / Zl get Z's TF32
+// hi / lo (floats); split 2: the FP16 hi / lo (uint16) of sc Z.  l_pad <= 112.
+bool xt_supported(int l_pad);
+int launch_xt(cudaStream_t s, int sm_count, const float* X, int64_t ld, int64_t rows, int l, int l_pad, const float* T,
+              float* Z, int split, void* Zh, void* Zl, float sc);
+// Scaled FP16 hi / lo split of a column-major rows x l panel (ld even) over
+// l_pad columns for the FP16x3 passes: column j is multiplied by the power of
+// two bringing its max magnitude into [2^13, 2^14), pinv[j] receives the
+// inverse of that factor (1 for columns >= l); rows >= rows and columns >= l
+// are written as zero.
+void launch_panel_f16(cudaStream_t s, const float* in, int64_t ld, int64_t rows, int l, int l_pad, uint16_t* hi,
+                      uint16_t* lo, float* pinv);
+// max|a| of a row-major rows x cols matrix (FP32, or BF16 bits when a_bf16),
+// atomicMax'ed as float bits into *amax (zero it beforehand).
+void launch_absmax(cudaStream_t s, int sm_count, const void* A, int64_t lda, int a_bf16, int64_t rows, int64_t cols,
+                   unsigned int* amax);
 int64_t tc_pass_max_splits(int64_t m, int64_t n, int l_pad, int sm_count);
 int64_t tc_split_count(int64_t k_total, int64_t units, int sm_count);
 // l x l row-major T -> column-major L x L TF32 hi/lo panel (zero padded),
@@ -186,8 +226,10 @@ void launch_finalize_info(cudaStream_t s, const float* sigma, int l, int k, floa
 // Raise the dynamic shared-memory limit of the one-CTA kernels on the
 // current device (called once per handle).
 int init_small_kernels();
-// Set an int to zero and a double to zero.
-void launch_clear_scalars(cudaStream_t s, int* status, int* breakdowns, double* fro2);
+// Zero the status / breakdown counters, ||A||_F^2 and max|A| (each may be
+// null), and set fillv[0..nfill) to fillval (fillv may be null).
+void launch_clear_scalars(cudaStream_t s, int* status, int* breakdowns, double* fro2, unsigned int* amax = nullptr,
+                          float* fillv = nullptr, int nfill = 0, float fillval = 0.f);
 
 // Convert a column-major r x l (ld) matrix to row-major (ldo) with cols
 // columns (cols <= l), i.e. out[i*ldo + j] = in[j*ld + i].

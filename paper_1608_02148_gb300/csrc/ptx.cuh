@@ -121,7 +121,9 @@ __device__ __forceinline__ uint32_t bf16_idesc(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16_tmemA(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+// kind::f16 MMA (BF16 or FP16 operands, per the instruction descriptor),
+// A operand in tensor memory, B from a shared-memory descriptor.
+__device__ __forceinline__ void mma_kf16_tmemA(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
                                                uint32_t accumulate)
 {
     asm volatile(
@@ -129,6 +131,58 @@ __device__ __forceinline__ void mma_bf16_tmemA(uint32_t d_tmem, uint32_t a_tmem,
         " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
         "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+
+// Instruction descriptor of kind::f16 with FP16 A and B (both K-major), D FP32.
+__device__ __forceinline__ uint32_t f16_idesc(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Two floats to an FP16 pair (round to nearest): lo_elem in the low half.
+__device__ __forceinline__ uint32_t pack_f16(float lo_elem, float hi_elem)
+{
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi_elem), "f"(lo_elem));
+    return r;
+}
+
+// The two halves of an FP16 pair as floats (exact).
+__device__ __forceinline__ float2 unpack_f16(uint32_t v)
+{
+    float a, b;
+    asm("{\n .reg .b16 l, h;\n mov.b32 {l, h}, %2;\n cvt.f32.f16 %0, l;\n cvt.f32.f16 %1, h;\n}\n"
+        : "=f"(a), "=f"(b)
+        : "r"(v));
+    return make_float2(a, b);
+}
+
+// Split two floats x0, x1 (already scaled into the FP16 range) into FP16 hi
+// and lo pairs: x = hi + lo to within 2^-22 |x| while lo stays in FP16's
+// normal range (|x| above about 2^-2); below that, to within 2^-25 absolute.
+__device__ __forceinline__ void split_f16_pair(float x0, float x1, uint32_t& hi, uint32_t& lo)
+{
+    hi = pack_f16(x0, x1);
+    const float2 h = unpack_f16(hi);
+    lo = pack_f16(x0 - h.x, x1 - h.y);
+}
+
+// Power-of-two scale that brings |x| <= amax below 2^14 (and amax at or above
+// 2^13): 2^(14 - e) with amax < 2^e.  1 for a zero or non-finite amax.
+__device__ __forceinline__ float pow2_scale_below(float amax, int target_exp = 14)
+{
+    if (!(amax > 0.f) || !(amax <= 3.4e38f)) return 1.f;
+    int e;
+    frexpf(amax, &e);
+    return ldexpf(1.f, max(-100, min(100, target_exp - e)));
+}
+
+// 32 lanes x 32 bit, 4 consecutive columns per thread.
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&v)[4])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3])
+                 : "memory");
 }
 
 // 32 lanes x 32 bit, 8 consecutive columns per thread.

@@ -113,6 +113,7 @@ struct Geom {
     int l;
     int L;         // l rounded up to 16 (tensor-core N granularity)
     bool use_tc;   // passes over A on the tensor cores
+    bool h16 = false;  // FP32-accurate passes after the first as scaled FP16x3 (tensor cores)
     bool bf16;     // sketch and power passes in BF16 (mixed precision)
     int64_t ldm, ldn;
     const Affine* aff = nullptr;  // randomized PCA: products with X instead of A
@@ -145,6 +146,12 @@ struct Work {
     int64_t* slot_i;
     int* piv;
     unsigned int* bar;
+    // scaled FP16x3 passes: max|A| (float bits, from the first pass) and the
+    // inverse column scales of the n-side panel (Pth / Ptl then hold its FP16
+    // hi / lo) and of the m-side panels (constant: their columns are unit
+    // vectors up to rounding)
+    unsigned int* amax;
+    float *Ppinv, *Qpinv;
 };
 
 constexpr int kPqrSlots = 1024;  // per-CTA maxima of the pivoted QR (its grid is at most this wide)
@@ -228,6 +235,9 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w, int L_lo = 0)
     // Jacobi columns when they do not fit in shared memory: 2 x l x Lp with the
     // padded column stride Lp <= l rounded up to 32
     w.jwork = c.take<float>(2 * (L + 32) * (L + 32));
+    w.amax = c.take<unsigned int>(1);
+    w.Ppinv = c.take<float>(L);
+    w.Qpinv = c.take<float>(L);
     w.status = c.take<int>(1);
     w.breakdowns = c.take<int>(1);
     w.sweeps = c.take<int>(1);
@@ -350,13 +360,14 @@ void tall_gemm(cudaStream_t s, int sm, bool AT, bool BT, bool CT, const void* A,
 double a_bytes(const Geom& g) { return (double)g.m * (double)g.n * (g.a_bf16 ? 2.0 : 4.0); }
 
 // One pass over A:  out = A_logical P (A_side) or A_logical^T P (!A_side).
-// P is column-major (K x l, ldP) in FP32 (SIMT engine) or as its TF32 hi/lo
-// parts (tensor-core engine).  out is column-major (rows x l, ldO); when
-// out_h/out_l are given (tensor-core engine) they receive its TF32 split.
+// P is column-major (K x l, ldP) in FP32 (SIMT engine) or as its split parts
+// (tensor-core engine: TF32 hi / lo, or FP16 hi / lo with x->h16).  out is
+// column-major (rows x l, ldO); when out_h/out_l are given (tensor-core
+// engine) they receive its TF32 split.
 void pass_over_A(rsvdgb_handle* h, const Geom& g, Work& w, bool A_side, const float* P, const float* Ph,
                  const float* Pl, float* out, float* out_h, float* out_l, double* fro2, const void* Pbf = nullptr,
                  int chunk = 0, const float* aff_h = nullptr, const float* aff_u = nullptr,
-                 const float* aff_r = nullptr)
+                 const float* aff_r = nullptr, const TcExtra* x = nullptr)
 {
     const cudaStream_t s = h->stream;
     const int64_t rows = A_side ? g.m : g.n;
@@ -378,17 +389,23 @@ void pass_over_A(rsvdgb_handle* h, const Geom& g, Work& w, bool A_side, const fl
     if (Pbf)
         launch_tc_gemm(s, h->sm_count, stored_atx, (const float*)g.A, g.sm(), g.sn(), g.lda, (const float*)Pbf,
                        nullptr, ldP, g.L, out, out_h, out_l, ldO, w.part, stored_atx ? 0 : 1, &splits, w.status, fro2,
-                       0, 0, 1, g.a_bf16, chunk, aff_h, aff_u, aff_r);
+                       0, 0, 1, g.a_bf16, chunk, aff_h, aff_u, aff_r, x);
     else
         launch_tc_gemm(s, h->sm_count, stored_atx, (const float*)g.A, g.sm(), g.sn(), g.lda, Ph, Pl, ldP, g.L, out,
                        out_h, out_l, ldO, w.part, stored_atx ? 0 : 1, &splits, w.status, fro2, 0, 0, 0, g.a_bf16,
-                       chunk, aff_h, aff_u, aff_r);
+                       chunk, aff_h, aff_u, aff_r, x);
     prof_mark(h, false, a_bytes(g));
     if (splits > 0) {
         launch_reduce_splits(s, w.part, (int)splits, (int64_t)g.L * ldO, g.l, rows, ldO, out, ldO);
         if (out_h) launch_split_tf32(s, out, ldO, rows, g.l, g.L, out_h, out_l);
     }
 }
+
+// Scale of the FP16 hi / lo split of an m-side basis Q (the panel of an
+// FP16x3 A^T-side pass): its columns are unit vectors up to rounding, so
+// |q_ij| <= 1 (a little more after a Cholesky step on an ill-conditioned
+// sketch) and 2^13 keeps them below FP16's range with room to spare.
+constexpr float kQSplitScale = 8192.f;
 
 // G (l x l) = X^T X for a column-major rows x l matrix X (leading dimension
 // ld) on the tensor cores (3xTF32).  Up to l_pad = 128 the Gram kernel reads
@@ -409,24 +426,44 @@ void tc_gram(rsvdgb_handle* h, const Geom& g, Work& w, const float* Xt, const fl
     launch_reduce_splits(h->stream, w.part, (int)splits, (int64_t)g.L * g.L, g.l, g.l, g.L, w.G, g.l);
 }
 
-// Z = X T (rows x l, column-major, with TF32 hi/lo parts) for a column-major
-// rows x l matrix X and an l x l row-major T, on the tensor cores.
+// Z = X T (rows x l, column-major) for a column-major rows x l matrix X and
+// an l x l row-major upper triangular T.  Zh / Zl (optional) receive
+// Z's split: TF32 hi / lo floats, or with f16 the FP16 hi / lo (uint16) of
+// kQSplitScale Z (Z is then a basis with unit columns).
 void tc_times_small(rsvdgb_handle* h, const Geom& g, Work& w, const float* Xt, int64_t ld, int64_t rows,
-                    const float* T, float* Zt, float* Zh, float* Zl)
+                    const float* T, float* Zt, float* Zh, float* Zl, bool f16 = false)
 {
+    // T is a Cholesky factor's inverse (upper triangular): up to l_pad = 112
+    // the FP32 FMA kernel streams X once at the bandwidth bound
+    if (xt_supported(g.L)) {
+        launch_xt(h->stream, h->sm_count, Xt, ld, rows, g.l, g.L, T, Zt, Zh ? (f16 ? 2 : 1) : 0, Zh, Zl,
+                  kQSplitScale);
+        return;
+    }
     launch_small_panel(h->stream, T, g.l, g.L, w.Th, w.Tl);
     int64_t splits = 0;
-    launch_tc_gemm(h->stream, h->sm_count, true, Xt, g.L, rows, ld, w.Th, w.Tl, g.L, g.L, Zt, Zh, Zl, ld, nullptr, 1,
-                   &splits, w.status, nullptr);
+    TcExtra x{};
+    if (f16 && Zh) {
+        x.out_h16 = (uint16_t*)Zh;
+        x.out_l16 = (uint16_t*)Zl;
+        x.split_sc_const = kQSplitScale;
+    }
+    launch_tc_gemm(h->stream, h->sm_count, true, Xt, g.L, rows, ld, w.Th, w.Tl, g.L, g.L, Zt, f16 ? nullptr : Zh,
+                   f16 ? nullptr : Zl, ld, nullptr, 1, &splits, w.status, nullptr, 0, 0, 0, 0, 0, nullptr, nullptr,
+                   nullptr, f16 ? &x : nullptr);
 }
 
-// Y = A_logical X with X = Pt (n x l) -> Yt (m x l) [+ TF32 split of Y].
+// Y = A_logical X with X = Pt (n x l) -> Yt (m x l).  The first pass
+// (first = true) measures ||A||_F^2 (fro2) and, for the FP16x3 form, max|A|;
+// later passes use the FP16x3 form where the geometry has it (the panel's
+// FP16 split in Pth / Ptl, scales in Ppinv).  Y's TF32 split goes to Yth /
+// Ytl only when the Gram of Y runs on the pass kernel (wide sketches).
 // In mixed precision the product runs in BF16 on the BF16 copy of the panel.
 // With an affine map (randomized PCA) the result is Y = X_pca Pt: the panel
 // was already scaled by split_panel when the variables are the columns;
 // here the correction Y = r (A P - u h^T) follows the pass, with
 // h = P^T mu (columns: u = 1, r = 1) or h = P^T 1 (rows: u = mu, r = c).
-void apply_A(rsvdgb_handle* h, const Geom& g, Work& w, double* fro2)
+void apply_A(rsvdgb_handle* h, const Geom& g, Work& w, double* fro2, bool first)
 {
     const Affine* af = g.aff;
     const bool corr = af && (af->mu || (af->rows && af->c));
@@ -446,32 +483,45 @@ void apply_A(rsvdgb_handle* h, const Geom& g, Work& w, double* fro2)
         }
         fr = af->rows ? af->c : nullptr;
     }
-    pass_over_A(h, g, w, true, w.Pt, w.Pth, w.Ptl, w.Yt, w.Yth, w.Ytl, af ? nullptr : fro2,
-                g.bf16 ? w.Ptb : nullptr, 0, fh, fu, fr);
+    const bool y_split = g.use_tc && !tc_gram_direct(g, w.Yt, g.ldm);
+    TcExtra x{};
+    const bool h16 = g.h16 && !first && !g.bf16;
+    if (g.h16 && first) x.amax_out = w.amax;
+    if (h16) {
+        x.h16 = 1;
+        x.amax_in = w.amax;
+        x.pinv = w.Ppinv;
+    }
+    pass_over_A(h, g, w, true, w.Pt, w.Pth, w.Ptl, w.Yt, y_split ? w.Yth : nullptr, y_split ? w.Ytl : nullptr,
+                af ? nullptr : fro2, g.bf16 ? w.Ptb : nullptr, 0, fh, fu, fr, g.use_tc ? &x : nullptr);
     if (corr && !fused)
         launch_affine_post(h->stream, w.Yt, g.ldm, g.m, g.l, af->rows ? af->c : nullptr,
                            af->rows ? af->mu : nullptr, af->mu ? af->part : nullptr, chunks,
-                           g.use_tc ? w.Yth : nullptr, g.use_tc ? w.Ytl : nullptr);
+                           y_split ? w.Yth : nullptr, y_split ? w.Ytl : nullptr);
 }
 
-// W = A_logical^T Y with Y = Yt (m x l) -> Wt (n x l).  `accurate` keeps the
-// FP32-accurate 3xTF32 product (the projection B = Q^T A); otherwise mixed
-// precision runs it in BF16.  With an affine map: W = X_pca^T Y, i.e.
-// W = c (A^T Y - mu h^T) with h = Y^T 1 (variables = columns), or
-// W = A^T (c Y) - 1 h^T with h = (c Y)^T mu (rows; c Y staged in Qt).
-void apply_At(rsvdgb_handle* h, const Geom& g, Work& w, bool accurate)
+// W = A_logical^T X with the m-side basis X (m x l, column-major, ldm; its
+// split in Xh / Xl: TF32 hi / lo, or the FP16 hi / lo of kQSplitScale X when
+// the geometry runs FP16x3) -> Wt (n x l).  `accurate` keeps the
+// FP32-accurate product (the projection B = Q^T A); otherwise mixed precision
+// runs it in BF16.  With an affine map: W = X_pca^T X, i.e.
+// W = c (A^T X - mu h^T) with h = X^T 1 (variables = columns), or
+// W = A^T (c X) - 1 h^T with h = (c X)^T mu (rows; c X staged in the scratch
+// buffer S with its TF32 split Sh / Sl).
+void apply_At(rsvdgb_handle* h, const Geom& g, Work& w, bool accurate, const float* X, const float* Xh,
+              const float* Xl, float* S, float* Sh, float* Sl)
 {
     const Affine* af = g.aff;
     const cudaStream_t s = h->stream;
     const bool mixed = g.bf16 && !accurate;
-    const float *Y = w.Yt, *Yh = w.Yth, *Yl = w.Ytl;
+    const float *Y = X, *Yh = Xh, *Yl = Xl;
     if (af && af->rows && af->c) {
         const bool want_split = g.use_tc && !mixed;
-        launch_scale_rows(s, w.Yt, g.ldm, g.m, g.l, g.L, af->c, w.Qt, want_split ? w.Qth : nullptr,
-                          want_split ? w.Qtl : nullptr);
-        Y = w.Qt;
-        Yh = w.Qth;
-        Yl = w.Qtl;
+        launch_scale_rows(s, X, g.ldm, g.m, g.l, g.L, af->c, S, want_split ? Sh : nullptr,
+                          want_split ? Sl : nullptr);
+        Y = S;
+        Yh = Sh;
+        Yl = Sl;
     }
     int chunks = 0;
     if (af && af->mu)
@@ -480,18 +530,27 @@ void apply_At(rsvdgb_handle* h, const Geom& g, Work& w, bool accurate)
         launch_to_bf16(s, Y, g.ldm, g.m, g.l, g.L, w.Ytb);
         pass_over_A(h, g, w, false, Y, nullptr, nullptr, w.Wt, nullptr, nullptr, nullptr, w.Ytb);
     } else {
+        TcExtra x{};
+        if (g.h16) {
+            x.h16 = 1;
+            x.amax_in = w.amax;
+            x.pinv = w.Qpinv;
+        }
         // the projection B = Q^T A (accurate) keeps its scale: short accumulation chains
-    pass_over_A(h, g, w, false, Y, Yh, Yl, w.Wt, nullptr, nullptr, nullptr, nullptr, accurate ? kExactChunk : 0);
+        pass_over_A(h, g, w, false, Y, Yh, Yl, w.Wt, nullptr, nullptr, nullptr, nullptr, accurate ? kExactChunk : 0,
+                    nullptr, nullptr, nullptr, g.h16 ? &x : nullptr);
     }
     if (af && (af->mu || (!af->rows && af->c)))
         launch_affine_post(s, w.Wt, g.ldn, g.n, g.l, af->rows ? nullptr : af->c, af->rows ? nullptr : af->mu,
                            af->mu ? af->part : nullptr, chunks, nullptr, nullptr);
 }
 
-// After the panel Pt changed: its TF32 split (or BF16 copy) for the
-// tensor-core engine.  With an affine map whose variables are the logical
-// columns, the panel is first scaled by the multipliers (P <- diag(c) P).
-void split_panel(cudaStream_t s, const Geom& g, Work& w)
+// After the panel Pt changed: its split for the tensor-core engine -- TF32
+// hi / lo for the first pass, the scaled FP16 hi / lo (with Ppinv) for the
+// later FP16x3 passes -- or its BF16 copy in mixed precision.  With an affine
+// map whose variables are the logical columns, the panel is first scaled by
+// the multipliers (P <- diag(c) P).
+void split_panel(cudaStream_t s, const Geom& g, Work& w, bool first)
 {
     if (g.aff && !g.aff->rows && g.aff->c) {
         const bool tf = g.use_tc && !g.bf16;
@@ -501,6 +560,8 @@ void split_panel(cudaStream_t s, const Geom& g, Work& w)
     }
     if (g.bf16)
         launch_to_bf16(s, w.Pt, g.ldn, g.n, g.l, g.L, w.Ptb);
+    else if (g.h16 && !first)
+        launch_panel_f16(s, w.Pt, g.ldn, g.n, g.l, g.L, (uint16_t*)w.Pth, (uint16_t*)w.Ptl, w.Ppinv);
     else if (g.use_tc)
         launch_split_tf32(s, w.Pt, g.ldn, g.n, g.l, g.L, w.Pth, w.Ptl);
 }
@@ -618,8 +679,8 @@ void sketch(rsvdgb_handle* h, const Geom& g, Work& w, int sdist, uint64_t seed)
 {
     const cudaStream_t s = h->stream;
     launch_omega(s, g.n, g.ldn, g.l, g.L, seed, sdist, w.Pt, g.ldn);
-    split_panel(s, g, w);
-    apply_A(h, g, w, w.fro2);
+    split_panel(s, g, w, true);
+    apply_A(h, g, w, w.fro2, true);
     if (g.use_tc)
         tc_gram(h, g, w, w.Yt, w.Yth, w.Ytl, g.ldm, g.m);
     else
@@ -675,11 +736,18 @@ int rid_tail(rsvdgb_handle* h, const Geom& g, Work& w, int k, const RidSpec& r)
     return RSVDGB_OK;
 }
 
+int engine_code(const Geom& g)
+{
+    return !g.use_tc ? RSVDGB_ENGINE_SIMT : (g.h16 ? RSVDGB_ENGINE_TC : RSVDGB_ENGINE_TC_TF32);
+}
+
 int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, const Outputs& o,
              const Learned* lc = nullptr, const PcaSpec* pca = nullptr)
 {
     const cudaStream_t s = h->stream;
     const int sm = h->sm_count;
+    // the randomized PCA's implicit centring runs on the 3xTF32 passes
+    if (pca) g.h16 = false;
     Carve probe(nullptr);
     Work w{};
     const int L_lo = lc ? (int)round_up(std::min<int64_t>((int64_t)k + 2, g.n), 16) : 0;
@@ -689,7 +757,8 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
     Carve c(h->ws);
     carve_work(c, g, sm, w, L_lo);
 
-    launch_clear_scalars(s, w.status, w.breakdowns, w.fro2);
+    // the m-side bases carry the fixed FP16 split scale kQSplitScale
+    launch_clear_scalars(s, w.status, w.breakdowns, w.fro2, w.amax, w.Qpinv, g.L, 1.f / kQSplitScale);
     Affine aff{};
     if (pca) {
         // randomized PCA: per-variable centre and scale in one pass over A;
@@ -732,21 +801,30 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
             gram(s, sm, w.Yt, g.ldm, g.m, g.l, w.part, w.G);
     }
     const int l = g.l;
+    // split of an m-side basis for the A^T-side pass that reads it: none in
+    // mixed precision (BF16 copy), FP16 with the FP16x3 passes, else TF32
+    const bool q_split = g.use_tc && !g.bf16;
     // step 4: subspace iterations
     for (int it = 0; it < q; ++it) {
-        // Q = qr(Y): only the span is carried forward, so one Cholesky step
-        // (Q = Y T); A^T Q = (A^T Y) T.
+        // Q = qr(Y) by one Cholesky step, Q = Y R^{-1}: only the span is carried
+        // forward.  Q is formed before A^T Q so that the directions of small
+        // singular values keep their relative accuracy (A^T Y T would carry
+        // them at the size sigma^2 / sigma_1^2 within its columns).
         launch_chol_inv(s, w.G, l, 0.f, w.R1, w.T, w.status, w.breakdowns);
-        apply_At(h, g, w, false);
-        times_small(s, sm, w.Wt, g.ldn, g.n, l, w.T, w.Zt, w.part);
+        if (g.use_tc)
+            tc_times_small(h, g, w, w.Yt, g.ldm, g.m, w.T, w.Qt, q_split ? w.Qth : nullptr,
+                           q_split ? w.Qtl : nullptr, g.h16);
+        else
+            times_small(s, sm, w.Yt, g.ldm, g.m, l, w.T, w.Qt, w.part);
+        apply_At(h, g, w, false, w.Qt, w.Qth, w.Qtl, w.Yt, w.Yth, w.Ytl);
         // Q = qr(A^T Q) on the n side: here too only the span is carried
         // forward, so one CholeskyQR step, Q_n = Z R^{-1}, into the panel
-        gram(s, sm, w.Zt, g.ldn, g.n, l, w.part, w.G, g.use_tc ? (int)g.L : 0, w.status);
+        gram(s, sm, w.Wt, g.ldn, g.n, l, w.part, w.G, g.use_tc ? (int)g.L : 0, w.status);
         launch_chol_inv(s, w.G, l, 0.f, w.R1, w.T1, w.status, w.breakdowns);
-        times_small(s, sm, w.Zt, g.ldn, g.n, l, w.T1, w.Pt, w.part);
-        split_panel(s, g, w);
+        times_small(s, sm, w.Wt, g.ldn, g.n, l, w.T1, w.Pt, w.part);
+        split_panel(s, g, w, false);
         // Y = A Q
-        apply_A(h, g, w, nullptr);
+        apply_A(h, g, w, nullptr, false);
         if (g.use_tc)
             tc_gram(h, g, w, w.Yt, w.Yth, w.Ytl, g.ldm, g.m);
         else
@@ -766,16 +844,16 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
     }
     launch_chol_inv(s, w.G, l, 0.f, w.R2, w.T2, w.status, w.breakdowns);
     if (g.use_tc)
-        tc_times_small(h, g, w, w.Qt, g.ldm, g.m, w.T2, w.Yt, w.Yth, w.Ytl);
+        tc_times_small(h, g, w, w.Qt, g.ldm, g.m, w.T2, w.Yt, w.Yth, w.Ytl, g.h16);
     else
         times_small(s, sm, w.Qt, g.ldm, g.m, l, w.T2, w.Yt, w.part);
     // step 10: B^T = A^T Q (n x l, column-major: row j of B is contiguous)
-    apply_At(h, g, w, true);
+    apply_At(h, g, w, true, w.Yt, w.Yth, w.Ytl, w.Qt, w.Qth, w.Qtl);
     if (o.rid) {
         const int rc = rid_tail(h, g, w, k, *o.rid);
         if (rc) return rc;
-        launch_finalize_info(s, nullptr, 0, k, nullptr, w.fro2, w.status, w.breakdowns, q, l - k,
-                             g.use_tc ? RSVDGB_ENGINE_TC : RSVDGB_ENGINE_SIMT, nullptr, o.info);
+        launch_finalize_info(s, nullptr, 0, k, nullptr, w.fro2, w.status, w.breakdowns, q, l - k, engine_code(g),
+                             nullptr, o.info);
         RSVDGB_CUDA_TRY(cudaGetLastError());
         return RSVDGB_OK;
     }
@@ -816,7 +894,7 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
         // through a cheap Gram of B (sigma unused).
     }
     launch_finalize_info(s, o.d ? w.sigma : nullptr, o.d ? l : 0, k, o.d, w.fro2, w.status, w.breakdowns, q,
-                         l - k, g.use_tc ? RSVDGB_ENGINE_TC : RSVDGB_ENGINE_SIMT, o.d ? w.sweeps : nullptr, o.info);
+                         l - k, engine_code(g), o.d ? w.sweeps : nullptr, o.info);
     // Lambda = Sigma^2 / (m - 1) over the singular values just copied to d
     if (pca) launch_pca_values(s, w.sigma, k, pca->m_obs, pca->eig, pca->sdev);
     RSVDGB_CUDA_TRY(cudaGetLastError());
@@ -867,10 +945,11 @@ int make_geom(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int l
     g.ldn = round_up(g.n, 32);
     g.L = (int)round_up(g.l, 16);
     if (g.l > kMaxL) return RSVDGB_ERR_UNSUPPORTED;
-    if (engine < RSVDGB_ENGINE_AUTO || engine > RSVDGB_ENGINE_TC) return RSVDGB_ERR_INVALID_ARG;
+    if (engine < RSVDGB_ENGINE_AUTO || engine > RSVDGB_ENGINE_TC_TF32) return RSVDGB_ERR_INVALID_ARG;
     const bool tc_ok = tc_pass_supported(g.sm(), g.sn(), g.lda, g.L, A, g.a_bf16);
-    if (engine == RSVDGB_ENGINE_TC && !tc_ok) return RSVDGB_ERR_UNSUPPORTED;
+    if ((engine == RSVDGB_ENGINE_TC || engine == RSVDGB_ENGINE_TC_TF32) && !tc_ok) return RSVDGB_ERR_UNSUPPORTED;
     g.use_tc = (engine != RSVDGB_ENGINE_SIMT) && tc_ok;
+    g.h16 = g.use_tc && engine != RSVDGB_ENGINE_TC_TF32;
     if (prec != RSVDGB_PREC_FP32 && prec != RSVDGB_PREC_BF16_SKETCH) return RSVDGB_ERR_INVALID_ARG;
     g.bf16 = (prec == RSVDGB_PREC_BF16_SKETCH);
     if (g.bf16 && !g.use_tc) return RSVDGB_ERR_UNSUPPORTED;  // mixed precision runs on the tensor cores
@@ -1422,13 +1501,14 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
     if (!A || !X || !Y || m < 1 || n < 1 || l < 1 || lda < n) return RSVDGB_ERR_INVALID_ARG;
     if (dtype != RSVDGB_F32 && dtype != RSVDGB_BF16) return RSVDGB_ERR_INVALID_ARG;
     if (ldx < l || ldy < l) return RSVDGB_ERR_INVALID_ARG;
-    if (engine < RSVDGB_ENGINE_AUTO || engine > RSVDGB_ENGINE_TC) return RSVDGB_ERR_INVALID_ARG;
+    if (engine < RSVDGB_ENGINE_AUTO || engine > RSVDGB_ENGINE_TC_TF32) return RSVDGB_ERR_INVALID_ARG;
     if (prec != RSVDGB_PREC_FP32 && prec != RSVDGB_PREC_BF16_SKETCH) return RSVDGB_ERR_INVALID_ARG;
     const bool bf = prec == RSVDGB_PREC_BF16_SKETCH;
+    const bool want_tc = engine == RSVDGB_ENGINE_TC || engine == RSVDGB_ENGINE_TC_TF32;
     const int64_t M = transpose ? n : m, K = transpose ? m : n;
     const int L = (int)round_up(l, 16);
     const bool tc_ok = l <= 256 && tc_pass_supported(m, n, lda, L, A, dtype == RSVDGB_BF16);
-    if ((engine == RSVDGB_ENGINE_TC || bf) && !tc_ok) return RSVDGB_ERR_UNSUPPORTED;
+    if ((want_tc || bf) && !tc_ok) return RSVDGB_ERR_UNSUPPORTED;
     if (bf && engine == RSVDGB_ENGINE_SIMT) return RSVDGB_ERR_UNSUPPORTED;
     if (engine == RSVDGB_ENGINE_SIMT || !tc_ok) {
         const int64_t tiles = ceil_div(M, 64) * ceil_div(l, 64);
@@ -1450,6 +1530,7 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
     probe.take<float>(L * ldM);
     probe.take<float>(splits * L * ldM);
     probe.take<int>(4);
+    probe.take<float>(L);
     rc = ensure_workspace(h, probe.off + 1024);
     if (rc) return rc;
     Carve c(h->ws);
@@ -1459,8 +1540,10 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
     float* Yc = c.take<float>(L * ldM);
     float* part = c.take<float>(splits * L * ldM);
     int* status = c.take<int>(4);
+    float* pinv = c.take<float>(L);
+    unsigned int* amax = (unsigned int*)(status + 1);
     const cudaStream_t s = h->stream;
-    RSVDGB_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    RSVDGB_CUDA_TRY(cudaMemsetAsync(status, 0, 2 * sizeof(int), s));
     launch_rowmajor_to_colmajor(s, X, ldx, K, l, L, Xc, ldK);
     int64_t used = 0;
     if (bf) {
@@ -1468,6 +1551,17 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
         rc = launch_tc_gemm(s, h->sm_count, transpose, (const float*)A, m, n, lda, Xh, nullptr, ldK, L, Yc, nullptr,
                             nullptr, ldM, part, transpose ? 0 : 1, &used, status, nullptr, 0, 0, 1,
                             dtype == RSVDGB_BF16);
+    } else if (engine != RSVDGB_ENGINE_TC_TF32) {
+        // scaled FP16x3: max|A| first (a rSVD takes it from its first pass)
+        launch_absmax(s, h->sm_count, A, lda, dtype == RSVDGB_BF16, m, n, amax);
+        launch_panel_f16(s, Xc, ldK, K, l, L, (uint16_t*)Xh, (uint16_t*)Xl, pinv);
+        TcExtra x{};
+        x.h16 = 1;
+        x.amax_in = amax;
+        x.pinv = pinv;
+        rc = launch_tc_gemm(s, h->sm_count, transpose, (const float*)A, m, n, lda, Xh, Xl, ldK, L, Yc, nullptr,
+                            nullptr, ldM, part, transpose ? 0 : 1, &used, status, nullptr, 0, 0, 0,
+                            dtype == RSVDGB_BF16, kExactChunk, nullptr, nullptr, nullptr, &x);
     } else {
         launch_split_tf32(s, Xc, ldK, K, l, L, Xh, Xl);
         rc = launch_tc_gemm(s, h->sm_count, transpose, (const float*)A, m, n, lda, Xh, Xl, ldK, L, Yc, nullptr,

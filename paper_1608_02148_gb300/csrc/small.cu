@@ -728,11 +728,16 @@ __global__ void finalize_info_kernel(const float* __restrict__ sigma, int l, int
     }
 }
 
-__global__ void clear_scalars_kernel(int* status, int* breakdowns, double* fro2)
+__global__ void clear_scalars_kernel(int* status, int* breakdowns, double* fro2, unsigned int* amax, float* fillv,
+                                     int nfill, float fillval)
 {
-    if (status) *status = 0;
-    if (breakdowns) *breakdowns = 0;
-    if (fro2) *fro2 = 0.0;
+    if (threadIdx.x == 0) {
+        if (status) *status = 0;
+        if (breakdowns) *breakdowns = 0;
+        if (fro2) *fro2 = 0.0;
+        if (amax) *amax = 0u;
+    }
+    for (int i = threadIdx.x; i < nfill; i += blockDim.x) fillv[i] = fillval;
 }
 
 __global__ void split_tf32_kernel(const float* __restrict__ in, int64_t ld, int64_t rows, int l, int l_pad,
@@ -917,9 +922,11 @@ void launch_finalize_info(cudaStream_t s, const float* sigma, int l, int k, floa
                                            info); count_launches();
 }
 
-void launch_clear_scalars(cudaStream_t s, int* status, int* breakdowns, double* fro2)
+void launch_clear_scalars(cudaStream_t s, int* status, int* breakdowns, double* fro2, unsigned int* amax,
+                          float* fillv, int nfill, float fillval)
 {
-    clear_scalars_kernel<<<1, 1, 0, s>>>(status, breakdowns, fro2); count_launches();
+    clear_scalars_kernel<<<1, 256, 0, s>>>(status, breakdowns, fro2, amax, fillv, fillv ? nfill : 0, fillval);
+    count_launches();
 }
 
 void launch_split_tf32(cudaStream_t s, const float* in, int64_t ld, int64_t rows, int l, int l_pad, float* hi,

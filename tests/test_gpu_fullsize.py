@@ -98,7 +98,7 @@ def test_spiked_200000x2000_fp32_matches_oracle(rs, handle, spiked200k):
 
 def test_spiked_200000x2000_bf16_sketch_at_equal_error(rs, handle, spiked200k):
     A, A_host, ref, (k, p, q) = spiked200k
-    _check_equal_error(rs, handle, A, A_host, ref, k, p, q, seed=0, prec="bf16")
+    _check_equal_error(rs, handle, A, A_host, ref, k, p, q, seed=0, prec="bf16_sketch")
 
 
 @pytest.fixture(scope="module")
@@ -118,4 +118,4 @@ def test_step_bf16_20000x5000_fp32_matches_oracle(rs, handle, step20k):
 
 def test_step_bf16_20000x5000_mixed_at_equal_error(rs, handle, step20k):
     A, bits, ref, (k, p, q) = step20k
-    _check_equal_error(rs, handle, A, bits, ref, k, p, q, seed=1, prec="bf16")
+    _check_equal_error(rs, handle, A, bits, ref, k, p, q, seed=1, prec="bf16_sketch")

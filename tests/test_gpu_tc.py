@@ -1,10 +1,17 @@
-"""Parity of the tensor-core (tcgen05 + TMA, 3xTF32) passes over A with the
-FP64 oracle, through the C ABI.
+"""Parity of the tensor-core (tcgen05 + TMA) passes over A with the FP64
+oracle, through the C ABI, in both FP32-accurate forms.
 
-Error model of one 3xTF32 product: a_hi p_hi + a_hi p_lo + a_lo p_hi with the
-lo parts rounded to TF32 and a_lo p_lo dropped leaves at most 2^-20 |a||p| per
-product; FP32 accumulation adds K u32 |a||p|.  The bound below is
-(2^-19 + 2 K u32) (|A| |X|) element by element.
+Error model of one 3xTF32 product (engine tc_tf32): a_hi p_hi + a_hi p_lo +
+a_lo p_hi with the lo parts rounded to TF32 and a_lo p_lo dropped leaves at
+most 2^-20 |a||p| per product; FP32 accumulation adds K u32 |a||p|.  The
+bound below is (2^-19 + 2 K u32) (|A| |X|) element by element.
+Scaled FP16x3 (engine tc): A scaled by 2^eA and each panel column by 2^ej
+(largest magnitude into [2^13, 2^14)), both split into FP16 hi + lo; the
+same three products leave at most 2^-20 |a||p| while the lo parts are
+normal FP16 numbers, and below that an absolute 2^-25 in scaled units, i.e.
+2^-38 max|A| per element of A (2^-38 max|x_j| per panel element): the bound
+gains K 2^-37 max|A| max|X|, which only matters for rows many orders of
+magnitude below the largest.
 """
 import numpy as np
 import pytest
@@ -37,23 +44,57 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+def _product_bounds(A, X, W, engine):
+    Aa = np.abs(A).astype(np.float64)
+    m, n = A.shape
+    by = (2.0 ** -19 + 2 * n * 2.0 ** -24) * (Aa @ np.abs(X))
+    bz = (2.0 ** -19 + 2 * m * 2.0 ** -24) * (Aa.T @ np.abs(W))
+    if engine == "tc":
+        amax = float(Aa.max())
+        by = by + n * 2.0 ** -37 * amax * np.abs(X).max(axis=0)[None, :]
+        bz = bz + m * 2.0 ** -37 * amax * np.abs(W).max(axis=0)[None, :]
+    return by, bz
+
+
+@pytest.mark.parametrize("engine", ["tc", "tc_tf32"])
 @pytest.mark.parametrize("m,n,l", [(300, 200, 30), (1000, 64, 1), (520, 332, 24), (260, 128, 110),
                                    (64, 640, 8), (1030, 516, 220), (4096, 256, 256), (777, 1000, 112)])
-def test_tc_passes_match_oracle_products(rs, handle, m, n, l):
+def test_tc_passes_match_oracle_products(rs, handle, m, n, l, engine):
     rng = np.random.default_rng(7 * m + n + l)
     A = rng.standard_normal((m, n)).astype(np.float32)
     X = rng.standard_normal((n, l)).astype(np.float32)
     W = rng.standard_normal((m, l)).astype(np.float32)
     Ad = to_dev(A)
-    Y = rs.rsvdgb_pass_ax(handle, Ad, to_dev(X), engine="tc").cpu().numpy().astype(np.float64)
-    Z = rs.rsvdgb_pass_atx(handle, Ad, to_dev(W), engine="tc").cpu().numpy().astype(np.float64)
+    Y = rs.rsvdgb_pass_ax(handle, Ad, to_dev(X), engine=engine).cpu().numpy().astype(np.float64)
+    Z = rs.rsvdgb_pass_atx(handle, Ad, to_dev(W), engine=engine).cpu().numpy().astype(np.float64)
     Yo = oracle.gemm_ax(A, X.astype(np.float64))
     Zo = oracle.gemm_atx(A, W.astype(np.float64))
-    Aa = np.abs(A).astype(np.float64)
-    by = (2.0 ** -19 + 2 * n * 2.0 ** -24) * (Aa @ np.abs(X))
-    bz = (2.0 ** -19 + 2 * m * 2.0 ** -24) * (Aa.T @ np.abs(W))
+    by, bz = _product_bounds(A, X, W, engine)
     assert np.all(np.abs(Y - Yo) <= by), float(np.max(np.abs(Y - Yo) / by))
     assert np.all(np.abs(Z - Zo) <= bz), float(np.max(np.abs(Z - Zo) / bz))
+
+
+@pytest.mark.parametrize("engine", ["tc", "tc_tf32"])
+def test_tc_passes_rows_of_very_different_scale(rs, handle, engine):
+    """Rows and panel columns spread over 2^-30 .. 2^10 of magnitude (and a
+    zero row): the FP16x3 form keeps the relative bound for the rows near
+    max|A| and the absolute floor K 2^-37 max|A| max|x_j| for the others."""
+    rng = np.random.default_rng(99)
+    m, n, l = 1500, 700, 40
+    A = rng.standard_normal((m, n)) * np.exp2(rng.integers(-30, 11, size=(m, 1)))
+    A[17] = 0.0
+    A = A.astype(np.float32)
+    X = (rng.standard_normal((n, l)) * np.exp2(rng.integers(-20, 8, size=(1, l)))).astype(np.float32)
+    W = (rng.standard_normal((m, l)) * np.exp2(rng.integers(-20, 8, size=(1, l)))).astype(np.float32)
+    Ad = to_dev(A)
+    Y = rs.rsvdgb_pass_ax(handle, Ad, to_dev(X), engine=engine).cpu().numpy().astype(np.float64)
+    Z = rs.rsvdgb_pass_atx(handle, Ad, to_dev(W), engine=engine).cpu().numpy().astype(np.float64)
+    Yo = oracle.gemm_ax(A, X.astype(np.float64))
+    Zo = oracle.gemm_atx(A, W.astype(np.float64))
+    by, bz = _product_bounds(A, X, W, engine)
+    assert np.all(np.abs(Y - Yo) <= by), float(np.max(np.abs(Y - Yo) / by))
+    assert np.all(np.abs(Z - Zo) <= bz), float(np.max(np.abs(Z - Zo) / bz))
+    assert np.all(Y[17] == 0.0)
 
 
 def test_tc_rejects_unaligned_rows(rs, handle):
@@ -65,17 +106,19 @@ def test_tc_rejects_unaligned_rows(rs, handle):
     assert e.value.status == 7
 
 
+@pytest.mark.parametrize("engine", ["tc", "tc_tf32"])
 @pytest.mark.parametrize("m,n,k,p,q", [(2000, 1000, 20, 10, 2), (513, 256, 100, 10, 1), (300, 1000, 12, 6, 2),
                                        (400, 232, 200, 20, 1), (4096, 64, 10, 6, 3)])
-def test_tc_rsvd_matches_oracle(rs, handle, m, n, k, p, q):
+def test_tc_rsvd_matches_oracle(rs, handle, m, n, k, p, q, engine):
     import torch
     sigma = inputs.exp_spectrum(min(m, n), 3.0 / min(m, n)) if (m, n) != (2000, 1000) else \
         inputs.exp_spectrum(1000, 1.0 / 20.0)
     A = inputs.planted(m, n, sigma, seed=m + 3 * n)
     d_o, U_o, V_o, Q_o, B_o = oracle.rsvd(A, k, p=p, q=q, seed=5, return_qb=True)
-    d, U, V, info = rs.rsvdgb_rsvd(handle, to_dev(A), k, opts=rs.make_opts(p=p, q=q, seed=5, engine="tc"))
+    d, U, V, info = rs.rsvdgb_rsvd(handle, to_dev(A), k, opts=rs.make_opts(p=p, q=q, seed=5, engine=engine))
     torch.cuda.synchronize()
     assert info.status == 0, info.as_dict()
+    assert info.engine == {"tc": 2, "tc_tf32": 3}[engine]
     assert sigma_err(d.cpu().numpy(), d_o) <= 1e-5, sigma_err(d.cpu().numpy(), d_o)
     sB = np.linalg.svd(B_o, compute_uv=False)
     tol = subspace_tol(sB, k, sB[0])
