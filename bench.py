@@ -47,8 +47,7 @@ WORKLOADS = {
 
 # DRAM bytes (read + write) per byte of A of the FP32 tensor-core pass kernel,
 # averaged over the six passes of one rSVD, from one ncu capture on the
-# 50000 x 2000 workload (the pass kernel's ncu summary under profiles/).  The
-# traffic scales with the rows processed, so the full-size launches carry the
+# 50000 x 2000 workload.  The traffic scales with the rows processed, so the full-size launches carry the
 # same ratio.  None until the current pass kernel has been captured.
 TC_PASS_TRAFFIC_PER_A_BYTE = None
 
@@ -372,8 +371,18 @@ def run_rrpca(rs, h, dev, stream, peaks):
             "L_rel_err_vs_planted": rec, "hbm_roofline_ms": roof_ms, "hbm_frac": roof_ms / ms, "status": res.status}
 
 
+def workload_config(wl, world):
+    """The workload as both arms report it (no implementation keys)."""
+    m, n = wl["m"], wl["n"]
+    a_bytes = m * n * (2 if wl.get("dtype") == "bf16" else 4)
+    return {"workload": wl["desc"], "m": m, "n": n, "k": wl["k"], "p": wl["p"], "q": wl["q"],
+            "l": min(wl["k"] + wl["p"], m, n), "passes_over_A": 2 * wl["q"] + 2,
+            "l2": "A (%.1f GB) larger than L2; no flush needed" % (a_bytes / 1e9),
+            "parallelism": f"replicas x{world}"}
+
+
 def cpu_oracle_time(A_host_rows, wl, seed_omega):
-    """Median-free single timing of the FP64 oracle rSVD on a row block."""
+    """One timing of the FP64 oracle rSVD on a row block (callers take medians)."""
     import oracle
     t0 = time.perf_counter()
     oracle.rsvd(A_host_rows, wl["k"], p=wl["p"], q=wl["q"], seed=seed_omega)
@@ -408,10 +417,11 @@ def run_reference(args, wl):
     line = {"metric": METRIC, "impl": "reference", "value": ms, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["desc"], "m": wl["m"], "n": wl["n"], "k": wl["k"], "p": wl["p"],
-                       "q": wl["q"]},
+            "config": workload_config(wl, world),
+            "implementation": {"prec": "fp64 oracle (plain C, OpenMP)", "engine": "host cores"},
             "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
                              "sample": f"oracle rsvd on a {rows}x{wl['n']} row block of the workload, time x{scale:g}"},
+            "sample_ms_per_step": statistics.median(times) / scale,
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -669,20 +679,20 @@ def main():
             A_rows = A[:rows].view(torch.int16).cpu().numpy().view(np.uint16)
         else:
             A_rows = A[:rows].cpu().numpy()
-        t = cpu_oracle_time(A_rows, wl, 0)
+        reps = [cpu_oracle_time(A_rows, wl, 0) for _ in range(3)]
+        t = statistics.median(reps)
         cpu = {"value": t * (m / rows) * 1e3, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": f"oracle rsvd on rows 0..{rows - 1} of the same A ({rows}x{n}), time x{m / rows:g}"}
+               "sample": f"oracle rsvd on rows 0..{rows - 1} of the same A ({rows}x{n}), median of 3, "
+                         f"time x{m / rows:g}",
+               "sample_s": [round(x, 4) for x in reps]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16-stored A, f32 arithmetic" if A.dtype == torch.bfloat16 else "f32",
                 "data": "synthetic",
-                "config": {"workload": wl["desc"], "m": m, "n": n, "k": k, "p": wl["p"], "q": wl["q"], "l": l,
-                           "prec": args.prec, "engine": engine, "engine_requested": args.engine,
-                           "passes_over_A": passes,
-                           "l2": "A (%.1f GB) larger than L2; no flush needed" % (a_bytes / 1e9),
-                           "parallelism": f"replicas x{world}"},
+                "config": workload_config(wl, world),
+                "implementation": {"prec": args.prec, "engine": engine, "engine_requested": args.engine},
                 "hbm_roofline": {"time_ms": roof_ms, "frac_of_step": roof_ms / ms_per_step,
                                  "peak_gbs": hbm, "peak_source": peak_kind},
                 "hbm_roofline_nominal": {"time_ms": passes * a_bytes / (NOMINAL_HBM_TBS * 1e12) * 1e3,

@@ -464,6 +464,18 @@ int rsvdgb_mlp_grad(rsvdgb_handle* h, const float* P, const float* X, const floa
                     float* loss);
 
 /*
+ * Test hook for failure detection (the paper has no counterpart).  Arms the
+ * handle so that the next rsvdgb_rid / rsvdgb_rcur call runs its pivoted-QR
+ * kernel with one CTA leaving out its arrival at the first grid barrier and
+ * every barrier wait bounded by spin_ticks clock64 ticks (spin_ticks >= 1).
+ * All waits then run out: the kernel records RSVDGB_ERR_TIMEOUT in that
+ * call's info.status and returns, and the CUDA context stays usable -- no
+ * device fault is raised.  The setting is consumed by that launch.
+ * Returns RSVDGB_OK or RSVDGB_ERR_INVALID_ARG.
+ */
+int rsvdgb_test_pqr_barrier(rsvdgb_handle* h, int64_t spin_ticks);
+
+/*
  * Instrumentation (not part of the paper's method).
  *  rsvdgb_profile_passes : when enable != 0, the handle records a CUDA event
  *      pair on its stream around every launch of a pass kernel over A (the

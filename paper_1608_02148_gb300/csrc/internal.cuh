@@ -274,9 +274,13 @@ void launch_pca_values(cudaStream_t s, const float* sigma, int k, int64_t m_obs,
 // R rows (k x N row-major, optional), one cooperative launch with a bounded
 // grid barrier.  Workspace: nrm (N doubles), max_slots (double, int64)
 // slots, one counter.
+// spin_limit bounds each barrier wait (clock64 ticks; <= 0: the default of
+// about 2 s); absent_cta >= 0 (a test hook) makes that CTA skip its arrival at
+// the first barrier, so that every wait runs out and RSVDGB_ERR_TIMEOUT is
+// recorded.
 int launch_pqr(cudaStream_t s, int sm_count, const float* X, int64_t ldx, int r, int64_t N, int k, int* piv,
                float* R, double* nrm, double* slot_val, int64_t* slot_idx, int max_slots, unsigned int* bar,
-               int* status);
+               int* status, long long spin_limit = 0, int absent_cta = -1);
 // Z (k x N, ld ldz) of the ID from R and the pivots (Algorithm id steps 2-5).
 void launch_id_solve(cudaStream_t s, const float* R, int64_t N, int k, const int* piv, float* Z, int64_t ldz,
                      int* status);

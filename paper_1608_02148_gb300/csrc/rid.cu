@@ -40,6 +40,8 @@ struct PqrArgs {
     int64_t* slot_idx;
     unsigned int* bar;  // grid barrier counter (zero at launch)
     int* status;
+    long long spin_limit;  // bound of each barrier wait in clock64 ticks
+    int absent_cta;        // test hook: this CTA skips its arrival at the first barrier (-1: none)
 };
 
 __device__ __forceinline__ double warp_sum_d(double v)
@@ -64,18 +66,20 @@ __device__ __forceinline__ bool better(double v, int64_t i, double bv, int64_t b
     return v > bv || (v == bv && i < bi);
 }
 
-// Grid-wide barrier on a monotone counter; bounded (about 2 s), on expiry
-// RSVDGB_ERR_TIMEOUT is recorded and false returned.
-__device__ bool grid_barrier(unsigned int* bar, unsigned int target, int* status, volatile int* flag)
+// Grid-wide barrier on a monotone counter; bounded (spin_limit ticks, about
+// 2 s by default), on expiry RSVDGB_ERR_TIMEOUT is recorded and false
+// returned.  arrive = false (a test hook) waits without arriving.
+__device__ bool grid_barrier(unsigned int* bar, unsigned int target, int* status, volatile int* flag,
+                             long long spin_limit, bool arrive = true)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        atomicAdd(bar, 1u);
+        if (arrive) atomicAdd(bar, 1u);
         const long long t0 = clock64();
         bool ok = true;
         while (*(volatile unsigned int*)bar < target) {
-            if (clock64() - t0 > dev::kSpinLimit) {
+            if (clock64() - t0 > spin_limit) {
                 ok = false;
                 break;
             }
@@ -184,6 +188,11 @@ __global__ void __launch_bounds__(kPqrThreads, 1) pqr_kernel(PqrArgs a)
     const int r = a.r;
     const int64_t c0 = a.N * b / G, c1 = a.N * (b + 1) / G;
     unsigned int epoch = 0;
+    // CTA 0 writes the pivots (only it does, and only after this): -1 until
+    // a step chooses one, so that a launch left early (a barrier wait that
+    // ran out) hands the gathers and the ID solve only -1 entries
+    if (b == 0)
+        for (int u = threadIdx.x; u < a.k; u += kPqrThreads) a.piv[u] = -1;
 
     // residual norms of this CTA's columns (lane L of a warp owns column
     // j0 + L of each 32-column block), and their maximum
@@ -202,7 +211,8 @@ __global__ void __launch_bounds__(kPqrThreads, 1) pqr_kernel(PqrArgs a)
         }
     }
     block_argmax_to_slot(bv, bi, wv, wi, a, (int)((epoch + 1) & 1));
-    if (!grid_barrier(a.bar, ++epoch * (unsigned)G, a.status, &flag)) return;
+    if (!grid_barrier(a.bar, ++epoch * (unsigned)G, a.status, &flag, a.spin_limit, (int)blockIdx.x != a.absent_cta))
+        return;
 
     for (int t = 0; t < a.k; ++t) {
         {
@@ -324,7 +334,7 @@ __global__ void __launch_bounds__(kPqrThreads, 1) pqr_kernel(PqrArgs a)
             }
         }
         block_argmax_to_slot(bv, bi, wv, wi, a, (int)((epoch + 1) & 1));
-        if (!grid_barrier(a.bar, ++epoch * (unsigned)G, a.status, &flag)) return;
+        if (!grid_barrier(a.bar, ++epoch * (unsigned)G, a.status, &flag, a.spin_limit)) return;
     }
 }
 
@@ -487,7 +497,7 @@ int pqr_max_ctas(int sm_count, size_t smem)
 
 int launch_pqr(cudaStream_t s, int sm_count, const float* X, int64_t ldx, int r, int64_t N, int k, int* piv,
                float* R, double* nrm, double* slot_val, int64_t* slot_idx, int max_slots, unsigned int* bar,
-               int* status)
+               int* status, long long spin_limit, int absent_cta)
 {
     if (r < 1 || r > 256 || k < 1 || k > r || k > 256 || N < k) return RSVDGB_ERR_INVALID_ARG;
     const size_t smem = ((size_t)r * k + r) * sizeof(float);
@@ -499,7 +509,8 @@ int launch_pqr(cudaStream_t s, int sm_count, const float* X, int64_t ldx, int r,
     int G = (int)std::min<int64_t>(std::min<int64_t>(cap, max_slots / 2), ceil_div(N, 32 * kPqrWarps));
     G = std::max(G, 1);
     if (cudaMemsetAsync(bar, 0, sizeof(unsigned int), s) != cudaSuccess) return RSVDGB_ERR_CUDA;
-    PqrArgs a{X, ldx, r, N, k, piv, R, nrm, slot_val, slot_idx, bar, status};
+    PqrArgs a{X, ldx, r, N, k, piv, R, nrm, slot_val, slot_idx, bar, status,
+              spin_limit > 0 ? spin_limit : dev::kSpinLimit, absent_cta};
     void* params[] = {&a};
     if (cudaLaunchCooperativeKernel((const void*)pqr_kernel, dim3(G), dim3(kPqrThreads), params, smem, s) !=
         cudaSuccess)

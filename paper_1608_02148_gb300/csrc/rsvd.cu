@@ -60,6 +60,11 @@ struct rsvdgb_handle {
     void* aux = nullptr;  // iterates of rsvdgb_rrpca (kept apart from ws, which its rSVDs resize)
     size_t aux_bytes = 0;
     PassProfile prof;
+    // test hook (rsvdgb_test_pqr_barrier): the next pivoted-QR launch of a
+    // rid / rcur call leaves CTA 0's first grid-barrier arrival out and bounds
+    // the waits by test_spin ticks; consumed by that launch
+    int test_pqr_absent = 0;
+    long long test_spin = 0;
     BatchedPlan* batched = nullptr;  // plan of the last batch layout
     float* ctl_params = nullptr;     // learned (q, p) controller (device, kMlpParams floats)
     float* ctl_scratch = nullptr;    // features, network output, decision (device)
@@ -704,8 +709,11 @@ int rid_tail(rsvdgb_handle* h, const Geom& g, Work& w, int k, const RidSpec& r)
     const int l = g.l;
     // B (l x n, column j contiguous) from B^T
     launch_transpose_cm(s, w.Wt, g.ldn, g.n, l, w.Xb, g.L);
+    const int absent = h->test_pqr_absent ? 0 : -1;
+    const long long spin = h->test_pqr_absent ? h->test_spin : 0;
+    h->test_pqr_absent = 0;
     int rc = launch_pqr(s, sm, w.Xb, g.L, l, g.n, k, w.piv, w.Rk, w.pnrm, w.slot_v, w.slot_i, kPqrSlots, w.bar,
-                        w.status);
+                        w.status, spin, absent);
     if (rc) return rc;
     float* Z = r.Z ? r.Z : w.Zw;
     const int64_t ldz = r.Z ? r.ldz : g.n;
@@ -1178,8 +1186,14 @@ int rsvdgb_rsvd_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int6
     rc = ensure_host_stage(h, off);
     if (rc) return rc;
     char* base = (char*)h->host_stage;
-    RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(base + oA, cols_s * esz, A, lda * esz, cols_s * esz, rows_s,
-                                      cudaMemcpyHostToDevice, h->stream));
+    // contiguous rows: one linear copy (the pitched form ran at about two
+    // thirds of the linear copy's rate on the host-to-device link)
+    if (lda == cols_s)
+        RSVDGB_CUDA_TRY(cudaMemcpyAsync(base + oA, A, (size_t)rows_s * cols_s * esz, cudaMemcpyHostToDevice,
+                                        h->stream));
+    else
+        RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(base + oA, cols_s * esz, A, lda * esz, cols_s * esz, rows_s,
+                                          cudaMemcpyHostToDevice, h->stream));
     rc = rsvdgb_rsvd(h, base + oA, m, n, cols_s, dtype, k, nu, nv, &o, (float*)(base + od),
                      nu > 0 ? (float*)(base + oU) : nullptr, std::max(nu, 1), nv > 0 ? (float*)(base + oV) : nullptr,
                      std::max(nv, 1), (rsvdgb_info*)(base + oI));
@@ -1277,8 +1291,12 @@ int rsvdgb_rpca_host(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int6
     if (rc) return rc;
     char* base = (char*)h->host_stage;
     auto dev = [&](size_t o_) { return (float*)(base + o_); };
-    RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(base + oA, cols_s * esz, A, lda * esz, cols_s * esz, rows_s,
-                                      cudaMemcpyHostToDevice, h->stream));
+    if (lda == cols_s)
+        RSVDGB_CUDA_TRY(cudaMemcpyAsync(base + oA, A, (size_t)rows_s * cols_s * esz, cudaMemcpyHostToDevice,
+                                        h->stream));
+    else
+        RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(base + oA, cols_s * esz, A, lda * esz, cols_s * esz, rows_s,
+                                          cudaMemcpyHostToDevice, h->stream));
     rc = rsvdgb_rpca(h, base + oA, m, n, cols_s, dtype, k, center, scale, &o, rotation ? dev(oR) : nullptr, k,
                      dev(oE), sdev ? dev(oS) : nullptr, x ? dev(oX) : nullptr, k,
                      center_out ? dev(oC) : nullptr, scale_out ? dev(oSc) : nullptr, (rsvdgb_info*)(base + oI));
@@ -1763,6 +1781,16 @@ int rsvdgb_profile_read(rsvdgb_handle* h, double* pass_ms, int64_t* pass_launche
     if (pass_ms) *pass_ms = total;
     if (pass_launches) *pass_launches = (int64_t)h->prof.used;
     if (pass_bytes) *pass_bytes = h->prof.bytes;
+    return RSVDGB_OK;
+}
+
+int rsvdgb_test_pqr_barrier(rsvdgb_handle* h, int64_t spin_ticks)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (spin_ticks < 1) return RSVDGB_ERR_INVALID_ARG;
+    h->test_pqr_absent = 1;
+    h->test_spin = spin_ticks;
     return RSVDGB_OK;
 }
 

@@ -28,7 +28,7 @@ LAYOUT = {"row": 0, "col": 1}
 EXPORTS = ["rsvdgb_create", "rsvdgb_destroy", "rsvdgb_set_stream", "rsvdgb_default_opts", "rsvdgb_status_string",
            "rsvdgb_sketch_width", "rsvdgb_rsvd", "rsvdgb_rsvd_host", "rsvdgb_rqb", "rsvdgb_omega",
            "rsvdgb_pass_ax", "rsvdgb_pass_atx", "rsvdgb_profile_passes", "rsvdgb_profile_read",
-           "rsvdgb_kernel_launches", "rsvdgb_pass_atx_noalloc", "rsvdgb_rsvd_batched",
+           "rsvdgb_kernel_launches", "rsvdgb_pass_atx_noalloc", "rsvdgb_test_pqr_barrier", "rsvdgb_rsvd_batched",
            "rsvdgb_default_train_opts", "rsvdgb_controller_load", "rsvdgb_controller_set",
            "rsvdgb_controller_train", "rsvdgb_controller_features", "rsvdgb_mlp_forward", "rsvdgb_mlp_grad",
            "rsvdgb_rpca", "rsvdgb_rpca_host", "rsvdgb_rid", "rsvdgb_rcur", "rsvdgb_default_rrpca_opts",
@@ -137,6 +137,7 @@ def load(path: Path | str | None = None):
     lib.rsvdgb_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64),
                                         ctypes.POINTER(ctypes.c_double)]
     lib.rsvdgb_pass_atx_noalloc.argtypes = [P, P, I64, I64, I64, I, P, I64, I, P, I64]
+    lib.rsvdgb_test_pqr_barrier.argtypes = [P, I64]
     lib.rsvdgb_rsvd_batched.argtypes = [P, I, ctypes.POINTER(RsvdgbMatrixDesc), I, ctypes.POINTER(RsvdgbOpts),
                                         ctypes.POINTER(RsvdgbResultDesc), P]
     lib.rsvdgb_kernel_launches.argtypes = []
@@ -476,6 +477,13 @@ def rsvdgb_profile_read(h: Handle):
     _check("rsvdgb_profile_read", load().rsvdgb_profile_read(h.ptr, ctypes.byref(ms), ctypes.byref(n),
                                                              ctypes.byref(b)))
     return ms.value, n.value, b.value
+
+
+def rsvdgb_test_pqr_barrier(h: Handle, spin_ticks: int):
+    """Arm the failure-detection test hook: the next rid / rcur call's pivoted
+    QR runs with one CTA absent from its first grid barrier and waits bounded
+    by spin_ticks clock ticks, so it reports RSVDGB_ERR_TIMEOUT."""
+    _check("rsvdgb_test_pqr_barrier", load().rsvdgb_test_pqr_barrier(h.ptr, int(spin_ticks)))
 
 
 def rsvdgb_kernel_launches() -> int:

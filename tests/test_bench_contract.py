@@ -22,6 +22,10 @@ def test_reference_arm_prints_one_contract_line():
     assert line["impl"] == "reference" and line["n_gpus"] == 1 and line["steps"] == 2 and line["warmup"] == 1
     assert line["higher_is_better"] is False and line["unit"] == "ms" and line["value"] > 0
     assert line["config"]["workload"] and line["config"]["m"] == 2000 and line["config"]["n"] == 1000
+    # the same workload dict the GPU arm prints (implementation keys live outside config)
+    sys.path.insert(0, ROOT)
+    import bench
+    assert line["config"] == bench.workload_config(bench.WORKLOADS["planted2k"], 1)
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == line["value"]
     e2e = line["e2e"]

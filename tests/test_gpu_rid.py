@@ -222,3 +222,36 @@ def test_rid_maximal_rank_and_rank_deficiency(rs, handle):
     assert np.all(J2[5:] == -1) and set(J2[J2 >= 0].tolist()) <= set(cols)
     np.testing.assert_array_equal(C2[:, J2 < 0], 0.0)
     np.testing.assert_array_equal(C2[:, J2 >= 0], D[:, J2[J2 >= 0]])
+
+
+@pytest.mark.parametrize("m,n", [(3000, 400), (600, 64)])  # several CTAs; one CTA
+def test_bounded_grid_barrier_wait_runs_out(rs, handle, m, n):
+    """Failure detection without a device fault: the test hook leaves one
+    CTA's arrival at the pivoted QR's first grid barrier out and bounds every
+    wait by 2e6 clock ticks (about 1 ms).  The waits run out, the call reports
+    RSVDGB_ERR_TIMEOUT in its info, the stream completes promptly, and the
+    same handle then computes a correct rid (the context stays usable)."""
+    import time
+    import torch
+    A = inputs.planted(m, n, inputs.exp_spectrum(n, 0.05), seed=m + n)
+    A_dev = to_dev(A)
+    opts = rs.make_opts(p=6, q=1, seed=4)
+    rs.rsvdgb_test_pqr_barrier(handle, 2_000_000)
+    t0 = time.perf_counter()
+    r = rs.rsvdgb_rid(handle, A_dev, 10, opts=opts)
+    torch.cuda.synchronize()
+    assert time.perf_counter() - t0 < 5.0
+    assert r["info"].status == 6, r["info"].as_dict()  # RSVDGB_ERR_TIMEOUT
+    # the hook was consumed: the next call runs normally on the same handle
+    r2 = rs.rsvdgb_rid(handle, A_dev, 10, opts=opts)
+    torch.cuda.synchronize()
+    assert r2["info"].status == 0
+    J = r2["J"].cpu().numpy()
+    assert len(set(J.tolist())) == 10 and J.min() >= 0 and J.max() < n
+    d_o, _, _ = oracle.rsvd(A, 10, p=6, q=1, seed=4)
+    C, Z = r2["C"].cpu().numpy().astype(np.float64), r2["Z"].cpu().numpy().astype(np.float64)
+    # an interpolative decomposition of rank 10 within a few times the optimum
+    opt = np.sqrt(np.sum(inputs.exp_spectrum(n, 0.05)[10:] ** 2))
+    assert np.linalg.norm(A - C @ Z) <= 20 * opt
+    with pytest.raises(rs.RsvdgbError):
+        rs.rsvdgb_test_pqr_barrier(handle, 0)
