@@ -286,6 +286,9 @@ __global__ void __launch_bounds__(NT) pass_at_kernel(const MatDev* __restrict__ 
             }
             __syncthreads();
             if (i0 + 32 < Mt.M) load_chunk(i0 + 32);
+            // each 32-row chunk is summed on its own and then added to the
+            // running sum: the FP32 error grows like 32 + M / 32, not M
+            float cacc[2][4] = {};
 #pragma unroll 8
             for (int ii = 0; ii < 32; ++ii) {
                 const float2 a2 = *(const float2*)&As[ii][2 * ty];
@@ -295,8 +298,12 @@ __global__ void __launch_bounds__(NT) pass_at_kernel(const MatDev* __restrict__ 
 #pragma unroll
                 for (int a = 0; a < 2; ++a)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(av[a], yv[c], acc[a][c]);
+                    for (int c = 0; c < 4; ++c) cacc[a][c] = fmaf(av[a], yv[c], cacc[a][c]);
             }
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[a][c] += cacc[a][c];
             __syncthreads();
         }
 #pragma unroll
@@ -850,8 +857,14 @@ void enqueue(BatchedPlan* pl, cudaStream_t s, int sm_count, rsvdgb_info* infos)
     chol_kernel<<<warps_blocks, 256, 0, s>>>(pl->D, B, pl->part, 0, RB, pl->T, nullptr, pl->status, pl->breakdowns);
     int launches = 3;
     for (int it = 0; it < pl->q; ++it) {
-        // Z = (A^T Y) T = A^T Q; Gram partials of Z
-        pass_at_kernel<<<grid, NT, 0, s>>>(pl->D, pl->it_nc, pl->n_nc, cursor(), pl->Y, pl->T, pl->Z, pl->part);
+        // Q = Y T in place (one Cholesky step; only the span is carried
+        // forward), then Z = A^T Q with the Gram partials of Z.  Forming Q
+        // first keeps the directions of small singular values at their
+        // relative accuracy (A^T Y T would carry them at sigma^2 / sigma_1^2
+        // of A^T Y's columns).
+        tall_small_kernel<<<grid, NT, 0, s>>>(pl->D, pl->it_m, pl->n_m, cursor(), 0, pl->Y, pl->T, pl->Y, nullptr,
+                                              nullptr, nullptr);
+        pass_at_kernel<<<grid, NT, 0, s>>>(pl->D, pl->it_nc, pl->n_nc, cursor(), pl->Y, nullptr, pl->Z, pl->part);
         chol_kernel<<<warps_blocks, 256, 0, s>>>(pl->D, B, pl->part, 1, CB, pl->T1, nullptr, pl->status,
                                                  pl->breakdowns);
         // Gram of Z T1 (not stored), then T2 and Tc = T1 T2
@@ -867,7 +880,7 @@ void enqueue(BatchedPlan* pl, cudaStream_t s, int sm_count, rsvdgb_info* infos)
         pass_a_kernel<<<grid, NT, 0, s>>>(pl->D, pl->it_m, pl->n_m, cursor(), pl->P, pl->Y, pl->part, nullptr);
         chol_kernel<<<warps_blocks, 256, 0, s>>>(pl->D, B, pl->part, 0, RB, pl->T, nullptr, pl->status,
                                                  pl->breakdowns);
-        launches += 8;
+        launches += 9;
     }
     // step 9: Q = qr(Y) by CholeskyQR2: Gram of Y T (not stored), T2, Q = Y (T T2) in place
     tall_small_kernel<<<grid, NT, 0, s>>>(pl->D, pl->it_m, pl->n_m, cursor(), 0, pl->Y, pl->T, nullptr, pl->part,

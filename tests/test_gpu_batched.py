@@ -65,3 +65,43 @@ def test_batched_rejects_wide_sketch(rs):
         assert e.value.status == 7  # l = 40 > 32
     finally:
         h.close()
+
+
+def test_batched_full_size_workload_sampled(rs):
+    """The batched workload the benchmark times: 4096 matrices, m log-uniform
+    in [256, 4096], n in [64, 1024], exponential spectra with decay rates in
+    [0.05, 0.5], k = 16, p = 8, q = 1, one graph launch.  Every matrix reports
+    status 0 and ||A||_F^2 within 1e-5; against the oracle, one by one: the
+    tallest matrices with the fastest decay (where FP32 rounding along the
+    rows meets a large sigma_1 / sigma_l) and a seeded random sample, all
+    under the same sigma and gap-rule tolerances as the single-matrix path."""
+    import torch
+    count, k, p, q = 4096, 16, 8, 1
+    mats, rates = inputs.ragged_batch(count, seed=0x160802148 + 4000, device="cuda")
+    h = rs.Handle(0)
+    try:
+        call = rs.BatchedCall(mats, k)
+        rs.rsvdgb_rsvd_batched(h, call, rs.make_opts(p=p, q=q, seed=3))
+        torch.cuda.synchronize()
+        fro = torch.stack([(A.double() ** 2).sum() for A in mats]).cpu().numpy()
+        for b in range(count):
+            info = call.info(b)
+            assert info.status == 0, (b, info.as_dict())
+            assert abs(info.fro2_A - fro[b]) <= 1e-5 * fro[b], b
+        shapes = np.array([A.shape for A in mats])
+        rates = np.asarray(rates)
+        hard = np.argsort(-(shapes[:, 0] * rates))[:16]  # tall and fast-decaying
+        rng = np.random.default_rng(4000)
+        sample = np.unique(np.concatenate([hard, rng.choice(count, 24, replace=False)]))
+        for b in sample.tolist():
+            An = mats[b].cpu().numpy()
+            d_o, U_o, V_o, Q_o, B_o = oracle.rsvd(An, k, p=p, q=q, seed=3, return_qb=True)
+            d = call.d[b].cpu().numpy()
+            assert sigma_err(d, d_o) <= 1e-5, (b, An.shape, rates[b], sigma_err(d, d_o))
+            sB = np.linalg.svd(B_o, compute_uv=False)
+            tol = subspace_tol(sB, k, sB[0])
+            su = sin_theta(call.U[b].cpu().numpy(), U_o)
+            sv = sin_theta(call.V[b].cpu().numpy(), V_o)
+            assert su <= tol and sv <= tol, (b, An.shape, rates[b], su, sv, tol)
+    finally:
+        h.close()
