@@ -64,6 +64,12 @@ def _load():
     lib.oracle_rqb.restype = I
     lib.oracle_rsvd.argtypes = [P, I, I64, I64, I64, I, I, I, I, U64, P, P, P, P, P]
     lib.oracle_rsvd.restype = I
+    lib.oracle_rqb_ex.argtypes = [P, I, I64, I64, I64, I, I, I, I, U64, I, P, P]
+    lib.oracle_rqb_ex.restype = I
+    lib.oracle_rsvd_ex.argtypes = [P, I, I64, I64, I64, I, I, I, I, U64, I, P, P, P, P, P]
+    lib.oracle_rsvd_ex.restype = I
+    lib.oracle_lu_pivot.argtypes = [I64, I64, P, P, P, P]
+    lib.oracle_lu_pivot.restype = I
     lib.oracle_power_direct.argtypes = [P, I, I64, I64, I64, I64, I, I, U64, P]
     lib.oracle_power_direct.restype = I
     lib.oracle_gemm_ax.argtypes = [P, I, I64, I64, I64, P, I64, P]
@@ -161,22 +167,43 @@ def sketch_width(m: int, n: int, k: int, p: int) -> int:
     return int(_load().oracle_sketch_width(m, n, k, p))
 
 
-def rqb(A: np.ndarray, k: int, p: int = 10, q: int = 2, sdist: str = "normal", seed: int = 0):
-    """Algorithm rqb. For m < n it returns Q, B of the transposed problem."""
+SCHEME = {"qr": 0, "lu": 1}
+
+
+def lu_pivot(Y: np.ndarray):
+    """Pivoted LU of a tall matrix as Algorithm norm_iterations uses it:
+    Y = L U, L (m x l) a row permutation of a unit lower trapezoid in Y's row
+    order, U (l x l) upper triangular, perm the pivot rows.  Returns (L, U, perm)."""
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    m, l = Y.shape
+    L = np.zeros((m, l))
+    U = np.zeros((l, l))
+    perm = np.zeros(l, dtype=np.int64)
+    rc = _load().oracle_lu_pivot(m, l, _ptr(Y), _ptr(L), _ptr(U), _ptr(perm))
+    if rc:
+        raise RuntimeError(f"lu_pivot failed ({rc})")
+    return L, U, perm
+
+
+def rqb(A: np.ndarray, k: int, p: int = 10, q: int = 2, sdist: str = "normal", seed: int = 0, scheme: str = "qr"):
+    """Algorithm rqb with subspace iterations (scheme "qr", Algorithm
+    sub_iterations) or normalized power iterations (scheme "lu", Algorithm
+    norm_iterations). For m < n it returns Q, B of the transposed problem."""
     ptr, code, m, n, lda = _amat(A)
     l = sketch_width(m, n, k, p)
     rows, cols = (m, n) if m >= n else (n, m)
     Q = np.zeros((rows, l))
     B = np.zeros((l, cols))
-    rc = _load().oracle_rqb(ptr, code, m, n, lda, k, p, q, SDIST[sdist], seed, _ptr(Q), _ptr(B))
+    rc = _load().oracle_rqb_ex(ptr, code, m, n, lda, k, p, q, SDIST[sdist], seed, SCHEME[scheme], _ptr(Q), _ptr(B))
     if rc:
         raise RuntimeError(f"oracle rqb failed ({rc})")
     return Q, B
 
 
 def rsvd(A: np.ndarray, k: int, p: int = 10, q: int = 2, sdist: str = "normal", seed: int = 0,
-         return_qb: bool = False):
-    """Algorithm rSVD: returns d (k), U (m x k), V (n x k) [, Q, B]."""
+         return_qb: bool = False, scheme: str = "qr"):
+    """Algorithm rSVD: returns d (k), U (m x k), V (n x k) [, Q, B].  scheme:
+    "qr" (subspace iterations) or "lu" (normalized power iterations)."""
     ptr, code, m, n, lda = _amat(A)
     l = sketch_width(m, n, k, p)
     rows, cols = (m, n) if m >= n else (n, m)
@@ -185,8 +212,8 @@ def rsvd(A: np.ndarray, k: int, p: int = 10, q: int = 2, sdist: str = "normal", 
     V = np.zeros((n, k))
     Q = np.zeros((rows, l)) if return_qb else None
     B = np.zeros((l, cols)) if return_qb else None
-    rc = _load().oracle_rsvd(ptr, code, m, n, lda, k, p, q, SDIST[sdist], seed, _ptr(d), _ptr(U), _ptr(V),
-                             _ptr(Q) if return_qb else None, _ptr(B) if return_qb else None)
+    rc = _load().oracle_rsvd_ex(ptr, code, m, n, lda, k, p, q, SDIST[sdist], seed, SCHEME[scheme], _ptr(d), _ptr(U),
+                                _ptr(V), _ptr(Q) if return_qb else None, _ptr(B) if return_qb else None)
     if rc:
         raise RuntimeError(f"oracle rsvd failed ({rc})")
     if return_qb:

@@ -371,12 +371,76 @@ int oracle_jacobi_svd(int64_t rows, int64_t cols, const double* M, double* s, do
     return converged ? sweeps : -1;
 }
 
+/*
+ * Pivoted LU of a tall m x l matrix (m >= l), [L, U] = lu(Y) in the sense of
+ * Algorithm norm_iterations (Sec. 2.2.2): Gaussian elimination with partial
+ * (row) pivoting, the pivot of column j being the first row, in the current
+ * order, of largest magnitude at or below j.  Y = L U with L (m x l) a row
+ * permutation of a unit lower trapezoidal matrix, returned in Y's own row
+ * order, and U (l x l) upper triangular.  perm[j] (optional) is the row of Y
+ * chosen as pivot j.  A zero pivot (a column already in the span of the
+ * earlier ones) leaves that column of L zero below its pivot row and U's
+ * diagonal entry zero.  U and perm may be NULL.  Returns 0 (2: no memory).
+ */
+int oracle_lu_pivot(int64_t m, int64_t l, const double* Y, double* L, double* U, int64_t* perm)
+{
+    if (m < l || l < 1) return 1;
+    double* W = (double*)malloc((size_t)(m * l) * sizeof(double));
+    int64_t* row = (int64_t*)malloc((size_t)m * sizeof(int64_t));
+    if (!W || !row) { free(W); free(row); return 2; }
+    memcpy(W, Y, (size_t)(m * l) * sizeof(double));
+    for (int64_t i = 0; i < m; ++i) row[i] = i;
+    for (int64_t j = 0; j < l; ++j) {
+        int64_t p = j;
+        double best = fabs(W[j * l + j]);
+        for (int64_t i = j + 1; i < m; ++i)
+            if (fabs(W[i * l + j]) > best) { best = fabs(W[i * l + j]); p = i; }
+        if (p != j) {
+            for (int64_t c = 0; c < l; ++c) {
+                const double t = W[j * l + c];
+                W[j * l + c] = W[p * l + c];
+                W[p * l + c] = t;
+            }
+            const int64_t t = row[j];
+            row[j] = row[p];
+            row[p] = t;
+        }
+        const double piv = W[j * l + j];
+        if (piv == 0.0) continue;
+        for (int64_t i = j + 1; i < m; ++i) {
+            const double f = W[i * l + j] / piv;
+            W[i * l + j] = f;
+            for (int64_t c = j + 1; c < l; ++c) W[i * l + c] -= f * W[j * l + c];
+        }
+    }
+    /* L in Y's row order: row row[i] of L is row i of the unit lower trapezoid */
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t c = 0; c < l; ++c) {
+            double v;
+            if (i < l)
+                v = (c == i) ? 1.0 : (c < i ? W[i * l + c] : 0.0);
+            else
+                v = W[i * l + c];
+            L[row[i] * l + c] = v;
+        }
+    if (U)
+        for (int64_t r = 0; r < l; ++r)
+            for (int64_t c = 0; c < l; ++c) U[r * l + c] = (c >= r) ? W[r * l + c] : 0.0;
+    if (perm)
+        for (int64_t j = 0; j < l; ++j) perm[j] = row[j];
+    free(W);
+    free(row);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Randomized QB decomposition, Algorithm rqb with Algorithm sub_iterations */
-/* (Secs. 2.1-2.2, 3.3).  The logical A is rows x cols with rows >= cols;   */
-/* l <= cols.  Outputs Q (rows x l) and B (l x cols), both row-major.       */
+/* (scheme 0) or Algorithm norm_iterations (scheme 1) (Secs. 2.1-2.2, 3.3). */
+/* The logical A is rows x cols with rows >= cols; l <= cols.  Outputs Q    */
+/* (rows x l) and B (l x cols), both row-major.                             */
 /* ------------------------------------------------------------------------ */
-static int rqb_logical(const amat* A, int64_t l, int q, int sdist, uint64_t seed, double* Q, double* B)
+static int rqb_logical(const amat* A, int64_t l, int q, int sdist, uint64_t seed, double* Q, double* B,
+                       int scheme)
 {
     const int64_t m = A->rows, n = A->cols;
     int rc = 0;
@@ -391,8 +455,16 @@ static int rqb_logical(const amat* A, int64_t l, int q, int sdist, uint64_t seed
     for (int64_t e = 0; e < n * l; ++e) X[e] = (double)omega_f[e];
     /* step 3: Y = A Omega (Eq. YAQ) */
     gemm_AX(A, X, l, Y);
-    /* step 4: Y = sub_iterations(A, Y, q) */
-    for (int j = 0; j < q; ++j) {
+    /* step 4: Y = norm_iterations(A, Y, q) (scheme 1): pivoted LU in place of
+     * the QR steps; the L factors span the same subspaces */
+    for (int j = 0; j < q && scheme == 1; ++j) {
+        if ((rc = oracle_lu_pivot(m, l, Y, Q, NULL, NULL))) goto done; /* [L, ~] = lu(Y)     */
+        gemm_AtX(A, Q, l, Z);                                          /* A^T L              */
+        if ((rc = oracle_lu_pivot(n, l, Z, X, NULL, NULL))) goto done; /* [L, ~] = lu(A^T L) */
+        gemm_AX(A, X, l, Y);                                           /* Y = A L            */
+    }
+    /* step 4: Y = sub_iterations(A, Y, q) (scheme 0) */
+    for (int j = 0; j < q && scheme == 0; ++j) {
         if ((rc = oracle_householder_qr(m, l, Y, Q, NULL))) goto done; /* Q = qr(Y)     */
         gemm_AtX(A, Q, l, Z);                                          /* A^T Q         */
         if ((rc = oracle_householder_qr(n, l, Z, X, NULL))) goto done; /* Q = qr(A^T Q) */
@@ -439,15 +511,21 @@ int64_t oracle_sketch_width(int64_t m, int64_t n, int k, int p)
  * B (l x n).  For m < n it factors A^T and writes Q (n x l) and B (l x m)
  * of that transposed problem (so A^T ~ Q B).  Returns 0 on success.
  */
-int oracle_rqb(const void* Adata, int dtype, int64_t m, int64_t n, int64_t lda, int k, int p, int q, int sdist,
-               uint64_t seed, double* Q, double* B)
+int oracle_rqb_ex(const void* Adata, int dtype, int64_t m, int64_t n, int64_t lda, int k, int p, int q, int sdist,
+                  uint64_t seed, int scheme, double* Q, double* B)
 {
     amat A;
     int tr = 0;
     if (setup_logical(&A, Adata, dtype, m, n, lda, &tr)) return 1;
-    if (k < 1 || k >= (m < n ? m : n) || p < 0 || q < 0) return 1;
+    if (k < 1 || k >= (m < n ? m : n) || p < 0 || q < 0 || scheme < 0 || scheme > 1) return 1;
     const int64_t l = oracle_sketch_width(m, n, k, p);
-    return rqb_logical(&A, l, q, sdist, seed, Q, B);
+    return rqb_logical(&A, l, q, sdist, seed, Q, B, scheme);
+}
+
+int oracle_rqb(const void* Adata, int dtype, int64_t m, int64_t n, int64_t lda, int k, int p, int q, int sdist,
+               uint64_t seed, double* Q, double* B)
+{
+    return oracle_rqb_ex(Adata, dtype, m, n, lda, k, p, q, sdist, seed, 0, Q, B);
 }
 
 /*
@@ -460,13 +538,13 @@ int oracle_rqb(const void* Adata, int dtype, int64_t m, int64_t n, int64_t lda, 
  * If Qout / Bout are non-NULL they receive Q and B of the (possibly
  * transposed) problem.  Returns 0 on success, < 0 if Jacobi did not converge.
  */
-int oracle_rsvd(const void* Adata, int dtype, int64_t m, int64_t n, int64_t lda, int k, int p, int q, int sdist,
-                uint64_t seed, double* d, double* U, double* V, double* Qout, double* Bout)
+int oracle_rsvd_ex(const void* Adata, int dtype, int64_t m, int64_t n, int64_t lda, int k, int p, int q, int sdist,
+                   uint64_t seed, int scheme, double* d, double* U, double* V, double* Qout, double* Bout)
 {
     amat A;
     int tr = 0;
     if (setup_logical(&A, Adata, dtype, m, n, lda, &tr)) return 1;
-    if (k < 1 || k >= (m < n ? m : n) || p < 0 || q < 0) return 1;
+    if (k < 1 || k >= (m < n ? m : n) || p < 0 || q < 0 || scheme < 0 || scheme > 1) return 1;
     const int64_t rows = A.rows, cols = A.cols;
     const int64_t l = oracle_sketch_width(m, n, k, p);
     int rc = 0;
@@ -478,7 +556,7 @@ int oracle_rsvd(const void* Adata, int dtype, int64_t m, int64_t n, int64_t lda,
     double* Ut = (double*)malloc((size_t)(l * l) * sizeof(double));
     if (!Q || !B || !Bt || !s || !Vl || !Ut) { rc = 2; goto done; }
 
-    if ((rc = rqb_logical(&A, l, q, sdist, seed, Q, B))) goto done;
+    if ((rc = rqb_logical(&A, l, q, sdist, seed, Q, B, scheme))) goto done;
     for (int64_t r = 0; r < l; ++r)
         for (int64_t c = 0; c < cols; ++c) Bt[c * l + r] = B[r * cols + c];
     if (oracle_jacobi_svd(cols, l, Bt, s, Vl, Ut) < 0) rc = -1;
@@ -501,6 +579,12 @@ int oracle_rsvd(const void* Adata, int dtype, int64_t m, int64_t n, int64_t lda,
 done:
     free(Q); free(B); free(Bt); free(s); free(Vl); free(Ut);
     return rc;
+}
+
+int oracle_rsvd(const void* Adata, int dtype, int64_t m, int64_t n, int64_t lda, int k, int p, int q, int sdist,
+                uint64_t seed, double* d, double* U, double* V, double* Qout, double* Bout)
+{
+    return oracle_rsvd_ex(Adata, dtype, m, n, lda, k, p, q, sdist, seed, 0, d, U, V, Qout, Bout);
 }
 
 /*

@@ -28,6 +28,7 @@ RSVD = ["test_oracle_philox_library.py", "test_oracle_pins.py"]
 RID = ["test_oracle_rid.py"]
 RPCA = ["test_oracle_rpca.py"]
 RRPCA = ["test_oracle_rrpca.py"]
+LU = ["test_oracle_lu.py"]
 CTL = ["test_oracle_controller.py"]
 
 # (name, file, [(original text, planted text)], pin files)
@@ -72,8 +73,8 @@ MUTANTS = [
     ("jacobi_rotations_transposed", C, [("J[i * cols + c] = V[src * cols + i];", "J[i * cols + c] = V[i * cols + src];")],
      RSVD),
     # Algorithms rqb / sub_iterations / rSVD
-    ("rqb_one_power_iteration_short", C, [("for (int j = 0; j < q; ++j) {\n        if ((rc = oracle_householder_qr",
-                                           "for (int j = 0; j < q - 1; ++j) {\n        if ((rc = oracle_householder_qr")],
+    ("rqb_one_power_iteration_short", C, [("for (int j = 0; j < q && scheme == 0; ++j) {\n        if ((rc = oracle_householder_qr",
+                                           "for (int j = 0; j < q - 1 && scheme == 0; ++j) {\n        if ((rc = oracle_householder_qr")],
      RSVD),
     ("rqb_b_wrong_index", C, [("B[r * n + c] = Z[c * l + r];", "B[r * n + c] = Z[r * n + c];")], RSVD),
     ("rqb_test_matrix_perturbed", C, [("for (int64_t e = 0; e < n * l; ++e) X[e] = (double)omega_f[e];\n    /* step 3",
@@ -110,6 +111,12 @@ MUTANTS = [
     ("rpca_eigenvalues_over_m", PY, [("lam = d * d / (m - 1)", "lam = d * d / m")], RPCA),
     ("rpca_scale_over_m", PY, [("np.sum(Xc * Xc, axis=0) / (m - 1)", "np.sum(Xc * Xc, axis=0) / m")], RPCA),
     ("rpca_scores_without_sigma", PY, [('"x": U * d[None, :]', '"x": U')], RPCA),
+    # pivoted LU and normalized power iterations (Algorithm norm_iterations)
+    ("lu_pivot_without_magnitude", C, [("if (fabs(W[i * l + j]) > best) { best = fabs(W[i * l + j]); p = i; }",
+                                        "if (W[i * l + j] > best) { best = W[i * l + j]; p = i; }")], LU),
+    ("lu_rows_not_tracked", C, [("            row[j] = row[p];\n            row[p] = t;", "            (void)t;")], LU),
+    ("lu_multiplier_not_stored", C, [("            W[i * l + j] = f;\n", "")], LU),
+    ("lu_ties_to_the_last_row", C, [("if (fabs(W[i * l + j]) > best) {", "if (fabs(W[i * l + j]) >= best) {")], LU),
     # robust PCA (Algorithm rrpca)
     ("rrpca_no_singular_value_shrinkage", PY, [("ds = np.maximum(d[:svp] - 1.0 / mu, 0.0)", "ds = d[:svp]")], RRPCA),
     ("rrpca_threshold_times_mu", PY, [("soft_threshold(M - L + Z / mu, lam / mu)", "soft_threshold(M - L + Z / mu, lam * mu)")],
