@@ -554,9 +554,11 @@ def main():
 
     # ---------------- the other test matrices of Sec. 2.3 on the same A ----------------
     if args.variants:
-        for sd in ("unif", "rademacher"):
+        for sd, power in (("unif", "subspace"), ("rademacher", "subspace"), ("normal", "lu")):
+            name = f"{args.prec}_omega_{sd}" if power == "subspace" else f"{args.prec}_power_{power}"
             try:
-                o4 = rs.make_opts(p=wl["p"], q=wl["q"], seed=rank, prec=args.prec, engine=args.engine, sdist=sd)
+                o4 = rs.make_opts(p=wl["p"], q=wl["q"], seed=rank, prec=args.prec, engine=args.engine, sdist=sd,
+                                  power=power)
                 for _ in range(2):
                     rs.rsvdgb_rsvd(h, A, k, opts=o4, out=bufs, sync_info=False)
                 torch.cuda.synchronize()
@@ -571,11 +573,11 @@ def main():
                 info4 = rs._info_from(bufs[3])
                 err_main = float(np.sqrt(max(info.err2_k, 0.0)))
                 err4 = float(np.sqrt(max(info4.err2_k, 0.0)))
-                variants[f"{args.prec}_omega_{sd}"] = {
+                variants[name] = {
                     "ms": e0.elapsed_time(e1) / nv, "err_k_fro": err4,
                     "err_ratio_vs_" + args.prec: err4 / err_main if err_main > 0 else None}
             except Exception as exc:
-                variants[f"{args.prec}_omega_{sd}"] = {"unavailable": str(exc)}
+                variants[name] = {"unavailable": str(exc)}
 
     # ---------------- learned (q, p) on the same A: the packaged controller ----------------
     ctl_path = os.path.join(ROOT, "paper_1608_02148_gb300", "controller_default.bin")

@@ -84,6 +84,16 @@ enum { RSVDGB_ENGINE_AUTO = 0, RSVDGB_ENGINE_SIMT = 1, RSVDGB_ENGINE_TC = 2, RSV
  * to read the decision. */
 enum { RSVDGB_Q_FIXED = 0, RSVDGB_Q_LEARNED = 1 };
 
+/* Renormalisation between the passes of the power iterations (Sec. 2.2.2).
+ * SUBSPACE: Algorithm sub_iterations, an orthonormal basis (CholeskyQR here)
+ * of each sketch.  LU: Algorithm norm_iterations, the L factor of a pivoted
+ * LU (here a tall-skinny LU with tournament pivoting: l pivot rows chosen by
+ * a reduction tree of small partial-pivoting LUs, then L = Y U^{-1} with U
+ * from the LU of those rows).  Both keep the span, so they give the same
+ * result in exact arithmetic; the final basis of the QB step is always
+ * orthonormal.  LU runs on the tensor-core engine with l <= 112. */
+enum { RSVDGB_POWER_SUBSPACE = 0, RSVDGB_POWER_LU = 1 };
+
 typedef struct rsvdgb_opts {
     int32_t p;       /* oversampling, l = k + p (Sec. 2.2.1); default 10         */
     int32_t q;       /* subspace iterations (Sec. 2.2.2); default 2              */
@@ -95,8 +105,11 @@ typedef struct rsvdgb_opts {
     int32_t q_mode;  /* RSVDGB_Q_FIXED / RSVDGB_Q_LEARNED; default FIXED          */
     int32_t p_max;   /* learned mode: largest oversampling (>= 2); default 24     */
     int32_t q_max;   /* learned mode: largest q; default 6                        */
-    int32_t reserved[3]; /* zero; reserved[0] = 1 runs rsvdgb_rsvd_batched
-                            eagerly instead of replaying its CUDA graph       */
+    int32_t batched_eager; /* 1: rsvdgb_rsvd_batched runs its stages eagerly
+                              instead of replaying its CUDA graph; default 0  */
+    int32_t power;   /* RSVDGB_POWER_*: how the power iterations renormalise;
+                        default SUBSPACE                                       */
+    int32_t reserved; /* zero                                                  */
 } rsvdgb_opts;
 
 /* Diagnostics written by the device at the end of a call (device memory). */

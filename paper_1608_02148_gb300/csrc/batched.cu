@@ -973,7 +973,7 @@ int batched_rsvd(BatchedPlan** cache, int device, int sm_count, cudaStream_t str
         pl->tuned = true;
         RSVDGB_CUDA_TRY(cudaGetLastError());
     }
-    if (o.reserved[0] == 1) {
+    if (o.batched_eager == 1) {
         // eager mode (no graph): every stage launched on the caller's stream
         enqueue(pl, stream, sm_count, infos);
         count_launches(pl->kernels_per_run);

@@ -173,6 +173,16 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
 bool xt_supported(int l_pad);
 int launch_xt(cudaStream_t s, int sm_count, const float* X, int64_t ld, int64_t rows, int l, int l_pad, const float* T,
               float* Z, int split, void* Zh, void* Zl, float sc);
+// Pivoted LU of a tall column-major rows x l matrix X (ld) for the normalized
+// power iterations (tslu.cu): tournament pivoting picks l pivot rows; U (l x
+// l row-major, upper triangular) is the LU factor of those rows and T = U^{-1}
+// (l x l row-major), so that L = X T.  scratch: tslu_scratch_ints(rows, l)
+// ints.  A zero pivot in U sets *status = RSVDGB_ERR_BREAKDOWN.  l <= 112,
+// rows >= l.
+bool tslu_supported(int l);
+int64_t tslu_scratch_ints(int64_t rows, int l);
+int launch_tslu(cudaStream_t s, const float* X, int64_t ld, int64_t rows, int l, int* scratch, float* U, float* T,
+                int* status);
 // Scaled FP16 hi / lo split of a column-major rows x l panel (ld even) over
 // l_pad columns for the FP16x3 passes: column j is multiplied by the power of
 // two bringing its max magnitude into [2^13, 2^14), pinv[j] receives the

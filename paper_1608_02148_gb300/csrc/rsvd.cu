@@ -119,6 +119,7 @@ struct Geom {
     int L;         // l rounded up to 16 (tensor-core N granularity)
     bool use_tc;   // passes over A on the tensor cores
     bool h16 = false;  // FP32-accurate passes after the first as scaled FP16x3 (tensor cores)
+    bool lu = false;   // power iterations renormalised by pivoted LU (Algorithm norm_iterations)
     bool bf16;     // sketch and power passes in BF16 (mixed precision)
     int64_t ldm, ldn;
     const Affine* aff = nullptr;  // randomized PCA: products with X instead of A
@@ -157,6 +158,7 @@ struct Work {
     // vectors up to rounding)
     unsigned int* amax;
     float *Ppinv, *Qpinv;
+    int* luscr;  // pivot-row proposals of the tall-skinny LU (normalized power iterations)
 };
 
 constexpr int kPqrSlots = 1024;  // per-CTA maxima of the pivoted QR (its grid is at most this wide)
@@ -240,6 +242,7 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w, int L_lo = 0)
     // Jacobi columns when they do not fit in shared memory: 2 x l x Lp with the
     // padded column stride Lp <= l rounded up to 32
     w.jwork = c.take<float>(2 * (L + 32) * (L + 32));
+    w.luscr = g.lu ? c.take<int>(tslu_scratch_ints(std::max(g.ldm, g.ldn), g.L)) : nullptr;
     w.amax = c.take<unsigned int>(1);
     w.Ppinv = c.take<float>(L);
     w.Qpinv = c.take<float>(L);
@@ -812,8 +815,22 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
     // split of an m-side basis for the A^T-side pass that reads it: none in
     // mixed precision (BF16 copy), FP16 with the FP16x3 passes, else TF32
     const bool q_split = g.use_tc && !g.bf16;
-    // step 4: subspace iterations
-    for (int it = 0; it < q; ++it) {
+    // step 4, Algorithm norm_iterations: each sketch is renormalised by the L
+    // factor of a pivoted LU, L = Y U^{-1} (U from the tall-skinny LU's pivot
+    // rows); only the final basis (step 9) is orthonormal
+    for (int it = 0; it < q && g.lu; ++it) {
+        launch_tslu(s, w.Yt, g.ldm, g.m, l, w.luscr, w.R1, w.T, w.status);
+        tc_times_small(h, g, w, w.Yt, g.ldm, g.m, w.T, w.Qt, q_split ? w.Qth : nullptr, q_split ? w.Qtl : nullptr,
+                       g.h16);
+        apply_At(h, g, w, false, w.Qt, w.Qth, w.Qtl, w.Yt, w.Yth, w.Ytl);
+        launch_tslu(s, w.Wt, g.ldn, g.n, l, w.luscr, w.R2, w.T1, w.status);
+        times_small(s, sm, w.Wt, g.ldn, g.n, l, w.T1, w.Pt, w.part);
+        split_panel(s, g, w, false);
+        apply_A(h, g, w, nullptr, false);
+        if (it == q - 1) tc_gram(h, g, w, w.Yt, w.Yth, w.Ytl, g.ldm, g.m);
+    }
+    // step 4, Algorithm sub_iterations
+    for (int it = 0; it < q && !g.lu; ++it) {
         // Q = qr(Y) by one Cholesky step, Q = Y R^{-1}: only the span is carried
         // forward.  Q is formed before A^T Q so that the directions of small
         // singular values keep their relative accuracy (A^T Y T would carry
@@ -964,6 +981,18 @@ int make_geom(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int l
     return RSVDGB_OK;
 }
 
+// The power-iteration scheme of the options (RSVDGB_POWER_*): the LU form
+// runs on the tensor-core engine with l <= 112.
+int apply_power(Geom& g, int power)
+{
+    if (power != RSVDGB_POWER_SUBSPACE && power != RSVDGB_POWER_LU) return RSVDGB_ERR_INVALID_ARG;
+    if (power == RSVDGB_POWER_LU) {
+        if (!g.use_tc || !tslu_supported(g.l) || !xt_supported(g.L)) return RSVDGB_ERR_UNSUPPORTED;
+        g.lu = true;
+    }
+    return RSVDGB_OK;
+}
+
 const char* kStatusNames[] = {"RSVDGB_OK",           "RSVDGB_ERR_INVALID_ARG", "RSVDGB_ERR_NOMEM",
                               "RSVDGB_ERR_CUDA",     "RSVDGB_ERR_BREAKDOWN",   "RSVDGB_ERR_NONFINITE",
                               "RSVDGB_ERR_TIMEOUT",  "RSVDGB_ERR_UNSUPPORTED"};
@@ -1077,6 +1106,8 @@ int rsvdgb_rsvd(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t l
     Geom g{};
     rc = make_geom(A, m, n, lda, dtype, o.layout, k, learned ? o.p_max : o.p, o.engine, o.prec, g);
     if (rc) return rc;
+    rc = apply_power(g, o.power);
+    if (rc) return rc;
     if (nu < 0) nu = k;
     if (nv < 0) nv = k;
     if (nu > k || nv > k || !d) return RSVDGB_ERR_INVALID_ARG;
@@ -1113,6 +1144,8 @@ int rsvdgb_rqb(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t ld
     if (m < n || o.layout != RSVDGB_ROW_MAJOR) return RSVDGB_ERR_INVALID_ARG;
     Geom g{};
     rc = make_geom(A, m, n, lda, dtype, o.layout, k, o.p, o.engine, o.prec, g);
+    if (rc) return rc;
+    rc = apply_power(g, o.power);
     if (rc) return rc;
     if (!Q || !B || ldq < g.l || ldb < n) return RSVDGB_ERR_INVALID_ARG;
     Outputs out{};

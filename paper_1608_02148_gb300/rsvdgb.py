@@ -47,7 +47,7 @@ class RsvdgbOpts(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("q", ctypes.c_int32), ("sdist", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("layout", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("q_mode", ctypes.c_int32), ("p_max", ctypes.c_int32), ("q_max", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("batched_eager", ctypes.c_int32), ("power", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class RsvdgbRrpcaOpts(ctypes.Structure):
@@ -180,11 +180,15 @@ def _rowmajor_ld(t):
     return t.stride(0)
 
 
+POWER = {"subspace": 0, "lu": 1}
+
+
 def make_opts(p=10, q=2, sdist="normal", prec="fp32", seed=0, layout="row", engine="auto", q_mode="fixed",
-              p_max=None, q_max=None) -> RsvdgbOpts:
+              p_max=None, q_max=None, power="subspace") -> RsvdgbOpts:
     o = RsvdgbOpts()
     load().rsvdgb_default_opts(ctypes.byref(o))
     o.p, o.q, o.sdist, o.prec = p, q, SDIST[sdist], PREC[prec]
+    o.power = POWER[power]
     o.seed, o.layout, o.engine = seed, LAYOUT[layout], ENGINE[engine]
     o.q_mode = Q_MODE[q_mode]
     if p_max is not None:
