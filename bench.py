@@ -525,32 +525,32 @@ def main():
 
     # ---------------- the other precision at equal error (same A, same Omega) ----------------
     variants = {}
-    other = "bf16_sketch" if args.prec == "fp32" else "fp32"
-    try:
-        if not args.variants:
-            raise RuntimeError("skipped (--variants 0)")
-        o2 = rs.make_opts(p=wl["p"], q=wl["q"], seed=rank, prec=other, engine=args.engine)
-        for _ in range(2):
-            rs.rsvdgb_rsvd(h, A, k, opts=o2, out=bufs, sync_info=False)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        nv = max(3, args.steps // 2)
-        for _ in range(nv):
-            rs.rsvdgb_rsvd(h, A, k, opts=o2, out=bufs, sync_info=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        info2 = rs._info_from(bufs[3])
-        err_main = float(np.sqrt(max(info.err2_k, 0.0)))
-        err_other = float(np.sqrt(max(info2.err2_k, 0.0)))
-        variants = {
-            args.prec: {"ms": ms_per_step, "err_k_fro": err_main},
-            other: {"ms": e0.elapsed_time(e1) / nv, "err_k_fro": err_other,
-                    "err_ratio_vs_" + args.prec: err_other / err_main if err_main > 0 else None},
-        }
-    except Exception as exc:  # a variant the build does not serve
-        variants = {other: {"unavailable": str(exc)}}
+    others = [x for x in ("fp32", "bf16_sketch", "fp8_sketch") if x != args.prec]
+    err_main = float(np.sqrt(max(info.err2_k, 0.0)))
+    variants = {args.prec: {"ms": ms_per_step, "err_k_fro": err_main}}
+    for other in others:
+        try:
+            if not args.variants:
+                raise RuntimeError("skipped (--variants 0)")
+            o2 = rs.make_opts(p=wl["p"], q=wl["q"], seed=rank, prec=other, engine=args.engine)
+            for _ in range(2):
+                rs.rsvdgb_rsvd(h, A, k, opts=o2, out=bufs, sync_info=False)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            nv = max(3, args.steps // 2)
+            for _ in range(nv):
+                rs.rsvdgb_rsvd(h, A, k, opts=o2, out=bufs, sync_info=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            info2 = rs._info_from(bufs[3])
+            err_other = float(np.sqrt(max(info2.err2_k, 0.0)))
+            variants[other] = {"ms": e0.elapsed_time(e1) / nv, "err_k_fro": err_other,
+                               "err_ratio_vs_" + args.prec: err_other / err_main if err_main > 0 else None,
+                               "status": info2.status}
+        except Exception as exc:  # a variant the build does not serve
+            variants[other] = {"unavailable": str(exc)}
 
     # ---------------- the other test matrices of Sec. 2.3 on the same A ----------------
     if args.variants:

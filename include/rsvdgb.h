@@ -55,12 +55,17 @@ enum { RSVDGB_F32 = 0, RSVDGB_BF16 = 1 };
 enum { RSVDGB_SDIST_NORMAL = 0, RSVDGB_SDIST_UNIF = 1, RSVDGB_SDIST_RADEMACHER = 2 };
 
 /* Arithmetic of the passes over A.
- *  FP32        : every pass FP32-accurate (3xTF32 products on the tensor cores
- *                or FP32 FMA), FP32 accumulation.
+ *  FP32        : every pass FP32-accurate (scaled FP16x3 or 3xTF32 products on
+ *                the tensor cores, or FP32 FMA), FP32 accumulation.
  *  BF16_SKETCH : sketch and power passes with A and the panel rounded to BF16,
  *                FP32 accumulation; the final projection B = Q^T A stays
- *                FP32-accurate. */
-enum { RSVDGB_PREC_FP32 = 0, RSVDGB_PREC_BF16_SKETCH = 1 };
+ *                FP32-accurate.
+ *  FP8_SKETCH  : one pass first writes an E4M3 copy of A (and its transpose)
+ *                with a power-of-two scale per row; the sketch and power
+ *                passes read those copies (panels quantised per column),
+ *                FP32 accumulation; the projection stays FP32-accurate on A.
+ *                Tensor-core engine only; the workspace holds 2 m n bytes more. */
+enum { RSVDGB_PREC_FP32 = 0, RSVDGB_PREC_BF16_SKETCH = 1, RSVDGB_PREC_FP8_SKETCH = 2 };
 
 /* Storage order of A as passed by the caller. COL_MAJOR is served as the
  * row-major transpose (U and V swap roles internally). */

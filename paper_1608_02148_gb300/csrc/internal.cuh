@@ -183,6 +183,27 @@ bool tslu_supported(int l);
 int64_t tslu_scratch_ints(int64_t rows, int l);
 int launch_tslu(cudaStream_t s, const float* X, int64_t ld, int64_t rows, int l, int* scratch, float* U, float* T,
                 int* status);
+// FP8 (E4M3) power passes (fp8.cu, fp8_pass.cu).  launch_fp8_prep: A (m x n
+// row-major, lda; FP32 or BF16) -> A8 (row-major bytes, ld8 >= n, multiple of
+// 16), At8 (its transpose, column-major: At8[c * ldt + i], ldt >= m, multiple
+// of 16) and the row powers of two rs (m floats); adds ||A||_F^2 to *fro2 and
+// max|A| (bits) to *amax when non-null.  launch_fp8_panel: column-major K x l
+// panel P (ld), optionally row-scaled by r, -> P8 (column-major bytes, ld8
+// >= K, multiple of 16, l_pad columns) and column powers of two ts.
+// launch_f8_pass: out (lanes x l_pad column-major, ld_out) = A8_lanes P8 with
+// the lane-major copy A8 (A8 for the A side, At8 for the A^T side: lanes x
+// k_total, ld_a8 bytes), rows scaled by row_scale (optional) and columns by
+// col_scale; with K splits the partials go to `partial` and *splits_out is
+// their count (0: written to out).
+void launch_fp8_prep(cudaStream_t s, const void* A, int64_t lda, int a_bf16, int64_t m, int64_t n, uint8_t* A8,
+                     int64_t ld8, uint8_t* At8, int64_t ldt, float* rs, double* fro2, unsigned int* amax);
+void launch_fp8_panel(cudaStream_t s, const float* P, int64_t ld, int64_t K, int l, int l_pad, const float* r,
+                      uint8_t* P8, int64_t ld8, float* ts);
+int launch_f8_pass(cudaStream_t s, int sm_count, bool trans, const uint8_t* A8, int64_t lanes, int64_t k_total,
+                   int64_t ld_a8, const uint8_t* P8, int64_t ld_p8, int l_pad, const float* row_scale,
+                   const float* col_scale, float* out, int64_t ld_out, float* partial, int64_t* splits_out,
+                   int* status);
+int64_t f8_pass_max_splits(int64_t lanes, int64_t k_total, int l_pad, int sm_count);
 // Scaled FP16 hi / lo split of a column-major rows x l panel (ld even) over
 // l_pad columns for the FP16x3 passes: column j is multiplied by the power of
 // two bringing its max magnitude into [2^13, 2^14), pinv[j] receives the

@@ -120,6 +120,7 @@ struct Geom {
     bool use_tc;   // passes over A on the tensor cores
     bool h16 = false;  // FP32-accurate passes after the first as scaled FP16x3 (tensor cores)
     bool lu = false;   // power iterations renormalised by pivoted LU (Algorithm norm_iterations)
+    bool fp8 = false;  // sketch and power passes on E4M3 copies of A (mixed precision)
     bool bf16;     // sketch and power passes in BF16 (mixed precision)
     int64_t ldm, ldn;
     const Affine* aff = nullptr;  // randomized PCA: products with X instead of A
@@ -159,6 +160,11 @@ struct Work {
     unsigned int* amax;
     float *Ppinv, *Qpinv;
     int* luscr;  // pivot-row proposals of the tall-skinny LU (normalized power iterations)
+    // FP8 passes: E4M3 copies of the stored matrix (row-major A8, transposed
+    // At8), its row powers of two, the quantised panel and its column scales
+    uint8_t *A8, *At8, *P8;
+    int64_t ld8, ldt8, ldp8;
+    float *rs8, *ts8;
 };
 
 constexpr int kPqrSlots = 1024;  // per-CTA maxima of the pivoted QR (its grid is at most this wide)
@@ -190,6 +196,10 @@ size_t partial_floats(const Geom& g, int sm_count)
         need = std::max<int64_t>(need, s_tc * L * std::max(g.ldm, g.ldn));
         // tensor-core Gram: at most one split per SM, L x L each
         need = std::max<int64_t>(need, (int64_t)sm_count * L * L);
+        // FP8 passes: splits over the stored rows (lanes = stored columns) or columns
+        const int64_t s8 = std::max(f8_pass_max_splits(g.sn(), g.sm(), g.L, sm_count),
+                                    f8_pass_max_splits(g.sm(), g.sn(), g.L, sm_count));
+        need = std::max<int64_t>(need, s8 * L * std::max(g.ldm, g.ldn));
     }
     return (size_t)need;
 }
@@ -243,6 +253,18 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w, int L_lo = 0)
     // padded column stride Lp <= l rounded up to 32
     w.jwork = c.take<float>(2 * (L + 32) * (L + 32));
     w.luscr = g.lu ? c.take<int>(tslu_scratch_ints(std::max(g.ldm, g.ldn), g.L)) : nullptr;
+    w.A8 = w.At8 = w.P8 = nullptr;
+    w.rs8 = w.ts8 = nullptr;
+    w.ld8 = round_up(g.sn(), 16);
+    w.ldt8 = round_up(g.sm(), 16);
+    w.ldp8 = round_up(std::max(g.m, g.n), 16);
+    if (g.fp8) {
+        w.A8 = c.take<uint8_t>((size_t)g.sm() * w.ld8);
+        w.At8 = c.take<uint8_t>((size_t)g.sn() * w.ldt8);
+        w.P8 = c.take<uint8_t>((size_t)g.L * w.ldp8);
+        w.rs8 = c.take<float>(g.sm());
+        w.ts8 = c.take<float>(g.L);
+    }
     w.amax = c.take<unsigned int>(1);
     w.Ppinv = c.take<float>(L);
     w.Qpinv = c.take<float>(L);
@@ -461,6 +483,28 @@ void tc_times_small(rsvdgb_handle* h, const Geom& g, Work& w, const float* Xt, i
                    nullptr, f16 ? &x : nullptr);
 }
 
+// One FP8 pass: out (rows x l, column-major) = A_logical P (A_side) or
+// A_logical^T P, P the FP32 panel (K x l, column-major).  The lanes of the
+// FP8 kernel are the stored rows (A8, whose row powers of two scale the
+// output) or the stored columns (At8; K then runs over the stored rows, whose
+// powers of two scale the panel before it is quantised).
+void pass_fp8(rsvdgb_handle* h, const Geom& g, Work& w, bool A_side, const float* P, float* out)
+{
+    const cudaStream_t s = h->stream;
+    const bool stored_atx = (A_side == g.trans);
+    const int64_t K = A_side ? g.n : g.m;
+    const int64_t rows = A_side ? g.m : g.n;
+    const int64_t ldP = A_side ? g.ldn : g.ldm;
+    const int64_t ldO = A_side ? g.ldm : g.ldn;
+    launch_fp8_panel(s, P, ldP, K, g.l, g.L, stored_atx ? w.rs8 : nullptr, w.P8, w.ldp8, w.ts8);
+    int64_t splits = 0;
+    prof_mark(h, true, 0);
+    launch_f8_pass(s, h->sm_count, stored_atx, stored_atx ? w.At8 : w.A8, rows, K, stored_atx ? w.ldt8 : w.ld8,
+                   w.P8, w.ldp8, g.L, stored_atx ? nullptr : w.rs8, w.ts8, out, ldO, w.part, &splits, w.status);
+    prof_mark(h, false, (double)g.m * (double)g.n);
+    if (splits > 0) launch_reduce_splits(s, w.part, (int)splits, (int64_t)g.L * ldO, g.l, rows, ldO, out, ldO);
+}
+
 // Y = A_logical X with X = Pt (n x l) -> Yt (m x l).  The first pass
 // (first = true) measures ||A||_F^2 (fro2) and, for the FP16x3 form, max|A|;
 // later passes use the FP16x3 form where the geometry has it (the panel's
@@ -473,6 +517,12 @@ void tc_times_small(rsvdgb_handle* h, const Geom& g, Work& w, const float* Xt, i
 // h = P^T mu (columns: u = 1, r = 1) or h = P^T 1 (rows: u = mu, r = c).
 void apply_A(rsvdgb_handle* h, const Geom& g, Work& w, double* fro2, bool first)
 {
+    if (g.fp8) {
+        // the statistics of A came from the FP8 copy's pass (launch_fp8_prep)
+        pass_fp8(h, g, w, true, w.Pt, w.Yt);
+        if (!tc_gram_direct(g, w.Yt, g.ldm)) launch_split_tf32(h->stream, w.Yt, g.ldm, g.m, g.l, g.L, w.Yth, w.Ytl);
+        return;
+    }
     const Affine* af = g.aff;
     const bool corr = af && (af->mu || (af->rows && af->c));
     int chunks = 0;
@@ -519,6 +569,10 @@ void apply_A(rsvdgb_handle* h, const Geom& g, Work& w, double* fro2, bool first)
 void apply_At(rsvdgb_handle* h, const Geom& g, Work& w, bool accurate, const float* X, const float* Xh,
               const float* Xl, float* S, float* Sh, float* Sl)
 {
+    if (g.fp8 && !accurate) {
+        pass_fp8(h, g, w, false, X, w.Wt);
+        return;
+    }
     const Affine* af = g.aff;
     const cudaStream_t s = h->stream;
     const bool mixed = g.bf16 && !accurate;
@@ -560,6 +614,7 @@ void apply_At(rsvdgb_handle* h, const Geom& g, Work& w, bool accurate, const flo
 // the multipliers (P <- diag(c) P).
 void split_panel(cudaStream_t s, const Geom& g, Work& w, bool first)
 {
+    if (g.fp8) return;  // quantised by the FP8 pass itself
     if (g.aff && !g.aff->rows && g.aff->c) {
         const bool tf = g.use_tc && !g.bf16;
         launch_scale_rows(s, w.Pt, g.ldn, g.n, g.l, g.L, g.aff->c, w.Pt, tf ? w.Pth : nullptr, tf ? w.Ptl : nullptr);
@@ -688,6 +743,9 @@ void sketch(rsvdgb_handle* h, const Geom& g, Work& w, int sdist, uint64_t seed)
     const cudaStream_t s = h->stream;
     launch_omega(s, g.n, g.ldn, g.l, g.L, seed, sdist, w.Pt, g.ldn);
     split_panel(s, g, w, true);
+    if (g.fp8)
+        launch_fp8_prep(s, g.A, g.lda, g.a_bf16, g.sm(), g.sn(), w.A8, w.ld8, w.At8, w.ldt8, w.rs8, w.fro2,
+                        w.amax);
     apply_A(h, g, w, w.fro2, true);
     if (g.use_tc)
         tc_gram(h, g, w, w.Yt, w.Yth, w.Ytl, g.ldm, g.m);
@@ -757,8 +815,9 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
 {
     const cudaStream_t s = h->stream;
     const int sm = h->sm_count;
-    // the randomized PCA's implicit centring runs on the 3xTF32 passes
+    // the randomized PCA's implicit centring runs on the 3xTF32 or BF16 passes
     if (pca) g.h16 = false;
+    if (pca && g.fp8) return RSVDGB_ERR_UNSUPPORTED;
     Carve probe(nullptr);
     Work w{};
     const int L_lo = lc ? (int)round_up(std::min<int64_t>((int64_t)k + 2, g.n), 16) : 0;
@@ -814,7 +873,7 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
     const int l = g.l;
     // split of an m-side basis for the A^T-side pass that reads it: none in
     // mixed precision (BF16 copy), FP16 with the FP16x3 passes, else TF32
-    const bool q_split = g.use_tc && !g.bf16;
+    const bool q_split = g.use_tc && !g.bf16 && !g.fp8;
     // step 4, Algorithm norm_iterations: each sketch is renormalised by the L
     // factor of a pivoted LU, L = Y U^{-1} (U from the tall-skinny LU's pivot
     // rows); only the final basis (step 9) is orthonormal
@@ -975,9 +1034,12 @@ int make_geom(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int l
     if ((engine == RSVDGB_ENGINE_TC || engine == RSVDGB_ENGINE_TC_TF32) && !tc_ok) return RSVDGB_ERR_UNSUPPORTED;
     g.use_tc = (engine != RSVDGB_ENGINE_SIMT) && tc_ok;
     g.h16 = g.use_tc && engine != RSVDGB_ENGINE_TC_TF32;
-    if (prec != RSVDGB_PREC_FP32 && prec != RSVDGB_PREC_BF16_SKETCH) return RSVDGB_ERR_INVALID_ARG;
+    if (prec != RSVDGB_PREC_FP32 && prec != RSVDGB_PREC_BF16_SKETCH && prec != RSVDGB_PREC_FP8_SKETCH)
+        return RSVDGB_ERR_INVALID_ARG;
     g.bf16 = (prec == RSVDGB_PREC_BF16_SKETCH);
-    if (g.bf16 && !g.use_tc) return RSVDGB_ERR_UNSUPPORTED;  // mixed precision runs on the tensor cores
+    g.fp8 = (prec == RSVDGB_PREC_FP8_SKETCH);
+    // mixed precision runs on the tensor cores
+    if ((g.bf16 || g.fp8) && !g.use_tc) return RSVDGB_ERR_UNSUPPORTED;
     return RSVDGB_OK;
 }
 
@@ -1553,8 +1615,10 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
     if (dtype != RSVDGB_F32 && dtype != RSVDGB_BF16) return RSVDGB_ERR_INVALID_ARG;
     if (ldx < l || ldy < l) return RSVDGB_ERR_INVALID_ARG;
     if (engine < RSVDGB_ENGINE_AUTO || engine > RSVDGB_ENGINE_TC_TF32) return RSVDGB_ERR_INVALID_ARG;
-    if (prec != RSVDGB_PREC_FP32 && prec != RSVDGB_PREC_BF16_SKETCH) return RSVDGB_ERR_INVALID_ARG;
-    const bool bf = prec == RSVDGB_PREC_BF16_SKETCH;
+    if (prec != RSVDGB_PREC_FP32 && prec != RSVDGB_PREC_BF16_SKETCH && prec != RSVDGB_PREC_FP8_SKETCH)
+        return RSVDGB_ERR_INVALID_ARG;
+    const bool f8 = prec == RSVDGB_PREC_FP8_SKETCH;
+    const bool bf = prec == RSVDGB_PREC_BF16_SKETCH || f8;
     const bool want_tc = engine == RSVDGB_ENGINE_TC || engine == RSVDGB_ENGINE_TC_TF32;
     const int64_t M = transpose ? n : m, K = transpose ? m : n;
     const int L = (int)round_up(l, 16);
@@ -1579,9 +1643,18 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
     probe.take<float>(L * ldK);
     probe.take<float>(L * ldK);
     probe.take<float>(L * ldM);
-    probe.take<float>(splits * L * ldM);
+    const int64_t ld8 = round_up(n, 16), ldt8 = round_up(m, 16), ldp8 = round_up(K, 16);
+    const int64_t splits8 = f8 ? f8_pass_max_splits(transpose ? n : m, K, L, h->sm_count) : 0;
+    probe.take<float>(std::max(splits, splits8) * L * ldM);
     probe.take<int>(4);
     probe.take<float>(L);
+    if (f8) {
+        probe.take<uint8_t>((size_t)m * ld8);
+        probe.take<uint8_t>((size_t)n * ldt8);
+        probe.take<uint8_t>((size_t)L * ldp8);
+        probe.take<float>(m);
+        probe.take<float>(L);
+    }
     rc = ensure_workspace(h, probe.off + 1024);
     if (rc) return rc;
     Carve c(h->ws);
@@ -1589,15 +1662,30 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
     float* Xh = c.take<float>(L * ldK);
     float* Xl = c.take<float>(L * ldK);
     float* Yc = c.take<float>(L * ldM);
-    float* part = c.take<float>(splits * L * ldM);
+    float* part = c.take<float>(std::max(splits, splits8) * L * ldM);
     int* status = c.take<int>(4);
     float* pinv = c.take<float>(L);
+    uint8_t *A8 = nullptr, *At8 = nullptr, *P8 = nullptr;
+    float *rs8 = nullptr, *ts8 = nullptr;
+    if (f8) {
+        A8 = c.take<uint8_t>((size_t)m * ld8);
+        At8 = c.take<uint8_t>((size_t)n * ldt8);
+        P8 = c.take<uint8_t>((size_t)L * ldp8);
+        rs8 = c.take<float>(m);
+        ts8 = c.take<float>(L);
+    }
     unsigned int* amax = (unsigned int*)(status + 1);
     const cudaStream_t s = h->stream;
     RSVDGB_CUDA_TRY(cudaMemsetAsync(status, 0, 2 * sizeof(int), s));
     launch_rowmajor_to_colmajor(s, X, ldx, K, l, L, Xc, ldK);
     int64_t used = 0;
-    if (bf) {
+    if (f8) {
+        // E4M3 copies of A with row powers of two, the panel quantised per column
+        launch_fp8_prep(s, A, lda, dtype == RSVDGB_BF16, m, n, A8, ld8, At8, ldt8, rs8, nullptr, nullptr);
+        launch_fp8_panel(s, Xc, ldK, K, l, L, transpose ? rs8 : nullptr, P8, ldp8, ts8);
+        rc = launch_f8_pass(s, h->sm_count, transpose, transpose ? At8 : A8, M, K, transpose ? ldt8 : ld8, P8, ldp8,
+                            L, transpose ? nullptr : rs8, ts8, Yc, ldM, part, &used, status);
+    } else if (bf) {
         launch_to_bf16(s, Xc, ldK, K, l, L, Xh);
         rc = launch_tc_gemm(s, h->sm_count, transpose, (const float*)A, m, n, lda, Xh, nullptr, ldK, L, Yc, nullptr,
                             nullptr, ldM, part, transpose ? 0 : 1, &used, status, nullptr, 0, 0, 1,

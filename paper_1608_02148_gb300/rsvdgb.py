@@ -20,7 +20,7 @@ STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_NOMEM", 3: "ERR_CUDA", 4: "ERR_
           6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
 F32, BF16 = 0, 1
 SDIST = {"normal": 0, "unif": 1, "rademacher": 2}
-PREC = {"fp32": 0, "bf16_sketch": 1}
+PREC = {"fp32": 0, "bf16_sketch": 1, "fp8_sketch": 2}
 ENGINE = {"auto": 0, "simt": 1, "tc": 2, "tc_tf32": 3}
 LAYOUT = {"row": 0, "col": 1}
 

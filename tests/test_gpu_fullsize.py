@@ -6,8 +6,8 @@ run on the same stored matrix and the same Philox test matrix.
   default engine and precision) element by element against the oracle --
   sigma within 1e-5 sigma_1, U_k and V_k within the gap rule of the oracle's
   spectrum of B, and Q over the whole l-space within max(1e-4, 10 u32 kappa(B));
-  the BF16-sketch form at equal reconstruction error (<= 1.01x the oracle's
-  ||A - U S V^T||_F).
+  the BF16-sketch and FP8-sketch forms at equal reconstruction error (<= 1.01x
+  the oracle's ||A - U S V^T||_F).
 * A scaled case of the BF16-stored step-spectrum workload (20000 x 5000,
   sigma = 1 for i <= 200 and 1e-2 beyond, N(0, 1e-4^2) noise, k = 200, p = 20,
   q = 3): the FP32-accurate path against the same tolerances, the mixed form
@@ -96,9 +96,10 @@ def test_spiked_200000x2000_fp32_matches_oracle(rs, handle, spiked200k):
     _check_fp32(rs, handle, A, A_host, ref, k, p, q, seed=0)
 
 
-def test_spiked_200000x2000_bf16_sketch_at_equal_error(rs, handle, spiked200k):
+@pytest.mark.parametrize("prec", ["bf16_sketch", "fp8_sketch"])
+def test_spiked_200000x2000_mixed_at_equal_error(rs, handle, spiked200k, prec):
     A, A_host, ref, (k, p, q) = spiked200k
-    _check_equal_error(rs, handle, A, A_host, ref, k, p, q, seed=0, prec="bf16_sketch")
+    _check_equal_error(rs, handle, A, A_host, ref, k, p, q, seed=0, prec=prec)
 
 
 @pytest.fixture(scope="module")
@@ -116,6 +117,7 @@ def test_step_bf16_20000x5000_fp32_matches_oracle(rs, handle, step20k):
     _check_fp32(rs, handle, A, bits, ref, k, p, q, seed=1)
 
 
-def test_step_bf16_20000x5000_mixed_at_equal_error(rs, handle, step20k):
+@pytest.mark.parametrize("prec", ["bf16_sketch", "fp8_sketch"])
+def test_step_bf16_20000x5000_mixed_at_equal_error(rs, handle, step20k, prec):
     A, bits, ref, (k, p, q) = step20k
-    _check_equal_error(rs, handle, A, bits, ref, k, p, q, seed=1, prec="bf16_sketch")
+    _check_equal_error(rs, handle, A, bits, ref, k, p, q, seed=1, prec=prec)

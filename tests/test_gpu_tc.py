@@ -261,3 +261,61 @@ def test_full_size_scale_of_products(rs, handle):
     d = torch.diagonal(Q64.T @ Q64)
     assert float(torch.max(torch.abs(d - 1))) < 2e-6
     assert abs(scale_err(B, Q64.T @ A64)) < 5e-6
+
+
+@pytest.mark.parametrize("m,n,l", [(300, 200, 30), (1030, 520, 220), (4096, 256, 100), (777, 1024, 112), (64, 640, 8)])
+@pytest.mark.parametrize("stored", ["f32", "bf16"])
+def test_fp8_passes_match_oracle_products(rs, handle, m, n, l, stored):
+    """E4M3 products: A's rows and the panel's columns scaled by powers of two
+    into E4M3's range and rounded to nearest (relative error <= 2^-4 each in
+    the normal range), FP32 accumulation: |Y - Y_o| <= (2^-3 + 2^-7 + 2 K u32)
+    |A||X| plus K 2^-18 max_i|a| max_j|x| for entries below E4M3's normal
+    range; and visibly not BF16-accurate."""
+    import torch
+    rng = np.random.default_rng(3 * m + n + l)
+    A = (rng.standard_normal((m, n)) * np.exp2(rng.integers(-6, 6, size=(m, 1)))).astype(np.float32)
+    if stored == "bf16":
+        Ab = inputs.bf16_bits(A)
+        A_dev = to_dev(Ab.view(np.int16)).view(torch.bfloat16)
+        A_or = Ab
+        Aval = inputs.bf16_to_f32(Ab).astype(np.float64)
+    else:
+        A_dev = to_dev(A)
+        A_or = A
+        Aval = A.astype(np.float64)
+    X = rng.standard_normal((n, l)).astype(np.float32)
+    W = rng.standard_normal((m, l)).astype(np.float32)
+    Y = rs.rsvdgb_pass_ax(handle, A_dev, to_dev(X), engine="tc", prec="fp8_sketch").cpu().numpy().astype(np.float64)
+    Z = rs.rsvdgb_pass_atx(handle, A_dev, to_dev(W), engine="tc", prec="fp8_sketch").cpu().numpy().astype(np.float64)
+    Yo = oracle.gemm_ax(A_or, X.astype(np.float64))
+    Zo = oracle.gemm_atx(A_or, W.astype(np.float64))
+    Aa = np.abs(Aval)
+    c = 2.0 ** -3 + 2.0 ** -7
+    by = (c + 2 * n * 2.0 ** -24) * (Aa @ np.abs(X)) + n * 2.0 ** -18 * Aa.max(axis=1)[:, None] * np.abs(X).max(axis=0)
+    bz = (c + 2 * m * 2.0 ** -24) * (Aa.T @ np.abs(W)) + \
+        2.0 ** -18 * (Aa.max(axis=1) @ np.abs(W)).max() * np.ones((1, l))
+    assert np.all(np.abs(Y - Yo) <= by), float(np.max(np.abs(Y - Yo) / by))
+    assert np.all(np.abs(Z - Zo) <= bz), float(np.max(np.abs(Z - Zo) / bz))
+    assert np.max(np.abs(Y - Yo) / ((2.0 ** -8) * (Aa @ np.abs(X)))) > 1.0
+
+
+@pytest.mark.parametrize("m,n,k,p,q", [(2000, 1000, 20, 10, 2), (3000, 512, 100, 10, 2), (800, 300, 16, 8, 1),
+                                       (400, 1200, 12, 6, 2)])
+def test_fp8_sketch_rsvd_equal_error(rs, handle, m, n, k, p, q):
+    """Mixed precision with FP8 sketch and power passes (FP32-accurate
+    projection): ||A - U S V^T||_F <= 1.01 x the oracle's at the same (k, p, q)."""
+    import torch
+    if (m, n) == (2000, 1000):
+        A = inputs.small_planted()
+    else:
+        A = inputs.planted(m, n, inputs.exp_spectrum(min(m, n), 2.0 / k), seed=m + n)
+    d_o, U_o, V_o = oracle.rsvd(A, k, p=p, q=q, seed=3)
+    err_o = np.sqrt(oracle.residual_fro2(A, U_o, d_o, V_o))
+    d, U, V, info = rs.rsvdgb_rsvd(handle, to_dev(A), k, opts=rs.make_opts(p=p, q=q, seed=3, prec="fp8_sketch"))
+    torch.cuda.synchronize()
+    assert info.status == 0, info.as_dict()
+    err = np.sqrt(oracle.residual_fro2(A, U.cpu().numpy().astype(np.float64), d.cpu().numpy().astype(np.float64),
+                                       V.cpu().numpy().astype(np.float64)))
+    assert err <= 1.01 * err_o, (err, err_o)
+    fa = oracle.fro2(A)
+    assert abs(info.fro2_A - fa) <= 1e-5 * fa
