@@ -188,8 +188,10 @@ int launch_tslu(cudaStream_t s, const float* X, int64_t ld, int64_t rows, int l,
 // 16), At8 (its transpose, column-major: At8[c * ldt + i], ldt >= m, multiple
 // of 16) and the row powers of two rs (m floats); adds ||A||_F^2 to *fro2 and
 // max|A| (bits) to *amax when non-null.  launch_fp8_panel: column-major K x l
-// panel P (ld), optionally row-scaled by r, -> P8 (column-major bytes, ld8
-// >= K, multiple of 16, l_pad columns) and column powers of two ts.
+// panel P (ld a multiple of 4, 16-byte aligned), optionally row-scaled by r,
+// -> P8 (column-major bytes, ld8 >= K, multiple of 16, l_pad columns) and
+// column powers of two ts; cm is l_pad + 1 uints of scratch that must be zero
+// on entry and is left zero.
 // launch_f8_pass: out (lanes x l_pad column-major, ld_out) = A8_lanes P8 with
 // the lane-major copy A8 (A8 for the A side, At8 for the A^T side: lanes x
 // k_total, ld_a8 bytes), rows scaled by row_scale (optional) and columns by
@@ -198,7 +200,7 @@ int launch_tslu(cudaStream_t s, const float* X, int64_t ld, int64_t rows, int l,
 void launch_fp8_prep(cudaStream_t s, const void* A, int64_t lda, int a_bf16, int64_t m, int64_t n, uint8_t* A8,
                      int64_t ld8, uint8_t* At8, int64_t ldt, float* rs, double* fro2, unsigned int* amax);
 void launch_fp8_panel(cudaStream_t s, const float* P, int64_t ld, int64_t K, int l, int l_pad, const float* r,
-                      uint8_t* P8, int64_t ld8, float* ts);
+                      uint8_t* P8, int64_t ld8, float* ts, unsigned int* cm);
 int launch_f8_pass(cudaStream_t s, int sm_count, bool trans, const uint8_t* A8, int64_t lanes, int64_t k_total,
                    int64_t ld_a8, const uint8_t* P8, int64_t ld_p8, int l_pad, const float* row_scale,
                    const float* col_scale, float* out, int64_t ld_out, float* partial, int64_t* splits_out,
@@ -258,9 +260,11 @@ void launch_finalize_info(cudaStream_t s, const float* sigma, int l, int k, floa
 // current device (called once per handle).
 int init_small_kernels();
 // Zero the status / breakdown counters, ||A||_F^2 and max|A| (each may be
-// null), and set fillv[0..nfill) to fillval (fillv may be null).
+// null), set fillv[0..nfill) to fillval (fillv may be null) and zero
+// zerov[0..nzero) (zerov may be null).
 void launch_clear_scalars(cudaStream_t s, int* status, int* breakdowns, double* fro2, unsigned int* amax = nullptr,
-                          float* fillv = nullptr, int nfill = 0, float fillval = 0.f);
+                          float* fillv = nullptr, int nfill = 0, float fillval = 0.f, unsigned int* zerov = nullptr,
+                          int nzero = 0);
 
 // Convert a column-major r x l (ld) matrix to row-major (ldo) with cols
 // columns (cols <= l), i.e. out[i*ldo + j] = in[j*ld + i].

@@ -165,6 +165,7 @@ struct Work {
     uint8_t *A8, *At8, *P8;
     int64_t ld8, ldt8, ldp8;
     float *rs8, *ts8;
+    unsigned int* cm8;  // the panel quantisation's column maxima and CTA count (zero between panels)
 };
 
 constexpr int kPqrSlots = 1024;  // per-CTA maxima of the pivoted QR (its grid is at most this wide)
@@ -255,6 +256,7 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w, int L_lo = 0)
     w.luscr = g.lu ? c.take<int>(tslu_scratch_ints(std::max(g.ldm, g.ldn), g.L)) : nullptr;
     w.A8 = w.At8 = w.P8 = nullptr;
     w.rs8 = w.ts8 = nullptr;
+    w.cm8 = nullptr;
     w.ld8 = round_up(g.sn(), 16);
     w.ldt8 = round_up(g.sm(), 16);
     w.ldp8 = round_up(std::max(g.m, g.n), 16);
@@ -264,6 +266,7 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w, int L_lo = 0)
         w.P8 = c.take<uint8_t>((size_t)g.L * w.ldp8);
         w.rs8 = c.take<float>(g.sm());
         w.ts8 = c.take<float>(g.L);
+        w.cm8 = c.take<unsigned int>(g.L + 1);
     }
     w.amax = c.take<unsigned int>(1);
     w.Ppinv = c.take<float>(L);
@@ -496,7 +499,7 @@ void pass_fp8(rsvdgb_handle* h, const Geom& g, Work& w, bool A_side, const float
     const int64_t rows = A_side ? g.m : g.n;
     const int64_t ldP = A_side ? g.ldn : g.ldm;
     const int64_t ldO = A_side ? g.ldm : g.ldn;
-    launch_fp8_panel(s, P, ldP, K, g.l, g.L, stored_atx ? w.rs8 : nullptr, w.P8, w.ldp8, w.ts8);
+    launch_fp8_panel(s, P, ldP, K, g.l, g.L, stored_atx ? w.rs8 : nullptr, w.P8, w.ldp8, w.ts8, w.cm8);
     int64_t splits = 0;
     prof_mark(h, true, 0);
     launch_f8_pass(s, h->sm_count, stored_atx, stored_atx ? w.At8 : w.A8, rows, K, stored_atx ? w.ldt8 : w.ld8,
@@ -828,7 +831,8 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
     carve_work(c, g, sm, w, L_lo);
 
     // the m-side bases carry the fixed FP16 split scale kQSplitScale
-    launch_clear_scalars(s, w.status, w.breakdowns, w.fro2, w.amax, w.Qpinv, g.L, 1.f / kQSplitScale);
+    launch_clear_scalars(s, w.status, w.breakdowns, w.fro2, w.amax, w.Qpinv, g.L, 1.f / kQSplitScale, w.cm8,
+                         w.cm8 ? g.L + 1 : 0);
     Affine aff{};
     if (pca) {
         // randomized PCA: per-variable centre and scale in one pass over A;
@@ -1654,6 +1658,7 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
         probe.take<uint8_t>((size_t)L * ldp8);
         probe.take<float>(m);
         probe.take<float>(L);
+        probe.take<unsigned int>(L + 1);
     }
     rc = ensure_workspace(h, probe.off + 1024);
     if (rc) return rc;
@@ -1667,12 +1672,15 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
     float* pinv = c.take<float>(L);
     uint8_t *A8 = nullptr, *At8 = nullptr, *P8 = nullptr;
     float *rs8 = nullptr, *ts8 = nullptr;
+    unsigned int* cm8 = nullptr;
     if (f8) {
         A8 = c.take<uint8_t>((size_t)m * ld8);
         At8 = c.take<uint8_t>((size_t)n * ldt8);
         P8 = c.take<uint8_t>((size_t)L * ldp8);
         rs8 = c.take<float>(m);
         ts8 = c.take<float>(L);
+        cm8 = c.take<unsigned int>(L + 1);
+        RSVDGB_CUDA_TRY(cudaMemsetAsync(cm8, 0, (L + 1) * sizeof(unsigned int), h->stream));
     }
     unsigned int* amax = (unsigned int*)(status + 1);
     const cudaStream_t s = h->stream;
@@ -1682,7 +1690,7 @@ static int pass_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, in
     if (f8) {
         // E4M3 copies of A with row powers of two, the panel quantised per column
         launch_fp8_prep(s, A, lda, dtype == RSVDGB_BF16, m, n, A8, ld8, At8, ldt8, rs8, nullptr, nullptr);
-        launch_fp8_panel(s, Xc, ldK, K, l, L, transpose ? rs8 : nullptr, P8, ldp8, ts8);
+        launch_fp8_panel(s, Xc, ldK, K, l, L, transpose ? rs8 : nullptr, P8, ldp8, ts8, cm8);
         rc = launch_f8_pass(s, h->sm_count, transpose, transpose ? At8 : A8, M, K, transpose ? ldt8 : ld8, P8, ldp8,
                             L, transpose ? nullptr : rs8, ts8, Yc, ldM, part, &used, status);
     } else if (bf) {

@@ -729,8 +729,9 @@ __global__ void finalize_info_kernel(const float* __restrict__ sigma, int l, int
 }
 
 __global__ void clear_scalars_kernel(int* status, int* breakdowns, double* fro2, unsigned int* amax, float* fillv,
-                                     int nfill, float fillval)
+                                     int nfill, float fillval, unsigned int* zerov, int nzero)
 {
+    for (int i = threadIdx.x; i < nzero; i += blockDim.x) zerov[i] = 0u;
     if (threadIdx.x == 0) {
         if (status) *status = 0;
         if (breakdowns) *breakdowns = 0;
@@ -923,9 +924,10 @@ void launch_finalize_info(cudaStream_t s, const float* sigma, int l, int k, floa
 }
 
 void launch_clear_scalars(cudaStream_t s, int* status, int* breakdowns, double* fro2, unsigned int* amax,
-                          float* fillv, int nfill, float fillval)
+                          float* fillv, int nfill, float fillval, unsigned int* zerov, int nzero)
 {
-    clear_scalars_kernel<<<1, 256, 0, s>>>(status, breakdowns, fro2, amax, fillv, fillv ? nfill : 0, fillval);
+    clear_scalars_kernel<<<1, 256, 0, s>>>(status, breakdowns, fro2, amax, fillv, fillv ? nfill : 0, fillval, zerov,
+                                           zerov ? nzero : 0);
     count_launches();
 }
 

@@ -263,14 +263,16 @@ def test_full_size_scale_of_products(rs, handle):
     assert abs(scale_err(B, Q64.T @ A64)) < 5e-6
 
 
-@pytest.mark.parametrize("m,n,l", [(300, 200, 30), (1030, 520, 220), (4096, 256, 100), (777, 1024, 112), (64, 640, 8)])
+@pytest.mark.parametrize("m,n,l", [(300, 200, 30), (1030, 520, 220), (4096, 256, 100), (777, 1024, 112), (64, 640, 8),
+                                   (200, 2104, 40), (90, 4200, 24)])
 @pytest.mark.parametrize("stored", ["f32", "bf16"])
 def test_fp8_passes_match_oracle_products(rs, handle, m, n, l, stored):
     """E4M3 products: A's rows and the panel's columns scaled by powers of two
     into E4M3's range and rounded to nearest (relative error <= 2^-4 each in
     the normal range), FP32 accumulation: |Y - Y_o| <= (2^-3 + 2^-7 + 2 K u32)
     |A||X| plus K 2^-18 max_i|a| max_j|x| for entries below E4M3's normal
-    range; and visibly not BF16-accurate."""
+    range; and visibly not BF16-accurate.  n > 2048 takes the prep kernel's
+    two-read path (rows wider than a register-resident chunk)."""
     import torch
     rng = np.random.default_rng(3 * m + n + l)
     A = (rng.standard_normal((m, n)) * np.exp2(rng.integers(-6, 6, size=(m, 1)))).astype(np.float32)
@@ -296,7 +298,9 @@ def test_fp8_passes_match_oracle_products(rs, handle, m, n, l, stored):
         2.0 ** -18 * (Aa.max(axis=1) @ np.abs(W)).max() * np.ones((1, l))
     assert np.all(np.abs(Y - Yo) <= by), float(np.max(np.abs(Y - Yo) / by))
     assert np.all(np.abs(Z - Zo) <= bz), float(np.max(np.abs(Z - Zo) / bz))
-    assert np.max(np.abs(Y - Yo) / ((2.0 ** -8) * (Aa @ np.abs(X)))) > 1.0
+    # E4M3 rounding of both operands leaves ~5% relative error in Frobenius
+    # norm (BF16 would leave ~0.15%), whatever K
+    assert np.linalg.norm(Y - Yo) / np.linalg.norm(Yo) > 2.0 ** -7
 
 
 @pytest.mark.parametrize("m,n,k,p,q", [(2000, 1000, 20, 10, 2), (3000, 512, 100, 10, 2), (800, 300, 16, 8, 1),
