@@ -169,7 +169,8 @@ int launch_tc_gemm(cudaStream_t s, int sm_count, bool trans, const float* A, int
 // row-major upper triangular T (entries below the diagonal must be zero),
 // in FP32 FMA; Z column-major (ld) over l_pad columns, rows beyond `rows` up
 // to ld and columns beyond l written as zero.  split 1: Zh / Zl get Z's TF32
-// hi / lo (floats); split 2: the FP16 hi / lo (uint16) of sc Z.  l_pad <= 112.
+// hi / lo (floats); split 2: the FP16 hi / lo (uint16) of sc Z.  l_pad a
+// multiple of 16 up to 112, ld a multiple of 4, X 16-byte aligned.
 bool xt_supported(int l_pad);
 int launch_xt(cudaStream_t s, int sm_count, const float* X, int64_t ld, int64_t rows, int l, int l_pad, const float* T,
               float* Z, int split, void* Zh, void* Zl, float sc);

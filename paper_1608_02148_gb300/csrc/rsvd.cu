@@ -468,11 +468,9 @@ void tc_times_small(rsvdgb_handle* h, const Geom& g, Work& w, const float* Xt, i
 {
     // T is a Cholesky factor's inverse (upper triangular): up to l_pad = 112
     // the FP32 FMA kernel streams X once at the bandwidth bound
-    if (xt_supported(g.L)) {
-        launch_xt(h->stream, h->sm_count, Xt, ld, rows, g.l, g.L, T, Zt, Zh ? (f16 ? 2 : 1) : 0, Zh, Zl,
-                  kQSplitScale);
+    if (xt_supported(g.L) && launch_xt(h->stream, h->sm_count, Xt, ld, rows, g.l, g.L, T, Zt,
+                                       Zh ? (f16 ? 2 : 1) : 0, Zh, Zl, kQSplitScale) == RSVDGB_OK)
         return;
-    }
     launch_small_panel(h->stream, T, g.l, g.L, w.Th, w.Tl);
     int64_t splits = 0;
     TcExtra x{};
