@@ -46,10 +46,10 @@ WORKLOADS = {
 }
 
 # DRAM bytes (read + write) per byte of A of the FP32 tensor-core pass kernel,
-# averaged over the six passes of one rSVD, from one ncu capture on the
-# 50000 x 2000 workload.  The traffic scales with the rows processed, so the full-size launches carry the
-# same ratio.  None until the current pass kernel has been captured.
-TC_PASS_TRAFFIC_PER_A_BYTE = None
+# per launch, from one ncu capture (--set full, the first two launches of the
+# 200000 x 2000 rSVD): the first pass (3xTF32, Y written) 1.711 GB and an
+# A^T-side FP16x3 pass (panel read) 1.694 GB, for 1.6 GB of A each.
+TC_PASS_TRAFFIC_PER_A_BYTE = (1.711e9 + 1.694e9) / 2 / 1.6e9
 
 # The roofline the method's target is stated against: bytes of A per pass x
 # passes at 8 TB/s (nominal HBM3e); the measured copy bandwidth is the other.
@@ -511,11 +511,12 @@ def main():
                                  "peak_source": peak_kind}}
     else:
         traffic = None
-        if TC_PASS_TRAFFIC_PER_A_BYTE is not None and args.prec == "fp32" and A.dtype == torch.float32:
+        if (TC_PASS_TRAFFIC_PER_A_BYTE is not None and args.prec == "fp32" and A.dtype == torch.float32
+                and engine == "tc_fp16x3"):
             traffic = TC_PASS_TRAFFIC_PER_A_BYTE * a_bytes
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                     "frac": achieved_gbs / hbm, "traffic": traffic, "peak_source": peak_kind,
-                    "traffic_source": "ncu dram bytes on the 50000x2000 workload, scaled by rows"
+                    "traffic_source": "ncu dram bytes per launch (first pass and an A^T-side pass, 200000x2000)"
                     if traffic is not None else None,
                     "kernel": ("tc_pass_kernel (pass over A, tcgen05: the first pass 3xTF32 measuring max|A|, "
                                "the later passes scaled FP16x3)" if engine == "tc_fp16x3" else
@@ -681,10 +682,10 @@ def main():
             A_rows = A[:rows].view(torch.int16).cpu().numpy().view(np.uint16)
         else:
             A_rows = A[:rows].cpu().numpy()
-        reps = [cpu_oracle_time(A_rows, wl, 0) for _ in range(3)]
+        reps = [cpu_oracle_time(A_rows, wl, 0) for _ in range(5)]
         t = statistics.median(reps)
         cpu = {"value": t * (m / rows) * 1e3, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": f"oracle rsvd on rows 0..{rows - 1} of the same A ({rows}x{n}), median of 3, "
+               "sample": f"oracle rsvd on rows 0..{rows - 1} of the same A ({rows}x{n}), median of 5, "
                          f"time x{m / rows:g}",
                "sample_s": [round(x, 4) for x in reps]}
 
