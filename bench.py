@@ -518,7 +518,11 @@ def main():
                     "frac": achieved_gbs / hbm, "traffic": traffic, "peak_source": peak_kind,
                     "traffic_source": "ncu dram bytes per launch (first pass and an A^T-side pass, 200000x2000)"
                     if traffic is not None else None,
-                    "kernel": ("tc_pass_kernel (pass over A, tcgen05: the first pass 3xTF32 measuring max|A|, "
+                    "kernel": ("f8_pass_kernel (E4M3 sketch and power passes, bytes of the E4M3 copy of A) and "
+                               "tc_pass_kernel (FP16x3 projection, bytes of A)" if args.prec == "fp8_sketch" else
+                               "tc_pass_kernel (BF16 sketch and power passes, FP16x3 projection)"
+                               if args.prec == "bf16_sketch" else
+                               "tc_pass_kernel (pass over A, tcgen05: the first pass 3xTF32 measuring max|A|, "
                                "the later passes scaled FP16x3)" if engine == "tc_fp16x3" else
                                "tc_pass_kernel (pass over A, tcgen05 3xTF32)"),
                     "tensor_view": {"achieved_tflops_algorithmic": achieved_tflops,
