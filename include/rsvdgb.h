@@ -108,7 +108,7 @@ typedef struct rsvdgb_opts {
     int32_t layout;  /* RSVDGB_ROW_MAJOR / COL_MAJOR; default ROW_MAJOR          */
     int32_t engine;  /* RSVDGB_ENGINE_*; default AUTO                             */
     int32_t q_mode;  /* RSVDGB_Q_FIXED / RSVDGB_Q_LEARNED; default FIXED          */
-    int32_t p_max;   /* learned mode: largest oversampling (>= 2); default 24     */
+    int32_t p_max;   /* learned mode: largest oversampling (>= 2); default 10     */
     int32_t q_max;   /* learned mode: largest q; default 6                        */
     int32_t batched_eager; /* 1: rsvdgb_rsvd_batched runs its stages eagerly
                               instead of replaying its CUDA graph; default 0  */

@@ -8,10 +8,11 @@ This script
    uniform in [2000, 20000], n in [1000, 5000], k log-uniform in
    [10, 200], spectra exponential / power-law / step), so the rank-k optimum
    ||A - A_k||_F = sqrt(sum_{i>k} sigma_i^2) is known in closed form;
-2. labels each one with the cheapest (q, p) on a grid (cost (2q + 2)(k + p),
-   proportional to the work of the passes) whose rSVD meets
-   ||A - U S V^T||_F <= 1.03 x optimum + 1e-4 ||A||_F, running this library's
-   rSVD (the evaluation asks for 1.05 x: the labels keep a margin for the
+2. labels each one with the fastest (q, p) on a grid, by measured wall time
+   of this library's rSVD on the GPU (passes and l x l kernels included),
+   among those whose rSVD meets
+   ||A - U S V^T||_F <= 1.03 x optimum + 1e-4 ||A||_F (the evaluation asks
+   for 1.05 x: the labels keep a margin for the
    randomness of Omega; the second term is the resolution of the FP32 path:
    on spectra decaying by more than ~10^4 across the sketch, FP32 CholeskyQR
    leaves an error near 1e-4 ||A||_F whatever q and p);
@@ -23,7 +24,7 @@ This script
    passes over A and wall time of the learned mode against fixed p = 10,
    q = 2.
 
-Usage (one GPU):  python -m paper_1608_02148_gb300.controller_train --train 2500 --eval 64 \\
+Usage (one GPU):  python -m paper_1608_02148_gb300.controller_train --train 1200 --eval 512 \\
                       --out paper_1608_02148_gb300/controller_default.bin
 """
 from __future__ import annotations
@@ -44,12 +45,16 @@ if __package__ in (None, ""):
 else:
     from . import inputs, rsvdgb
 
-P_GRID = (2, 4, 6, 10, 16, 24)
+# p at most the fixed default's 10: the learned mode takes its first sketch at
+# k + P_MAX, so a wider grid makes every learned run pay for a wider first
+# pass, Gram and Cholesky (measured: 0.48 ms per 20000 x 5000 rSVD at
+# P_MAX = 24 over the fixed path at the same (q, p))
+P_GRID = (2, 4, 6, 10)
 Q_GRID = (0, 1, 2, 3, 4, 5, 6)
 TARGET_RATIO = 1.05      # accuracy target of the evaluation
 LABEL_RATIO = 1.03       # labels ask for a margin inside it (one Omega per label)
 FP32_FLOOR = 1e-4        # resolution of the FP32 path on extremely graded spectra
-P_MAX = 24
+P_MAX = 10
 Q_MAX = 6
 
 
@@ -81,16 +86,52 @@ def run(h, A, k, p, q, seed, mode="fixed"):
     return d, U, V, info
 
 
+def timed(h, A, k, p, q, seed, reps=2):
+    """Fastest of `reps` CUDA-event timings of the rSVD at (q, p) (the caller
+    has just run it once, so the workspace is allocated and the caches warm)."""
+    import torch
+    st = torch.cuda.current_stream()
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        run(h, A, k, p, q, seed)
+        e1.record(st)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
 def label(h, A, k, target, seed):
-    """Cheapest (q, p) of the grid meeting the target; (Q_MAX, P_MAX) if none."""
-    cands = sorted(((2 * q + 2) * (k + p), q, p) for q in Q_GRID for p in P_GRID)
+    """The fastest (q, p) of the grid meeting the target, by measured time;
+    (Q_MAX, P_MAX) if none does.  Accuracy grows with q and with p, and so
+    does the time, so for each q only the smallest p that meets the target is
+    a candidate; it is at most the previous q's, and once it is the smallest
+    p of the grid a larger q can only be slower."""
     runs = 0
-    for _, q, p in cands:
-        d, U, V, info = run(h, A, k, p, q, seed)
-        runs += 1
-        if info.status == 0 and residual(A, d, U, V) <= target:
-            return q, p, runs
-    return Q_MAX, P_MAX, runs
+    best = None
+    p_cap = len(P_GRID) - 1
+    for q in Q_GRID:
+        found = None
+        for ip in range(p_cap + 1):
+            d, U, V, info = run(h, A, k, P_GRID[ip], q, seed)
+            runs += 1
+            if info.status == 0 and residual(A, d, U, V) <= target:
+                found = ip
+                break
+        if found is None:
+            continue
+        t = timed(h, A, k, P_GRID[found], q, seed)
+        runs += 2
+        if best is None or t < best[0]:
+            best = (t, q, P_GRID[found])
+        p_cap = found
+        if found == 0:
+            break
+    if best is None:
+        return Q_MAX, P_MAX, runs
+    return best[1], best[2], runs
 
 
 def features(h, A, k, seed):
@@ -133,13 +174,13 @@ def evaluate(h, count, seed, m=20000, n=5000):
     """Learned mode (controller loaded in h) against fixed p = 10, q = 2."""
     import torch
     rng = np.random.default_rng(seed)
-    res = {"learned": {"ok": 0, "passes": 0, "ms": 0.0, "p": 0}, "fixed": {"ok": 0, "passes": 0, "ms": 0.0, "p": 0}}
+    res = {name: {"ok": 0, "ok_strict": 0, "passes": 0, "ms": 0.0, "p": 0} for name in ("learned", "fixed")}
     st = torch.cuda.current_stream()
     for i in range(count):
         _, _, k, sigma, kind = draw(rng, (m, m), (n, n))
         A = inputs.planted_reflector(m, n, sigma, seed=seed * 100003 + i, device="cuda")
         fro = math.sqrt(float(np.sum(sigma ** 2)))
-        target, _ = target_of(sigma, k, fro)
+        target, opt = target_of(sigma, k, fro)
         for name, mode in (("learned", "learned"), ("fixed", "fixed")):
             run(h, A, k, 10, 2, seed + i, mode)  # warm
             e0 = torch.cuda.Event(enable_timing=True)
@@ -152,10 +193,13 @@ def evaluate(h, count, seed, m=20000, n=5000):
             r["ms"] += e0.elapsed_time(e1)
             r["passes"] += 2 * info.q_used + 2
             r["p"] += info.p_used
-            r["ok"] += int(info.status == 0 and residual(A, d, U, V) <= target)
+            err = residual(A, d, U, V)
+            r["ok"] += int(info.status == 0 and err <= target)
+            r["ok_strict"] += int(info.status == 0 and err <= TARGET_RATIO * opt)
         del A
     for r in res.values():
         r["success_rate"] = r.pop("ok") / count
+        r["success_rate_without_floor"] = r.pop("ok_strict") / count
         r["mean_passes"] = r.pop("passes") / count
         r["mean_ms"] = r.pop("ms") / count
         r["mean_p"] = r.pop("p") / count
@@ -169,10 +213,10 @@ def main(argv=None):
     torch.backends.cuda.matmul.allow_tf32 = False
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=2500, help="training matrices")
-    ap.add_argument("--eval", type=int, default=64, help="held-out 20000 x 5000 matrices")
+    ap.add_argument("--eval", type=int, default=512, help="held-out 20000 x 5000 matrices")
     ap.add_argument("--seed", type=int, default=0x160802148 + 5000)
     ap.add_argument("--epochs", type=int, default=500)
-    ap.add_argument("--tau", type=float, default=0.99)
+    ap.add_argument("--tau", type=float, default=0.98)
     ap.add_argument("--dataset", default=None, help="data set file (written, or read with --reuse)")
     ap.add_argument("--reuse", action="store_true", help="train on an existing data set file")
     ap.add_argument("--out", required=True, help="parameter file to write")

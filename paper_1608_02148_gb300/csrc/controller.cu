@@ -57,7 +57,10 @@ __device__ __forceinline__ float relu(float x) { return x > 0.f ? x : 0.f; }
 __global__ void features_kernel(const float* __restrict__ R, int lmax, const double* __restrict__ fro2, int64_t m,
                                 int64_t n, int k, int p_max, float* __restrict__ f)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    // one warp: lane c takes the columns j = c + 1, c + 33, ... of the sums
+    // (FP64 per lane, then a shuffle reduction); lane 0 writes the features
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
     const float tiny = 1e-30f;
     auto rd = [&](int j) {  // |R_jj|, j 1-based, clamped to [1, lmax]
         j = min(max(j, 1), lmax);
@@ -66,7 +69,7 @@ __global__ void features_kernel(const float* __restrict__ R, int lmax, const dou
     const float r1 = rd(1);
     auto lr = [&](int j) { return log10f(rd(j) / r1); };
     double e_all = 0.0, e_k = 0.0, tr = 0.0;
-    for (int j = 1; j <= lmax; ++j) {
+    for (int j = 1 + lane; j <= lmax; j += 32) {
         const double v = (double)rd(j) * (double)rd(j);
         e_all += v;
         if (j <= k) e_k += v;
@@ -76,6 +79,13 @@ __global__ void features_kernel(const float* __restrict__ R, int lmax, const dou
             tr += x * x;
         }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e_all += __shfl_xor_sync(0xffffffffu, e_all, o);
+        e_k += __shfl_xor_sync(0xffffffffu, e_k, o);
+        tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    }
+    if (lane != 0) return;
     const double fa = fro2 ? *fro2 : 0.0;
     f[0] = log10f((float)m);
     f[1] = log10f((float)n);
@@ -97,33 +107,32 @@ __global__ void features_kernel(const float* __restrict__ R, int lmax, const dou
 }
 
 // ---------------------------------------------------------------- inference
-// One thread per sample: out[i] = MLP((X[i] - mu) / sd).
-__global__ void mlp_forward_kernel(const float* __restrict__ P, const float* __restrict__ X, int n,
-                                   float* __restrict__ out)
+// out[i] = MLP((X[i] - mu) / sd).
+__global__ void __launch_bounds__(NH) mlp_forward_kernel(const float* __restrict__ P, const float* __restrict__ X,
+                                                           int n, float* __restrict__ out)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // one CTA per sample, thread j = hidden unit j; every sum runs over its
+    // inputs in increasing order, as a single thread would
+    __shared__ float x[NI], h1[NH], h2[NH];
+    const int i = blockIdx.x, j = threadIdx.x;
     if (i >= n) return;
-    float x[NI], h1[NH];
+    if (j < NI) x[j] = (X[(int64_t)i * NI + j] - P[kOffMu + j]) / P[kOffSd + j];
+    __syncthreads();
+    float a = P[kOffB1 + j];
 #pragma unroll
-    for (int t = 0; t < NI; ++t) x[t] = (X[(int64_t)i * NI + t] - P[kOffMu + t]) / P[kOffSd + t];
-    for (int j = 0; j < NH; ++j) {
-        float a = P[kOffB1 + j];
-#pragma unroll
-        for (int t = 0; t < NI; ++t) a = fmaf(P[kOffW1 + j * NI + t], x[t], a);
-        h1[j] = relu(a);
+    for (int t = 0; t < NI; ++t) a = fmaf(P[kOffW1 + j * NI + t], x[t], a);
+    h1[j] = relu(a);
+    __syncthreads();
+    float b = P[kOffB2 + j];
+#pragma unroll 16
+    for (int t = 0; t < NH; ++t) b = fmaf(P[kOffW2 + j * NH + t], h1[t], b);
+    h2[j] = relu(b);
+    __syncthreads();
+    if (j < NO) {
+        float o = P[kOffB3 + j];
+        for (int t = 0; t < NH; ++t) o = fmaf(P[kOffW3 + j * NH + t], h2[t], o);
+        out[(int64_t)i * NO + j] = o;
     }
-    float o[NO];
-#pragma unroll
-    for (int c = 0; c < NO; ++c) o[c] = P[kOffB3 + c];
-    for (int j = 0; j < NH; ++j) {
-        float a = P[kOffB2 + j];
-        for (int t = 0; t < NH; ++t) a = fmaf(P[kOffW2 + j * NH + t], h1[t], a);
-        a = relu(a);
-#pragma unroll
-        for (int c = 0; c < NO; ++c) o[c] = fmaf(P[kOffW3 + c * NH + j], a, o[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < NO; ++c) out[(int64_t)i * NO + c] = o[c];
 }
 
 // (q, p) from the network's (q_hat, log2 p_hat), rounded up from kRoundUp
@@ -311,7 +320,7 @@ void launch_controller_features(cudaStream_t s, const float* R, int lmax, const 
 void launch_mlp_forward(cudaStream_t s, const float* P, const float* X, int n, float* out)
 {
     if (n <= 0) return;
-    mlp_forward_kernel<<<(n + 127) / 128, 128, 0, s>>>(P, X, n, out);
+    mlp_forward_kernel<<<n, NH, 0, s>>>(P, X, n, out);
     count_launches();
 }
 

@@ -865,12 +865,17 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
         RSVDGB_CUDA_TRY(cudaStreamSynchronize(s));
         q = h->ctl_host[0];
         // continue with the first k + p columns of the sketch (Omega nested in l)
+        const int lw = g.l;
         g.l = (int)std::min<int64_t>((int64_t)k + h->ctl_host[1], g.n);
         g.L = (int)round_up(g.l, 16);
-        if (g.use_tc)
-            tc_gram(h, g, w, w.Yt, w.Yth, w.Ytl, g.ldm, g.m);
-        else
-            gram(s, sm, w.Yt, g.ldm, g.m, g.l, w.part, w.G);
+        // the Gram of the first l columns is the leading l x l block of the
+        // wide sketch's Gram (each entry is the same sum of products)
+        if (g.l < lw) {
+            const size_t row = sizeof(float) * (size_t)g.l;
+            RSVDGB_CUDA_TRY(cudaMemcpy2DAsync(w.M, row, w.G, sizeof(float) * (size_t)lw, row, (size_t)g.l,
+                                              cudaMemcpyDeviceToDevice, s));
+            RSVDGB_CUDA_TRY(cudaMemcpyAsync(w.G, w.M, row * (size_t)g.l, cudaMemcpyDeviceToDevice, s));
+        }
     }
     const int l = g.l;
     // split of an m-side basis for the A^T-side pass that reads it: none in
@@ -1077,7 +1082,7 @@ void rsvdgb_default_opts(rsvdgb_opts* o)
     o->layout = RSVDGB_ROW_MAJOR;
     o->engine = RSVDGB_ENGINE_AUTO;
     o->q_mode = RSVDGB_Q_FIXED;
-    o->p_max = 24;
+    o->p_max = 10;
     o->q_max = 6;
 }
 
