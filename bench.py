@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--rrpca", type=int, default=1, help="time the robust PCA workload (0 = skip)")
     ap.add_argument("--variants", type=int, default=1,
                     help="time the other precision and the learned mode on the same A (0 = skip)")
-    ap.add_argument("--controller-eval", type=int, default=16,
+    ap.add_argument("--controller-eval", type=int, default=64,
                     help="held-out 20000x5000 matrices for the learned-(q, p) evaluation (0 = skip)")
     return ap.parse_args()
 
