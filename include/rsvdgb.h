@@ -114,7 +114,8 @@ typedef struct rsvdgb_opts {
                               instead of replaying its CUDA graph; default 0  */
     int32_t power;   /* RSVDGB_POWER_*: how the power iterations renormalise;
                         default SUBSPACE                                       */
-    int32_t reserved; /* zero                                                  */
+    int32_t check_orth; /* 1: measure max |(Q^T Q - I)_ij| of the final basis
+                           into info.orth_max (one extra Gram of Q); default 0 */
 } rsvdgb_opts;
 
 /* Diagnostics written by the device at the end of a call (device memory). */
@@ -130,7 +131,9 @@ typedef struct rsvdgb_info {
     int32_t breakdowns;  /* Cholesky breakdowns met (each retried with a shift) */
     int32_t engine;      /* kernel family that ran the passes: RSVDGB_ENGINE_SIMT, _TC or _TC_TF32 */
     int32_t jacobi_sweeps; /* sweeps of the one-sided Jacobi SVD of the l x l factor */
-    int32_t reserved[5];
+    float orth_max;      /* max_ij |(Q^T Q - I)_ij| of the final basis Q (FP32
+                            Gram) when opts.check_orth, else -1               */
+    int32_t reserved[4];
 } rsvdgb_info;
 
 /* Create a handle bound to CUDA device `device` and stream `cuda_stream`

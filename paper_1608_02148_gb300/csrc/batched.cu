@@ -656,6 +656,7 @@ __global__ void finalize_kernel(const MatDev* __restrict__ D, int B, const float
     inf.breakdowns = *breakdowns;
     inf.engine = RSVDGB_ENGINE_SIMT;
     inf.jacobi_sweeps = *sweeps;
+    inf.orth_max = -1.f;  // not measured in the batched call
     infos[b] = inf;
 }
 

@@ -256,7 +256,9 @@ void launch_small_transpose(cudaStream_t s, const float* in, float* out, int l);
 // d[0..k) = sigma[0..k); info fields from fro2_A and sigma.
 void launch_finalize_info(cudaStream_t s, const float* sigma, int l, int k, float* d, const double* fro2A,
                           const int* status, const int* breakdowns, int q, int p_used, int engine,
-                          const int* sweeps, rsvdgb_info* info);
+                          const int* sweeps, rsvdgb_info* info, const float* orth = nullptr);
+// max_ij |G_ij - delta_ij| of an l x l row-major Gram into *out (device).
+void launch_orth_err(cudaStream_t s, const float* G, int l, float* out);
 // Raise the dynamic shared-memory limit of the one-CTA kernels on the
 // current device (called once per handle).
 int init_small_kernels();

@@ -141,6 +141,7 @@ struct Work {
     float *T1, *T2, *T, *R1, *R2, *RB, *M, *sigma, *Ut, *Jt, *jwork;
     int *status, *breakdowns, *sweeps;
     double* fro2;
+    float* orth;  // max |Q^T Q - I| of the final basis (opts.check_orth)
     // randomized PCA: centre and multiplier per variable, statistics and
     // correction partial sums
     float *mu, *cmul;
@@ -275,6 +276,7 @@ void carve_work(Carve& c, const Geom& g, int sm_count, Work& w, int L_lo = 0)
     w.breakdowns = c.take<int>(1);
     w.sweeps = c.take<int>(1);
     w.fro2 = c.take<double>(1);
+    w.orth = c.take<float>(1);
     w.mu = w.cmul = nullptr;
     w.spart = nullptr;
     w.hpart = w.fpart = nullptr;
@@ -699,6 +701,7 @@ struct Outputs {
     float* Brow;  // optional row-major B (l x n) for rqb
     int64_t ldb;
     rsvdgb_info* info;
+    bool check_orth;  // measure max |Q^T Q - I| of the final basis into info.orth_max
     int sigma_cols;  // 1: columns of the logical U scaled by sigma; 2: of V (PCA scores)
     const struct RidSpec* rid;  // interpolative / CUR decomposition instead of the SVD of B
 };
@@ -938,13 +941,18 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
         tc_times_small(h, g, w, w.Qt, g.ldm, g.m, w.T2, w.Yt, w.Yth, w.Ytl, g.h16);
     else
         times_small(s, sm, w.Qt, g.ldm, g.m, l, w.T2, w.Yt, w.part);
+    // optional check of the final basis: max |Q^T Q - I| from one more Gram
+    if (o.check_orth) {
+        gram(s, sm, w.Yt, g.ldm, g.m, l, w.part, w.G, (g.use_tc && g.L <= 128) ? (int)g.L : 0, w.status);
+        launch_orth_err(s, w.G, l, w.orth);
+    }
     // step 10: B^T = A^T Q (n x l, column-major: row j of B is contiguous)
     apply_At(h, g, w, true, w.Yt, w.Yth, w.Ytl, w.Qt, w.Qth, w.Qtl);
     if (o.rid) {
         const int rc = rid_tail(h, g, w, k, *o.rid);
         if (rc) return rc;
         launch_finalize_info(s, nullptr, 0, k, nullptr, w.fro2, w.status, w.breakdowns, q, l - k, engine_code(g),
-                             nullptr, o.info);
+                             nullptr, o.info, o.check_orth ? w.orth : nullptr);
         RSVDGB_CUDA_TRY(cudaGetLastError());
         return RSVDGB_OK;
     }
@@ -985,7 +993,7 @@ int run_fp32(rsvdgb_handle* h, Geom g, int k, int q, int sdist, uint64_t seed, c
         // through a cheap Gram of B (sigma unused).
     }
     launch_finalize_info(s, o.d ? w.sigma : nullptr, o.d ? l : 0, k, o.d, w.fro2, w.status, w.breakdowns, q,
-                         l - k, engine_code(g), o.d ? w.sweeps : nullptr, o.info);
+                         l - k, engine_code(g), o.d ? w.sweeps : nullptr, o.info, o.check_orth ? w.orth : nullptr);
     // Lambda = Sigma^2 / (m - 1) over the singular values just copied to d
     if (pca) launch_pca_values(s, w.sigma, k, pca->m_obs, pca->eig, pca->sdev);
     RSVDGB_CUDA_TRY(cudaGetLastError());
@@ -1185,6 +1193,7 @@ int rsvdgb_rsvd(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t l
     Outputs out{};
     out.d = d;
     out.info = info;
+    out.check_orth = o.check_orth != 0;
     if (!g.swap_uv) {
         out.U = U; out.ldU = ldu; out.nU = nu;
         out.V = V; out.ldV = ldv; out.nV = nv;
@@ -1223,6 +1232,7 @@ int rsvdgb_rqb(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int64_t ld
     out.Brow = B;
     out.ldb = ldb;
     out.info = info;
+    out.check_orth = o.check_orth != 0;
     return run_fp32(h, g, k, o.q, o.sdist, o.seed, out);
 }
 
@@ -1445,6 +1455,7 @@ static int rid_common(rsvdgb_handle* h, const void* A, int64_t m, int64_t n, int
     g.rid_cur = r.cur;
     Outputs out{};
     out.info = info;
+    out.check_orth = o.check_orth != 0;
     out.rid = &r;
     return run_fp32(h, g, k, o.q, o.sdist, o.seed, out);
 }

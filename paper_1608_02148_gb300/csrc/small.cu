@@ -689,9 +689,29 @@ __global__ void __launch_bounds__(NT, 1)
         }
 }
 
+// max_ij |G_ij - delta_ij| of an l x l row-major Gram (one CTA)
+__global__ void orth_err_kernel(const float* __restrict__ G, int l, float* __restrict__ out)
+{
+    __shared__ float red[8];
+    float mx = 0.f;
+    for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+        const int i = e / l, j = e - i * l;
+        mx = fmaxf(mx, fabsf(G[e] - (i == j ? 1.f : 0.f)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
+        *out = fmaxf(red[0], mx);
+    }
+}
+
 __global__ void finalize_info_kernel(const float* __restrict__ sigma, int l, int k, float* __restrict__ d,
                                      const double* fro2A, const int* status, const int* breakdowns, int q,
-                                     int p_used, int engine, const int* sweeps, rsvdgb_info* info)
+                                     int p_used, int engine, const int* sweeps, rsvdgb_info* info,
+                                     const float* orth)
 {
     const int tid = threadIdx.x;
     if (d && sigma)
@@ -725,6 +745,7 @@ __global__ void finalize_info_kernel(const float* __restrict__ sigma, int l, int
         info->breakdowns = breakdowns ? *breakdowns : 0;
         info->engine = engine;
         info->jacobi_sweeps = sweeps ? *sweeps : 0;
+        info->orth_max = orth ? *orth : -1.f;
     }
 }
 
@@ -917,10 +938,17 @@ void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, floa
 
 void launch_finalize_info(cudaStream_t s, const float* sigma, int l, int k, float* d, const double* fro2A,
                           const int* status, const int* breakdowns, int q, int p_used, int engine, const int* sweeps,
-                          rsvdgb_info* info)
+                          rsvdgb_info* info, const float* orth)
 {
     finalize_info_kernel<<<1, 256, 0, s>>>(sigma, l, k, d, fro2A, status, breakdowns, q, p_used, engine, sweeps,
-                                           info); count_launches();
+                                           info, orth);
+    count_launches();
+}
+
+void launch_orth_err(cudaStream_t s, const float* G, int l, float* out)
+{
+    orth_err_kernel<<<1, 256, 0, s>>>(G, l, out);
+    count_launches();
 }
 
 void launch_clear_scalars(cudaStream_t s, int* status, int* breakdowns, double* fro2, unsigned int* amax,

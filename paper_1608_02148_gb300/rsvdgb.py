@@ -47,7 +47,7 @@ class RsvdgbOpts(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("q", ctypes.c_int32), ("sdist", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("layout", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("q_mode", ctypes.c_int32), ("p_max", ctypes.c_int32), ("q_max", ctypes.c_int32),
-                ("batched_eager", ctypes.c_int32), ("power", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("batched_eager", ctypes.c_int32), ("power", ctypes.c_int32), ("check_orth", ctypes.c_int32)]
 
 
 class RsvdgbRrpcaOpts(ctypes.Structure):
@@ -70,8 +70,8 @@ class RsvdgbInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("q_used", ctypes.c_int32), ("p_used", ctypes.c_int32),
                 ("l", ctypes.c_int32), ("fro2_A", ctypes.c_double), ("fro2_B", ctypes.c_double),
                 ("err2_QB", ctypes.c_double), ("err2_k", ctypes.c_double), ("breakdowns", ctypes.c_int32),
-                ("engine", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("engine", ctypes.c_int32), ("jacobi_sweeps", ctypes.c_int32), ("orth_max", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 4)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -184,13 +184,14 @@ POWER = {"subspace": 0, "lu": 1}
 
 
 def make_opts(p=10, q=2, sdist="normal", prec="fp32", seed=0, layout="row", engine="auto", q_mode="fixed",
-              p_max=None, q_max=None, power="subspace") -> RsvdgbOpts:
+              p_max=None, q_max=None, power="subspace", check_orth=False) -> RsvdgbOpts:
     o = RsvdgbOpts()
     load().rsvdgb_default_opts(ctypes.byref(o))
     o.p, o.q, o.sdist, o.prec = p, q, SDIST[sdist], PREC[prec]
     o.power = POWER[power]
     o.seed, o.layout, o.engine = seed, LAYOUT[layout], ENGINE[engine]
     o.q_mode = Q_MODE[q_mode]
+    o.check_orth = int(bool(check_orth))
     if p_max is not None:
         o.p_max = p_max
     if q_max is not None:

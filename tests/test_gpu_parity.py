@@ -190,6 +190,25 @@ def test_rqb_q_orthonormal_and_b_projection(rs, handle):
     assert sin_theta(Q, Qo) <= max(1e-4, 10 * 2 ** -24 * sB[0] / max(sB[-1], 1e-30))
 
 
+@pytest.mark.parametrize("m,n,k", [(3000, 500, 30), (5000, 700, 150)])  # direct tensor-core Gram; l_pad > 128
+def test_info_orth_max_is_the_basis_orthogonality(rs, handle, m, n, k):
+    """opts.check_orth: info.orth_max = max |(Q^T Q - I)_ij| of the final basis
+    from one FP32 Gram on the device, against the same maximum taken in FP64
+    from the returned Q (the two differ by the Gram's FP32 rounding, a few
+    u32); without the flag the field reads -1."""
+    A = inputs.planted(m, n, inputs.exp_spectrum(n, 0.02), seed=m + k)
+    Q, _, info = rs.rsvdgb_rqb(handle, to_dev(A), k, opts=rs.make_opts(p=10, q=2, check_orth=True))
+    assert info.status == 0
+    Q = Q.cpu().numpy().astype(np.float64)
+    want = np.max(np.abs(Q.T @ Q - np.eye(Q.shape[1])))
+    assert 0.0 <= info.orth_max and abs(info.orth_max - want) <= 4e-6, (info.orth_max, want)
+    d, U, V, info2 = rs.rsvdgb_rsvd(handle, to_dev(A), k, opts=rs.make_opts(p=10, q=2, check_orth=True))
+    assert info2.status == 0 and abs(info2.orth_max - info.orth_max) <= 1e-6
+    _, _, _, info3 = rs.rsvdgb_rsvd(handle, to_dev(A), k, opts=rs.make_opts(p=10, q=2))
+    assert info3.orth_max == -1.0
+    np.testing.assert_array_equal(d.cpu().numpy(), rs.rsvdgb_rsvd(handle, to_dev(A), k)[0].cpu().numpy())
+
+
 def test_host_entry_point_matches_device(rs, handle):
     import torch
     A = inputs.planted(800, 300, inputs.exp_spectrum(300, 0.05), seed=12)
