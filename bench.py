@@ -73,6 +73,7 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=40000, help="row sample for the oracle baseline")
     ap.add_argument("--batched", type=int, default=4096, help="matrices in the batched workload (0 = skip)")
     ap.add_argument("--rpca", type=int, default=1, help="time the randomized PCA workload (0 = skip)")
+    ap.add_argument("--small", type=int, default=1, help="time the 2000 x 1000 planted workload (0 = skip)")
     ap.add_argument("--rid", type=int, default=1, help="time the interpolative and CUR decompositions (0 = skip)")
     ap.add_argument("--rrpca", type=int, default=1, help="time the robust PCA workload (0 = skip)")
     ap.add_argument("--variants", type=int, default=1,
@@ -185,6 +186,35 @@ def make_matrix(wl, seed, device):
         return inputs.spiked_noise(m, n, sigma, wl["noise"], seed, device=device)
     import torch
     return torch.from_numpy(inputs.planted(m, n, inputs.exp_spectrum(n, 1.0 / 20.0), seed)).to(device)
+
+
+def run_small(rs, h, dev, stream, steps):
+    """The small planted workload (2000 x 1000, sigma_i = exp(-i/20), k = 20,
+    p = 10, q = 2): device time of the rSVD, and its rank-k error (the
+    device's own estimate) against the planted optimum, known in closed form."""
+    import numpy as np
+    import torch
+    from paper_1608_02148_gb300 import inputs
+    wl = WORKLOADS["planted2k"]
+    A = torch.from_numpy(inputs.small_planted()).to(dev)
+    sigma = inputs.exp_spectrum(wl["n"], 1.0 / 20.0)
+    k = wl["k"]
+    opts = rs.make_opts(p=wl["p"], q=wl["q"], seed=1)
+    for _ in range(3):
+        rs.rsvdgb_rsvd(h, A, k, opts=opts, sync_info=False)
+    n_steps = max(steps, 20)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(n_steps):
+        rs.rsvdgb_rsvd(h, A, k, opts=opts, sync_info=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    _, _, _, info = rs.rsvdgb_rsvd(h, A, k, opts=opts)
+    opt = float(np.sqrt(np.sum(sigma[k:] ** 2)))
+    err = float(np.sqrt(max(info.err2_k, 0.0)))
+    return {"workload": wl["desc"], "ms": e0.elapsed_time(e1) / n_steps, "steps": n_steps, "status": info.status,
+            "err_k_fro": err, "optimum_k_fro": opt, "err_ratio_vs_optimum": err / opt}
 
 
 def run_batched(rs, h, dev, stream, count, steps, peaks):
@@ -633,6 +663,14 @@ def main():
         except Exception as exc:
             batched = {"unavailable": str(exc)}
 
+    # ---------------- the small planted workload (2000 x 1000) ----------------
+    small = None
+    if args.small > 0 and rank == 0:
+        try:
+            small = run_small(rs, h, dev, stream, args.steps)
+        except Exception as exc:
+            small = {"unavailable": str(exc)}
+
     # ---------------- interpolative and CUR decompositions (Algorithms rid, rcur) ----------------
     rid = None
     if args.rid > 0 and rank == 0 and A.dtype == torch.float32:
@@ -715,6 +753,7 @@ def main():
                 "variants": variants,
                 "controller": controller,
                 "batched": batched,
+                "small_planted": small,
                 "rpca": rpca,
                 "rid": rid,
                 "rrpca": rrpca,
