@@ -877,7 +877,7 @@ int init_small_kernels()
     rc |= raise_smem_limit(jacobi_kernel<8, 512, 2>, optin);
     rc |= raise_smem_limit(jacobi_kernel<10, 512, 2>, optin);
     rc |= raise_smem_limit(jacobi_kernel<12, 512, 2>, optin);
-    rc |= raise_smem_limit(jacobi_kernel<14, 512, 2>, optin);
+    rc |= raise_smem_limit(jacobi_kernel<14, 448, 2>, optin);
     rc |= raise_smem_limit(jacobi_kernel<16, 512, 2>, optin);
     rc |= raise_smem_limit(jacobi_kernel<20, 512, 1>, optin);
     rc |= raise_smem_limit(jacobi_kernel<24, 512, 3>, optin);
@@ -916,7 +916,9 @@ void launch_jacobi_typed(cudaStream_t s, const float* M, int l, int L, float* si
 // lanes of a pair, so the padded column stride 8 E covers L.  Up to L = 128
 // the columns and a staged M fit in shared memory (MODE 2), up to 160 the
 // columns alone (MODE 1); wider sketches keep M's columns in shared memory and
-// J in global memory (MODE 3).
+// J in global memory (MODE 3).  At E = 14 (L in [98, 112]) the 56 pairs fill
+// 448 threads exactly: no idle warps issue the round's instructions or wait
+// at its barrier (512 threads measured 9-20 us slower per SVD at l = 110).
 void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, float* Ut, float* Jt, float* work,
                        int* sweeps, int kv)
 {
@@ -928,7 +930,7 @@ void launch_jacobi_svd(cudaStream_t s, const float* M, int l, float* sigma, floa
     else if (e <= 8) launch_jacobi_typed<8, 512, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
     else if (e <= 10) launch_jacobi_typed<10, 512, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
     else if (e <= 12) launch_jacobi_typed<12, 512, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
-    else if (e <= 14) launch_jacobi_typed<14, 512, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
+    else if (e <= 14) launch_jacobi_typed<14, 448, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
     else if (e <= 16) launch_jacobi_typed<16, 512, 2>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
     else if (e <= 20) launch_jacobi_typed<20, 512, 1>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);
     else if (e <= 24) launch_jacobi_typed<24, 512, 3>(s, M, l, L, sigma, Ut, Jt, work, sweeps, kv);

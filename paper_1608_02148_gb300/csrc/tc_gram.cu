@@ -23,8 +23,11 @@
 // (round to nearest) one such chunk later, while the tensor core runs on.  Every CTA takes a range of rows and
 // writes its l x l partial; the partials are summed by the split reduction.
 //
-// Roles (192 threads): warp 0 issues the TMA loads, warp 1 allocates tensor
-// memory and issues the MMAs, warps 2..5 convert and run the epilogue.  All
+// Roles (320 threads): warp 0 issues the TMA loads, warp 1 allocates tensor
+// memory and issues the MMAs, warps 2..9 convert and run the epilogue: a
+// converter splits half of its row of the tile (four of its eight 16-byte
+// chunks), and in the drain each of the two warps of a TMEM lane quarter
+// sums half of the accumulator's columns.  All
 // mbarrier waits are bounded (see ptx.cuh); on expiry the kernel records
 // RSVDGB_ERR_TIMEOUT and leaves after its copies and MMAs in flight drain.
 #include <algorithm>
@@ -38,7 +41,7 @@ using namespace dev;
 
 constexpr int kBK = 32;       // rows of X per stage (one 128-byte swizzle row of FP32)
 constexpr int kRows = 128;    // tile rows (columns of X, padded): the MMA's M
-constexpr int kConvWarps = 4;
+constexpr int kConvWarps = 8;
 constexpr int kThreads = 64 + 32 * kConvWarps;
 constexpr int kMaxStages = 8;
 constexpr uint32_t kTile = kRows * kBK * 4;  // 16 KB
@@ -175,34 +178,36 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // =========================== converters + epilogue (warps 2..5)
-        const int t = (warp - 2) * 32 + lane;  // tile row (column of X) of this thread
+        const int cw = warp - 2;                // converter warp 0..7
+        const int half = cw >> 2;               // half of each row (converter) / of the columns (drain)
+        const int t = (cw & 3) * 32 + lane;     // tile row (column of X) of this thread
         // TMEM lane quarter warp % 4 holds accumulator rows 32 (warp % 4) ..;
         // this thread sums row r over the stages in FP32 registers
         const int q = warp & 3;
         const int r = q * 32 + lane;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        float sum[kRows];
+        float sum[kRows / 2];  // this warp's half of the columns: half * 64 + j
 #pragma unroll
-        for (int j = 0; j < kRows; ++j) sum[j] = 0.f;
+        for (int j = 0; j < kRows / 2; ++j) sum[j] = 0.f;
+        const int c0 = half * (kRows / 2);
         // add the accumulator of chunk ch into sum and hand it back to the MMA warp
         auto drain = [&](int64_t ch) -> bool {
             const int a = (int)(ch % kAcc);
             if (!mbar_wait_warp(&accf_bar[a], (uint32_t)((ch / kAcc) & 1), &abort_flag, p.status)) return false;
             tmem_fence_after();
             // two batches of four 16-column loads, one wait each
-#pragma unroll
-            for (int b0 = 0; b0 < kRows; b0 += 64) {
+            {
                 uint32_t v[4][16];
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
-                    if (b0 + 16 * t < l_pad) tmem_ld16(tmem + (uint32_t)(a * kRows + b0 + 16 * t) + lane_off, v[t]);
+                    if (c0 + 16 * t < l_pad) tmem_ld16(tmem + (uint32_t)(a * kRows + c0 + 16 * t) + lane_off, v[t]);
                 tmem_wait_ld();
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
-                    if (b0 + 16 * t < l_pad) {
+                    if (c0 + 16 * t < l_pad) {
                         tmem_regs_ready(v[t]);
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) sum[b0 + 16 * t + e] += __uint_as_float(v[t][e]);
+                        for (int e = 0; e < 16; ++e) sum[16 * t + e] += __uint_as_float(v[t][e]);
                     }
             }
             tmem_fence_before();
@@ -224,8 +229,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float4* hi = (float4*)(smem + (size_t)s * kStage + mtx * 2 * kTile + t * 128);
                     float4* lo = (float4*)((uint8_t*)hi + kTile);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int ch = j ^ (t & 7);
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int ch = (half * 4 + jj) ^ (t & 7);
                         const float4 v = hi[ch];
                         float4 h, r;
                         h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
@@ -254,10 +259,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         float* out = p.part + (int64_t)blockIdx.x * l_pad * l_pad;
         if (ok && r < l_pad) {
 #pragma unroll
-            for (int j0 = 0; j0 < kRows; j0 += 16)
-                if (j0 < l_pad)
+            for (int j0 = 0; j0 < kRows / 2; j0 += 16)
+                if (c0 + j0 < l_pad)
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) out[(int64_t)r * l_pad + j0 + e] = sum[j0 + e];
+                    for (int e = 0; e < 16; ++e) out[(int64_t)r * l_pad + c0 + j0 + e] = sum[j0 + e];
         }
         if (!ok) {
             // the MMA warp's final commit tells when its work has drained
