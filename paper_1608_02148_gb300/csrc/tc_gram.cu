@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             (void)ok;
         }
     } else {
-        // =========================== converters + epilogue (warps 2..5)
+        // =========================== converters + epilogue (warps 2..9)
         const int cw = warp - 2;                // converter warp 0..7
         const int half = cw >> 2;               // half of each row (converter) / of the columns (drain)
         const int t = (cw & 3) * 32 + lane;     // tile row (column of X) of this thread
