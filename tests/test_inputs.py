@@ -64,6 +64,29 @@ def test_spiked_noise_recipe():
     assert sv[-1] < edge  # the bulk sits at the noise level
 
 
+def test_step_noise_recipe():
+    """The BF16-stored step-spectrum workload: sigma = 1 for i <= step and
+    1e-2 beyond on the two-reflector factors, plus i.i.d. N(0, s^2) noise;
+    the BF16 form is the FP32 form rounded to BF16."""
+    m, n, step, s_noise = 2000, 600, 40, 1e-5
+    A32 = inputs.step_noise(m, n, step, s_noise, seed=9, bf16=False)
+    A16 = inputs.step_noise(m, n, step, s_noise, seed=9, bf16=True)
+    assert A32.dtype == torch.float32 and A16.dtype == torch.bfloat16
+    assert torch.equal(A16, A32.to(torch.bfloat16))
+    sigma = np.where(np.arange(1, n + 1) <= step, 1.0, 1e-2)
+    sv = np.linalg.svd(A32.double().numpy(), compute_uv=False)
+    E = (A32.double() - inputs.planted_reflector(m, n, sigma, seed=9).double()).numpy()
+    assert abs(E.std() / s_noise - 1.0) < 2e-2 and abs(E.mean()) < 0.1 * s_noise
+    # the noise's spectral norm is the Gaussian edge s (sqrt m + sqrt n), and by
+    # Weyl's inequality every singular value stays within it of the planted one
+    e2 = np.linalg.norm(E, 2)
+    assert abs(e2 / (s_noise * (math.sqrt(m) + math.sqrt(n))) - 1.0) < 5e-2
+    assert np.all(np.abs(sv - sigma) <= e2 + 1e-6)
+    assert np.all(sv[:step] > 0.99) and np.all(np.abs(sv[step:] - 1e-2) < 1e-3)
+    energy = np.sum(sigma ** 2) + s_noise ** 2 * m * n
+    assert abs(float((A32.double() ** 2).sum()) / energy - 1.0) < 1e-3
+
+
 def test_ragged_shapes_and_rates_in_range():
     ms, ns, rates = inputs.ragged_shapes(4096, (256, 4096), (64, 1024), seed=0x160802148 + 4000)
     assert ms.min() >= 256 and ms.max() <= 4096 and ns.min() >= 64 and ns.max() <= 1024
