@@ -117,6 +117,8 @@ MUTANTS = [
     ("lu_rows_not_tracked", C, [("            row[j] = row[p];\n            row[p] = t;", "            (void)t;")], LU),
     ("lu_multiplier_not_stored", C, [("            W[i * l + j] = f;\n", "")], LU),
     ("lu_ties_to_the_last_row", C, [("if (fabs(W[i * l + j]) > best) {", "if (fabs(W[i * l + j]) >= best) {")], LU),
+    ("lu_scheme_one_iteration_short", C, [("for (int j = 0; j < q && scheme == 1; ++j) {",
+                                           "for (int j = 1; j < q && scheme == 1; ++j) {")], LU),
     # robust PCA (Algorithm rrpca)
     ("rrpca_no_singular_value_shrinkage", PY, [("ds = np.maximum(d[:svp] - 1.0 / mu, 0.0)", "ds = d[:svp]")], RRPCA),
     ("rrpca_threshold_times_mu", PY, [("soft_threshold(M - L + Z / mu, lam / mu)", "soft_threshold(M - L + Z / mu, lam * mu)")],
