@@ -33,8 +33,10 @@
 //     within 2^-24 of the scaled unit where the parts fall below FP16's
 //     normal range; three kind::f16 MMAs per K step of 16, a_hi p_hi + a_hi
 //     p_lo + a_lo p_hi, each product exact in FP32; the epilogue multiplies
-//     column j by 2^-(eA + ej).  Each product is within 2^-20 |a||p| plus the
-//     FP16 underflow term.  The same error as 3xTF32 at half the tensor time
+//     column j by 2^-(eA + ej).  Each product is within 2^-19 |a||p| (the
+//     dropped a_lo p_lo, at most 2^-20, and the two roundings of the lo
+//     parts, 2^-21 each) plus the FP16 underflow term.  The same bound as
+//     3xTF32 at half the tensor time
 //     (K = 16 per FP16 MMA, 8 per TF32 MMA, same issue rate), and a 16-bit A
 //     operand takes half the TMEM, so the converted-A ring is twice as deep.
 //     BF16-stored A is exact in FP16 after the scaling, so only a p_hi +
