@@ -12,6 +12,8 @@
   and rounded to nearest E4M3 (saturating) is within 2^-4 of itself,
   relative, in E4M3's normal range, and within 2^-10 (half the smallest
   subnormal step, 2^-9) of the scaled unit below it.
+* 3xTF32: the three TF32 products are within 2^-19 |a||p| whether the tensor
+  core truncates or rounds the low part of a.
 The tolerances of tests/test_gpu_tc.py are built from these bounds."""
 import numpy as np
 import pytest
@@ -79,6 +81,33 @@ def test_fp16x3_products(seed):
     big = np.abs(exact) > 1e-3 * np.abs(exact).max()
     rel = np.abs(approx - exact)[big] / np.abs(exact)[big]
     assert rel.max() > 2.0 ** -20
+
+
+def rna_tf32(x):
+    """float32 x rounded to TF32 (10 explicit mantissa bits), ties away from
+    zero (the cvt.rna rule): add half of the dropped range, then clear it."""
+    b = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    return ((b + 0x1000) & 0xFFFFE000).astype(np.uint32).view(np.float32)
+
+
+@pytest.mark.parametrize("lo_rule", ["truncate", "round"])
+def test_3xtf32_products(lo_rule):
+    """a_hi = a with 13 bits cleared, a_lo = a - a_hi (exact), taken by the
+    tensor core as TF32 either truncated or rounded; the panel split by
+    round-to-nearest TF32 twice; a_hi p_hi + a_hi p_lo + a_lo p_hi is within
+    2^-19 |a||p| whichever rule the tensor core applies to a_lo."""
+    rng = np.random.default_rng(7)
+    a = (rng.standard_normal(100000) * np.exp2(rng.integers(-20, 20, size=100000))).astype(np.float32)
+    p = (rng.standard_normal(100000) * np.exp2(rng.integers(-20, 20, size=100000))).astype(np.float32)
+    ah = trunc13(a)
+    al = (a - ah).astype(np.float32)
+    al = trunc13(al) if lo_rule == "truncate" else rna_tf32(al)
+    ph = rna_tf32(p)
+    pl = rna_tf32((p - ph).astype(np.float32))
+    f = lambda v: v.astype(np.float64)
+    approx = f(ah) * f(ph) + f(ah) * f(pl) + f(al) * f(ph)
+    exact = f(a) * f(p)
+    assert np.all(np.abs(approx - exact) <= 2.0 ** -19 * np.abs(exact))
 
 
 def e4m3_round(x):
